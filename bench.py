@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Throughput of the IMRP hot path (radius sort, moment scans, field gather,
+leapfrog push, walls, Q_diff tally) in particle-steps/s.
+
+Default workload: N = 2e6 electron super-particles, l_max = 16, mixed precision
+(FP32 state, harmonics and push; FP64 scan carries), T_e = 3 eV,
+n_e = 1e16 m^-3, R_E = 4 mm, R_D = 5 mm, eps_D = 4, R_out = R_D + 20 lambda_D,
+dt = 0.05/omega_pe, Gaussian 1 V pulse; seeded synthetic Maxwellian shell.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica on its own GPU
+(the instances do not exchange data); value = all particle-steps / max time.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at N=2e6,l_max=16 (mixed vs FP64); served spectra p50/p99"
+UNIT = "particle-steps/s"
+LAUNCHES_PER_STEP = 18  # 12 sort + reorder + moments + tile scan + group scan + finalize + field
+
+
+def workload_desc(w):
+    return (f"{w.name}: N={w.N}, l_max={w.l_max}, T_e={w.T_e_eV} eV, n_e={w.n_e_m3:g} m^-3, "
+            f"R_E={w.R_E_m*1e3:g} mm, R_D={w.R_D_m*1e3:g} mm, eps_D={w.eps_D}, "
+            f"R_out=R_D+{w.outer_debye:g} lambda_D, dt={w.dt}/omega_pe, Gaussian {w.V_volts} V pulse "
+            f"(width {w.width_wpe}), {'mixed (FP32 state/harmonics/push, FP64 carries)' if w.precision else 'FP64'}")
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2111_13072_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([s.strip() for s in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for k, nm in enumerate(names):
+                    if r[4 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, budget_s=15.0, L=None):
+    """The FP64 oracle (radius-ordered scan evaluator, leapfrog, walls) on a
+    bounded sample: a smaller instance of the same workload (same geometry,
+    density, temperature and l_max), timed on one host core."""
+    import oracle
+    from paper_2111_13072_gb300.inputs import workload_state
+    L = w.l_max if L is None else L
+
+    def make(n):
+        p = oracle.from_physical(w.R_E_m, w.R_D_m, w.eps_D, w.R_out_m, w.n_e_m3, w.T_e_eV, n, L, w.dt,
+                                 drive_kind=w.drive_kind, V_volts=w.V_volts, width_wpe=w.width_wpe,
+                                 seed=w.seed)
+        x, v = workload_state(w, N=n)
+        return p, x, v
+
+    p, x, v = make(1000)
+    t = time.perf_counter()
+    oracle.run(p, x, v, 1)
+    per = (time.perf_counter() - t) / 1000.0
+    ns = int(max(1000, min(20000, budget_s / 10.0 / per)))
+    steps = max(1, int(budget_s / (per * ns)))
+    p, x, v = make(ns)
+    t = time.perf_counter()
+    oracle.run(p, x, v, steps)
+    dt = time.perf_counter() - t
+    return {"value": ns * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{ns} particles x {steps} steps of the same workload (l_max={L}), "
+                      f"scan evaluator, {dt:.1f} s"}
+
+
+def run_reference(args, w):
+    """--impl reference: the FP64 CPU oracle as the reference arm."""
+    import oracle
+    from paper_2111_13072_gb300.inputs import workload_state
+    p1 = oracle.from_physical(w.R_E_m, w.R_D_m, w.eps_D, w.R_out_m, w.n_e_m3, w.T_e_eV, 1000,
+                              w.l_max, w.dt, drive_kind=w.drive_kind, V_volts=w.V_volts,
+                              width_wpe=w.width_wpe, seed=w.seed)
+    x, v = workload_state(w, N=1000)
+    t = time.perf_counter()
+    oracle.run(p1, x, v, 1)
+    per = (time.perf_counter() - t) / 1000.0
+    total_budget = 90.0
+    ns = int(max(200, min(20000, total_budget / (args.steps + args.warmup) / per)))
+    p = oracle.from_physical(w.R_E_m, w.R_D_m, w.eps_D, w.R_out_m, w.n_e_m3, w.T_e_eV, ns, w.l_max,
+                             w.dt, drive_kind=w.drive_kind, V_volts=w.V_volts, width_wpe=w.width_wpe,
+                             seed=w.seed)
+    x, v = workload_state(w, N=ns)
+    x, v, _, _, _ = oracle.run(p, x, v, args.warmup)
+    t = time.perf_counter()
+    oracle.run(p, x, v, args.steps, step0=args.warmup, first_half_kick=False)
+    dt = time.perf_counter() - t
+    val = ns * args.steps / dt
+    sample = f"{ns} particles per step (same workload, l_max={w.l_max}), scan evaluator, FP64"
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload_desc(w), "sample_particles": ns, "parallelism": "host, 1 core"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mixed_n2e6_l16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2111_13072_gb300.inputs import WORKLOADS, workload_state
+    w = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, w)
+        return
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2111_13072_gb300 import build, imrp
+    build.build()
+    x, v = workload_state(w)
+    p = imrp.params_from_workload(w, seed=w.seed + rank)
+    sim = imrp.Sim(p)
+    stream = torch.cuda.Stream()
+    sim.set_stream(stream.cuda_stream)
+    sim.load(x, v)
+    sim.step_async(args.warmup)
+    sim.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        sim.step_async(args.steps)
+        e1.record(stream)
+        sim.sync()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    N = w.N
+    value = N * args.steps * world / (ms / 1e3)
+    clocks = clk.summary()
+
+    # per-stage device time (real steps launched one by one, CUDA events)
+    nprof = min(args.steps, 50)
+    stages = sim.profile_steps(nprof)
+    field_ms = stages["field"] / nprof
+    K = (w.l_max + 1) ** 2
+    flops_per_launch = 24.0 * K * N  # algorithmic FP32 flops of one particle-step, times N
+    achieved = flops_per_launch / (field_ms / 1e3) / 1e12
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "field_traffic.json")
+    if os.path.exists(tf):
+        try:
+            rec = json.load(open(tf))
+            if rec.get("kernel_hash") == kernel_hash() and rec.get("workload") == w.name:
+                traffic = rec.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_field (gather+push)",
+                "peak_basis": f"152 SMs x 128 FP32 FMA/clk x 2 x median SM clock {sm_mhz:.0f} MHz",
+                "stage_ms_per_step": {k: v / nprof for k, v in stages.items()}}
+
+    # end to end through the public API with host buffers (pinned):
+    # load the state (H2D), one step, read Q_diff (D2H), every step.
+    xh = torch.from_numpy(x).pin_memory()
+    vh = torch.from_numpy(v).pin_memory()
+    qh = torch.zeros(1, dtype=torch.float64).pin_memory()
+    ne = max(3, min(args.steps, 50))
+    sim.load_ptr(xh.data_ptr(), vh.data_ptr(), N)
+    sim.step_ptr(1, qh.data_ptr())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        sim.load_ptr(xh.data_ptr(), vh.data_ptr(), N)
+        sim.step_ptr(1, qh.data_ptr())
+    barrier()
+    te = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([te], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    e2e = {"value": N * ne * world / te, "unit": UNIT, "h2d_bytes_per_step": 48 * N,
+           "d2h_bytes_per_step": 8, "steps": ne}
+
+    fp64 = None
+    if not args.no_fp64:
+        p64 = imrp.params_from_workload(w, precision=0, seed=w.seed + rank)
+        with imrp.Sim(p64) as s64:
+            s64.set_stream(stream.cuda_stream)
+            s64.load(x, v)
+            s64.step_async(3)
+            s64.sync()
+            k64 = 6
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            s64.step_async(k64)
+            f1.record(stream)
+            s64.sync()
+            fp64 = {"value": N * k64 / (f0.elapsed_time(f1) / 1e3), "unit": UNIT, "steps": k64,
+                    "note": "plain FP64 GPU path, same workload"}
+    sim.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w.precision else "f64",
+                "data": "synthetic",
+                "config": {"workload": workload_desc(w), "N": N, "l_max": w.l_max,
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (per-step working set > 300 MB)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks, "fp64_gpu": fp64}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * imrp.h -- C ABI of the GB300-native spectral kinetic simulation of the ideal
+ * Multipole Resonance Probe (Gong, Friedrichs, Oberrath, Brinkmann,
+ * "Kinetic Simulation of the Ideal Multipole Resonance Probe", arXiv 2111.13072).
+ *
+ * One context owns one plasma instance on one GPU: N electron super-particles
+ * (charge q = -1, mass m = 1 in the units below) around a metal sphere of radius
+ * R_E covered by a dielectric shell (permittivity eps_D) out to R, with an
+ * immobile uniform ion background filling R <= r <= R_out.
+ *
+ * Units (Sec. 4 of the paper): lengths in R (= R_D, outer radius of the
+ * dielectric), time in 1/omega_pe, velocities in R*omega_pe, charge in e, mass
+ * in m_e. Positions and velocities cross this ABI in these units as FP64.
+ *
+ * Conventions for every entry point:
+ *   - returns IMRP_OK (0) on success or a negative IMRP_E_* code; the message
+ *     of the last failure on a context is available from imrp_last_error();
+ *   - no exception crosses the ABI; no entry point aborts the process;
+ *   - host buffers are owned by the caller and only read or written during the
+ *     call; all device memory is owned by the context;
+ *   - calls on one context must not overlap (one host thread at a time);
+ *   - calls return after the GPU work they issued has finished, except
+ *     imrp_step_async().
+ */
+#ifndef IMRP_H
+#define IMRP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IMRP_OK 0
+#define IMRP_E_INVAL (-1)   /* invalid argument or parameter                     */
+#define IMRP_E_NOMEM (-2)   /* device or host allocation failed                  */
+#define IMRP_E_CUDA (-3)    /* a CUDA call failed (message has the CUDA error)   */
+#define IMRP_E_TIMEOUT (-4) /* a bounded device-side wait gave up                */
+#define IMRP_E_NAN (-5)     /* a non-finite value appeared in the state          */
+#define IMRP_E_STATE (-6)   /* call out of order (e.g. step before load)         */
+
+typedef struct imrp_ctx imrp_ctx;
+
+/* Physical problem and numerical choices. Fill with imrp_default_params()
+ * and override fields. */
+typedef struct imrp_params {
+  double R_E_m;      /* electrode radius R_E [m] (Sec. 2: R_E = R - Rd)            */
+  double R_D_m;      /* outer radius of the dielectric shell, the length unit R [m] */
+  double eps_D;      /* relative permittivity eps_r of the shell (App. A)         */
+  double R_out_m;    /* radius of the outer particle wall [m] (Sec. 4)            */
+  double n_e_m3;     /* electron density n_inf [m^-3] (Sec. 4 units)              */
+  double T_e_eV;     /* electron temperature [eV]; informational (the field does not use it) */
+  int64_t N;         /* capacity: maximum number of super-particles               */
+  int32_t l_max;     /* truncation degree of the projection P^ (Sec. 2/3); one of 1,2,4,8,12,16,24 */
+  int32_t m0_only;   /* must be 0 (full (l,m) expansion)                          */
+  double dt;         /* time step [1/omega_pe]                                    */
+  int32_t drive_kind; /* 0 Gaussian pulse, 1 impulse at the first step (Sec. 4), 2 off */
+  int32_t wall_rule;  /* 0 diffuse reflection (Sec. 4), 1 specular reflection      */
+  double V_volts;    /* drive amplitude u_asy [V]: peak of the pulse or the impulse */
+  double width_wpe;  /* Gaussian pulse standard deviation [1/omega_pe]             */
+  double t0_wpe;     /* Gaussian pulse centre [1/omega_pe]; <= 0 selects 4*width   */
+  int32_t self_image; /* 0: a particle does not feel its own image (the pair sum of Sec. 2 has i != k); 1: it does */
+  int32_t precision;  /* 0 FP64 throughout; 1 mixed: FP32 state, harmonics and push, FP64 carries */
+  uint64_t seed;     /* key of the counter-based wall random numbers              */
+  double q_s;        /* surface charge Q_S in super-particle charges (Sec. 3), usually 0 */
+} imrp_params;
+
+/* Derived dimensionless quantities of a context (read-only). */
+typedef struct imrp_info {
+  double d;          /* relative dielectric thickness, R_E = (1 - d) R             */
+  double r_out;      /* outer wall radius in units of R                            */
+  double n_tilde;    /* super-particles per unit cube at density n_inf (Sec. 4)    */
+  double n_ion;      /* ion super-particles of the uniform background (= N loaded) */
+  double v_hat;      /* drive amplitude in units of e n_inf R^2 / eps0            */
+  double lambda_D;   /* Debye length in units of R                                 */
+  double omega_pe;   /* electron plasma frequency [1/s]                            */
+  int64_t n;         /* particles currently loaded                                 */
+  int64_t step;      /* steps taken since the last load                            */
+  int32_t l_max;
+  int32_t precision;
+} imrp_info;
+
+/* Fills p with the small FP64 workload: R_E = 4 mm, R_D = 5 mm, eps_D = 4,
+ * n_e = 1e15 m^-3, T_e = 2 eV, R_out = R_D + 20 lambda_D, l_max = 8, dt = 0.05,
+ * Gaussian pulse 1 V, width 2, diffuse walls, N = 20000, FP64. */
+void imrp_default_params(imrp_params* p);
+
+/* Validates p, derives the dimensionless problem (Sec. 4), allocates all
+ * device memory for N particles on the current CUDA device and creates the
+ * context's stream. *out receives the context; on failure *out is NULL.
+ * Errors: IMRP_E_INVAL (bad geometry, l_max not instantiated, N < 1 ...),
+ * IMRP_E_NOMEM, IMRP_E_CUDA. */
+int imrp_create(const imrp_params* p, imrp_ctx** out);
+
+/* Frees all device memory and the stream. NULL is accepted. */
+int imrp_destroy(imrp_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none). Valid until the next call. */
+const char* imrp_last_error(const imrp_ctx* ctx);
+
+/* Makes the context issue its work on a caller-owned cudaStream_t (passed as
+ * void*). NULL restores the context's own stream. */
+int imrp_set_stream(imrp_ctx* ctx, void* cuda_stream);
+
+/* Loads n <= N particles from host FP64 arrays x[n][3] (positions, units of R,
+ * each with 1 < |x| < r_out) and v[n][3] (velocities synchronous with x, units
+ * of R omega_pe). Particle ids are 0..n-1 in input order. Resets the step
+ * counter and the Q_diff history; the ion background is set to n ions.
+ * Errors: IMRP_E_INVAL (n out of range, a position outside the shell, a
+ * non-finite value). */
+int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t n);
+
+/* Advances n_steps leapfrog steps (Sec. 2 canonical equations; kick-drift
+ * with merged kicks, the first kick after a load is dt/2). Each step sorts the
+ * particles by radius, evaluates the field of the modified, truncated Green's
+ * function G~ (Sec. 3) plus ions, Q_S and the drive u_asy(t_n) Psi_anti
+ * (Sec. 3-4), pushes, applies the wall rule (Sec. 4) and records
+ * Q_diff(t_n) = -(1/n~) sum_i q_i Psi_anti,L(x_i) (Sec. 4) at the positions
+ * x_n used by the step. qdiff_out and uasy_out (host, n_steps doubles each,
+ * either may be NULL) receive Q_diff(t_n) and u_asy(t_n).
+ * Errors: IMRP_E_STATE (nothing loaded), IMRP_E_TIMEOUT, IMRP_E_NAN, IMRP_E_CUDA. */
+int imrp_step(imrp_ctx* ctx, int64_t n_steps, double* qdiff_out, double* uasy_out);
+
+/* As imrp_step without host outputs and without waiting for the GPU: the work
+ * is queued on the context's stream (replayed CUDA graphs). Device-side errors
+ * surface at the next synchronising call. */
+int imrp_step_async(imrp_ctx* ctx, int64_t n_steps);
+
+/* Waits for queued work and checks the device error flags. */
+int imrp_sync(imrp_ctx* ctx);
+
+/* Copies Q_diff(t_n) and u_asy(t_n) for steps first .. first+count-1 since the
+ * last load to host arrays (either may be NULL). */
+int imrp_get_qdiff(imrp_ctx* ctx, int64_t first, int64_t count, double* qdiff, double* uasy);
+
+/* Field E at the current positions (what the next step would use, with the
+ * drive u_asy(t_n) of the next step), written to E[n][3] in particle-id
+ * order. Does not advance the state. */
+int imrp_get_field(imrp_ctx* ctx, double* E);
+
+/* Current state in particle-id order: x[n][3] and the half-step velocity
+ * v_{n-1/2}[n][3] (v synchronous with x right after a load). Either may be NULL. */
+int imrp_get_particles(imrp_ctx* ctx, double* x, double* v);
+
+/* Spectrum of the run since the last load (Sec. 4): admittance
+ * Y(w) = i w Q^(w)/U^(w) with Q^ = dt sum_n (Q_n - Q_0) e^{-i w t_n} and
+ * U^ = sum_n w_n u_n e^{-i w t_n} (w_n: kick weight of step n), at
+ * w_j = (j+1) w_max / n_freq, j < n_freq; the sums run on the GPU in FP64.
+ * omega, reY, imY: host arrays of n_freq (any may be NULL). w_res: argmax Re Y
+ * (parabolic refinement); dw: full width at half maximum of Re Y around it.
+ * fit[4] (may be NULL): a, b, c, phi of the least-squares fit
+ * a e^{-b tau} sin(c tau + phi), tau = t - t_fit, over t >= t_fit, with
+ * t_fit = t0 + 3 width for the Gaussian pulse and 0 otherwise (Sec. 4, s = 1).
+ * Errors: IMRP_E_STATE (fewer than 8 steps recorded), IMRP_E_INVAL. */
+int imrp_spectrum(imrp_ctx* ctx, int64_t n_freq, double w_max, double* omega, double* reY,
+                  double* imY, double* w_res, double* dw, double* fit);
+
+/* Derived quantities of the context. */
+int imrp_get_info(const imrp_ctx* ctx, imrp_info* info);
+
+/* Stage timing. Runs n_steps steps launched one by one (no CUDA graph) with a
+ * CUDA event pair around each stage on the context's stream, and writes the
+ * summed device time of each stage in milliseconds to ms[IMRP_N_STAGES]:
+ * 0 radix sort, 1 reorder, 2 tile moments, 3 scans + finalize,
+ * 4 field gather + push. The steps are real steps (they advance the state and
+ * are recorded like imrp_step). */
+#define IMRP_N_STAGES 5
+int imrp_profile_steps(imrp_ctx* ctx, int64_t n_steps, double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMRP_H */

@@ -32,7 +32,15 @@ M_E = 9.1093837015e-31
 
 def build(force: bool = False) -> str:
     """Compiles the C oracle with gcc (plain -O2, IEEE arithmetic)."""
+    import platform
+    import shutil
+    stamp = os.path.join(_BUILD, "MACHINE")
+    if os.path.isdir(_BUILD) and (not os.path.exists(stamp) or open(stamp).read().strip() != platform.machine()):
+        shutil.rmtree(_BUILD, ignore_errors=True)
     os.makedirs(_BUILD, exist_ok=True)
+    if not os.path.exists(stamp):
+        with open(stamp, "w") as f:
+            f.write(platform.machine())
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])

@@ -1,0 +1,773 @@
+// Host side of the C ABI declared in include/imrp.h: parameter derivation
+// (Sec. 4 units), device memory, the per-step launch sequence, CUDA graphs of
+// step pairs, and the spectrum post-processing (Sec. 4).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/imrp.h"
+#include "imrp_internal.h"
+
+using namespace imrp;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kE = 1.602176634e-19;     // C
+constexpr double kEps0 = 8.8541878128e-12; // F/m
+constexpr double kMe = 9.1093837015e-31;   // kg
+
+std::once_flag g_reg_once;
+std::vector<KernelSet<float>> g_ks_f;
+std::vector<KernelSet<double>> g_ks_d;
+
+void ensure_registry() {
+  std::call_once(g_reg_once, [] { register_all(g_ks_f, g_ks_d); });
+}
+
+template <class T> const KernelSet<T>* find_set(int L);
+template <> const KernelSet<float>* find_set<float>(int L) {
+  for (auto& k : g_ks_f) if (k.L == L) return &k;
+  return nullptr;
+}
+template <> const KernelSet<double>* find_set<double>(int L) {
+  for (auto& k : g_ks_d) if (k.L == L) return &k;
+  return nullptr;
+}
+
+// Coefficients of the library (written from App. A and Sec. 3; R = 1).
+double coef_f(int l, double d, double eps) {
+  const double x = pow(1.0 - d, 2 * l + 1);
+  return (l * (eps - 1.0) + (l + eps + l * eps) * x) / ((l + 1 + l * eps) + (l + 1) * (eps - 1.0) * x);
+}
+double coef_bP(int l, double d, double eps) {
+  const double den = (l + 1) * (eps - 1.0) * pow(1.0 - d, 2 * l + 1) + l * eps + l + 1;
+  return (2 * l + 1) * eps * pow(1.0 - d, l + 1) / den;
+}
+// c_l' of Sec. 3 for odd degree l = 2l'-1: (-1/2)^{l'+1} (4l'-1) (2l'-3)!! / l'!
+double coef_cprime(int lp) {
+  double df = 1.0;
+  for (int k = 2 * lp - 3; k > 1; k -= 2) df *= k;
+  double fact = 1.0;
+  for (int k = 2; k <= lp; ++k) fact *= k;
+  double sgn = ((lp + 1) % 2 == 0) ? 1.0 : -1.0;
+  return sgn * pow(0.5, lp + 1) * (4.0 * lp - 1.0) * df / fact;
+}
+
+}  // namespace
+
+struct imrp_ctx {
+  imrp_params p{};
+  std::string err;
+  int device = 0;
+  int L = 8;
+  int prec = 0;  // 0 fp64, 1 mixed (fp32)
+  // derived
+  double d = 0, r_out = 0, v_hat = 0, lambda_D = 0, omega_pe = 0, t0 = 0;
+  double n_tilde = 0, n_ion = 0;
+  double f[kTabL] = {0}, canti[kTabL] = {0};
+  int64_t cap = 0, n = 0;
+  int64_t host_step = 0;
+  bool loaded = false, keys_valid = false;
+  int nc = 0;
+  int64_t ntiles = 0, ngroups = 0;
+  int wpb = 8;
+  // streams / graphs
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  cudaGraphExec_t graph2 = nullptr;
+  int graph_cur = -1;
+  // device memory
+  void* st_buf[2][6] = {{nullptr}};
+  uint32_t* id_buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint32_t *key0 = nullptr, *idx0 = nullptr, *key1 = nullptr, *idx1 = nullptr, *hist = nullptr;
+  void *agg = nullptr, *pfx = nullptr, *gbase = nullptr, *tot = nullptr, *eout = nullptr;
+  double *gagg = nullptr, *totd = nullptr;
+  double *qhist = nullptr, *uhist = nullptr;
+  int64_t hcap = 0;
+  double* stage = nullptr;  // [cap][6] FP64 staging for load / readback
+  StepState* st = nullptr;
+  int* derr = nullptr;
+  double* dft = nullptr;
+  int64_t dft_cap = 0;
+
+  int fail(int code, const char* fmt, ...) {
+    char b[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b, sizeof(b), fmt, ap);
+    va_end(ap);
+    err = b;
+    return code;
+  }
+};
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ctx->fail(IMRP_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                       __FILE__, __LINE__);                                             \
+  } while (0)
+
+namespace {
+
+template <class T> T** state_ptrs(imrp_ctx* c, int which) { return reinterpret_cast<T**>(c->st_buf[which]); }
+
+void free_all(imrp_ctx* c) {
+  if (c->graph2) cudaGraphExecDestroy(c->graph2);
+  c->graph2 = nullptr;
+  for (int b = 0; b < 2; ++b) {
+    for (int k = 0; k < 6; ++k) { cudaFree(c->st_buf[b][k]); c->st_buf[b][k] = nullptr; }
+    cudaFree(c->id_buf[b]); c->id_buf[b] = nullptr;
+  }
+  void* ps[] = {c->key0, c->idx0, c->key1, c->idx1, c->hist, c->agg, c->pfx, c->gbase, c->tot,
+                c->eout, c->gagg, c->totd, c->qhist, c->uhist, c->stage, c->st, c->derr, c->dft};
+  for (void* p : ps) cudaFree(p);
+  c->key0 = c->idx0 = c->key1 = c->idx1 = c->hist = nullptr;
+  c->agg = c->pfx = c->gbase = c->tot = c->eout = nullptr;
+  c->gagg = c->totd = c->qhist = c->uhist = c->stage = c->dft = nullptr;
+  c->st = nullptr;
+  c->derr = nullptr;
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  c->own_stream = nullptr;
+}
+
+int check_err(imrp_ctx* ctx) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h) {
+    CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
+    if (h & kErrNaN) return ctx->fail(IMRP_E_NAN, "non-finite value in the particle state");
+    if (h & kErrTimeout) return ctx->fail(IMRP_E_TIMEOUT, "a device-side wait gave up");
+    if (h & kErrRange) return ctx->fail(IMRP_E_INVAL, "a particle lies outside 1 < r < r_out");
+  }
+  return IMRP_OK;
+}
+
+int grow_history(imrp_ctx* ctx, int64_t need) {
+  if (need <= ctx->hcap) return IMRP_OK;
+  int64_t ncap = std::max<int64_t>(need, std::max<int64_t>(2 * ctx->hcap, 4096));
+  double *q = nullptr, *u = nullptr;
+  CK(cudaMalloc(&q, ncap * sizeof(double)));
+  CK(cudaMalloc(&u, ncap * sizeof(double)));
+  if (ctx->hcap) {
+    CK(cudaMemcpyAsync(q, ctx->qhist, ctx->hcap * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(u, ctx->uhist, ctx->hcap * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  cudaFree(ctx->qhist);
+  cudaFree(ctx->uhist);
+  ctx->qhist = q;
+  ctx->uhist = u;
+  ctx->hcap = ncap;
+  if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+  return IMRP_OK;
+}
+
+// Launches one step (record = 1) or the field evaluation without push (record = 0).
+// ev (optional): IMRP_N_STAGES + 1 events recorded at the stage boundaries.
+template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nullptr) {
+  const KernelSet<T>* ks = find_set<T>(ctx->L);
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  T** src = state_ptrs<T>(ctx, ctx->cur);
+  T** dst = state_ptrs<T>(ctx, 1 - ctx->cur);
+  if (!ctx->keys_valid) {
+    launch_keys<T>(src[0], src[1], src[2], ctx->key0, ctx->idx0, n,
+                   4294967296.0 / (ctx->r_out * ctx->r_out - 1.0), s);
+  }
+  if (ev) cudaEventRecord(ev[0], s);
+  launch_radix_sort(ctx->key0, ctx->idx0, ctx->key1, ctx->idx1, ctx->hist, n, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  launch_reorder<T>(src, dst, ctx->id_buf[ctx->cur], ctx->id_buf[1 - ctx->cur], ctx->idx0, n, s);
+  ctx->cur = 1 - ctx->cur;
+  T** S = dst;
+  MomArgs<T> ma;
+  ma.x = S[0]; ma.y = S[1]; ma.z = S[2];
+  ma.n = n;
+  ma.rho_inv = T(1.0 / ctx->r_out);
+  ma.agg = static_cast<T*>(ctx->agg);
+  if (ev) cudaEventRecord(ev[2], s);
+  ks->moments(ma, s);
+  if (ev) cudaEventRecord(ev[3], s);
+  launch_tile_scan<T>(static_cast<T*>(ctx->agg), static_cast<T*>(ctx->pfx), ctx->gagg, ctx->ntiles,
+                      ctx->nc, s);
+  launch_group_scan<T>(ctx->gagg, static_cast<T*>(ctx->gbase), static_cast<T*>(ctx->tot), ctx->totd,
+                       ctx->ngroups, ctx->nc, s);
+  FinalizeArgs fa;
+  fa.st = ctx->st;
+  fa.totd = ctx->totd;
+  fa.qhist = ctx->qhist;
+  fa.uhist = ctx->uhist;
+  fa.cap = ctx->hcap;
+  fa.record = record ? 1 : 0;
+  fa.L = ctx->L;
+  fa.drive_kind = ctx->p.drive_kind;
+  fa.inv_ntilde = 1.0 / ctx->n_tilde;
+  fa.v_hat = ctx->v_hat;
+  fa.sigma = ctx->p.width_wpe;
+  fa.t0 = ctx->t0;
+  fa.dt = ctx->p.dt;
+  for (int l = 0; l < kTabL; ++l) fa.canti[l] = ctx->canti[l];
+  launch_finalize(fa, s);
+  if (ev) cudaEventRecord(ev[4], s);
+  FieldArgs<T> a;
+  a.x = S[0]; a.y = S[1]; a.z = S[2]; a.vx = S[3]; a.vy = S[4]; a.vz = S[5];
+  a.id = ctx->id_buf[ctx->cur];
+  a.key = ctx->key0;
+  a.kidx = ctx->idx0;
+  a.n = n;
+  a.pfx = static_cast<const T*>(ctx->pfx);
+  a.gbase = static_cast<const T*>(ctx->gbase);
+  a.tot = static_cast<const T*>(ctx->tot);
+  a.st = ctx->st;
+  a.Eout = static_cast<T*>(ctx->eout);
+  a.err = ctx->derr;
+  a.mode = record ? 0 : 1;
+  a.L = ctx->L;
+  a.rho = T(ctx->r_out);
+  a.rho_inv = T(1.0 / ctx->r_out);
+  a.pf = 1.0 / (4.0 * kPi * ctx->n_tilde);
+  a.ion_coef = ctx->n_ion / (ctx->r_out * ctx->r_out * ctx->r_out - 1.0);
+  a.q_s = ctx->p.q_s;
+  a.r_out2 = ctx->r_out * ctx->r_out;
+  a.kscale = 4294967296.0 / (ctx->r_out * ctx->r_out - 1.0);
+  a.dt = T(ctx->p.dt);
+  a.r_out = T(ctx->r_out);
+  a.wall_rule = ctx->p.wall_rule;
+  a.self_image = ctx->p.self_image;
+  a.seed = ctx->p.seed;
+  double rl = 1.0;
+  for (int l = 0; l < kTabL; ++l) {
+    a.f[l] = T(ctx->f[l]);
+    a.rhol[l] = T(rl);
+    rl *= ctx->r_out;
+    a.cdrive[l] = ctx->canti[l] * 4.0 * kPi * ctx->n_tilde;
+  }
+  ks->field(a, ctx->wpb, s);
+  if (ev) cudaEventRecord(ev[5], s);
+  // the field kernel wrote fresh keys for the (now sorted) state in push mode
+  ctx->keys_valid = record;
+  return IMRP_OK;
+}
+
+int enqueue_any(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nullptr) {
+  return ctx->prec == 1 ? enqueue<float>(ctx, record, ev) : enqueue<double>(ctx, record, ev);
+}
+
+int launch_steps(imrp_ctx* ctx, int64_t nsteps) {
+  int rc = grow_history(ctx, ctx->host_step + nsteps + 1);
+  if (rc) return rc;
+  int64_t done = 0;
+  // keys must be valid before a captured pair (the pair assumes the push wrote them)
+  while (done < nsteps && (!ctx->keys_valid || (nsteps - done) < 2)) {
+    rc = enqueue_any(ctx, true);
+    if (rc) return rc;
+    CK(cudaGetLastError());
+    ++done;
+  }
+  if (nsteps - done >= 2) {
+    if (!ctx->graph2 || ctx->graph_cur != ctx->cur) {
+      if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+      const int cur0 = ctx->cur;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      int r1 = enqueue_any(ctx, true);
+      int r2 = r1 ? r1 : enqueue_any(ctx, true);
+      cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
+      if (r2) { if (g) cudaGraphDestroy(g); return r2; }
+      if (ec != cudaSuccess) return ctx->fail(IMRP_E_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+      ec = cudaGraphInstantiate(&ctx->graph2, g, 0);
+      cudaGraphDestroy(g);
+      if (ec != cudaSuccess) return ctx->fail(IMRP_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+      ctx->cur = cur0;  // capture did not execute anything
+      ctx->graph_cur = cur0;
+    }
+    while (nsteps - done >= 2) {
+      CK(cudaGraphLaunch(ctx->graph2, ctx->stream));
+      done += 2;
+    }
+    if (done < nsteps) {
+      rc = enqueue_any(ctx, true);
+      if (rc) return rc;
+      ++done;
+    }
+  }
+  CK(cudaGetLastError());
+  ctx->host_step += nsteps;
+  return IMRP_OK;
+}
+
+int alloc_ctx(imrp_ctx* ctx) {
+  const int64_t N = ctx->p.N;
+  const size_t es = ctx->prec == 1 ? sizeof(float) : sizeof(double);
+  const int64_t ntiles = (N + 31) / 32;
+  const int64_t ngroups = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
+  const int nc = 2 * ncomp(ctx->L);
+  for (int b = 0; b < 2; ++b) {
+    for (int k = 0; k < 6; ++k) CK(cudaMalloc(&ctx->st_buf[b][k], N * es));
+    CK(cudaMalloc(&ctx->id_buf[b], N * sizeof(uint32_t)));
+  }
+  CK(cudaMalloc(&ctx->key0, N * sizeof(uint32_t)));
+  CK(cudaMalloc(&ctx->idx0, N * sizeof(uint32_t)));
+  CK(cudaMalloc(&ctx->key1, N * sizeof(uint32_t)));
+  CK(cudaMalloc(&ctx->idx1, N * sizeof(uint32_t)));
+  CK(cudaMalloc(&ctx->hist, (256 * sort_blocks(N) + 256) * sizeof(uint32_t)));
+  CK(cudaMalloc(&ctx->agg, ntiles * nc * es));
+  CK(cudaMalloc(&ctx->pfx, ntiles * nc * es));
+  CK(cudaMalloc(&ctx->gbase, ngroups * nc * es));
+  CK(cudaMalloc(&ctx->tot, nc * es));
+  CK(cudaMalloc(&ctx->gagg, ngroups * nc * sizeof(double)));
+  CK(cudaMalloc(&ctx->totd, nc * sizeof(double)));
+  CK(cudaMalloc(&ctx->eout, 3 * N * es));
+  CK(cudaMalloc(&ctx->stage, 6 * N * sizeof(double)));
+  CK(cudaMalloc(&ctx->st, sizeof(StepState)));
+  CK(cudaMalloc(&ctx->derr, sizeof(int)));
+  CK(cudaMemset(ctx->derr, 0, sizeof(int)));
+  return IMRP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void imrp_default_params(imrp_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->R_E_m = 4e-3;
+  p->R_D_m = 5e-3;
+  p->eps_D = 4.0;
+  p->n_e_m3 = 1e15;
+  p->T_e_eV = 2.0;
+  const double lam = sqrt(kEps0 * p->T_e_eV / (p->n_e_m3 * kE));
+  p->R_out_m = p->R_D_m + 20.0 * lam;
+  p->N = 20000;
+  p->l_max = 8;
+  p->m0_only = 0;
+  p->dt = 0.05;
+  p->drive_kind = 0;
+  p->wall_rule = 0;
+  p->V_volts = 1.0;
+  p->width_wpe = 2.0;
+  p->t0_wpe = 0.0;
+  p->self_image = 0;
+  p->precision = 0;
+  p->seed = 0;
+  p->q_s = 0.0;
+}
+
+int imrp_create(const imrp_params* p, imrp_ctx** out) {
+  if (!out) return IMRP_E_INVAL;
+  *out = nullptr;
+  if (!p) return IMRP_E_INVAL;
+  ensure_registry();
+  imrp_ctx* ctx = new (std::nothrow) imrp_ctx();
+  if (!ctx) return IMRP_E_NOMEM;
+  ctx->p = *p;
+  auto bad = [&](const char* m) {
+    delete ctx;
+    (void)m;
+    return IMRP_E_INVAL;
+  };
+  if (!(p->R_D_m > 0 && p->R_E_m > 0 && p->R_E_m < p->R_D_m)) return bad("geometry");
+  if (!(p->R_out_m > p->R_D_m)) return bad("outer wall");
+  if (!(p->eps_D >= 1.0) || !(p->n_e_m3 > 0) || !(p->dt > 0) || !(p->T_e_eV > 0)) return bad("plasma");
+  if (p->N < 1 || p->N > (int64_t(1) << 31)) return bad("N");
+  if (p->m0_only != 0) return bad("m0_only");
+  if (p->precision != 0 && p->precision != 1) return bad("precision");
+  if (p->drive_kind < 0 || p->drive_kind > 2 || p->wall_rule < 0 || p->wall_rule > 1) return bad("rules");
+  if (p->drive_kind == 0 && !(p->width_wpe > 0)) return bad("width");
+  ctx->L = p->l_max;
+  ctx->prec = p->precision;
+  const bool have = ctx->prec == 1 ? find_set<float>(ctx->L) != nullptr : find_set<double>(ctx->L) != nullptr;
+  if (!have) return bad("l_max not instantiated");
+  const double R = p->R_D_m;
+  ctx->d = 1.0 - p->R_E_m / R;
+  ctx->r_out = p->R_out_m / R;
+  ctx->v_hat = p->V_volts * kEps0 / (p->n_e_m3 * kE * R * R);
+  ctx->lambda_D = sqrt(kEps0 * p->T_e_eV / (p->n_e_m3 * kE)) / R;
+  ctx->omega_pe = sqrt(p->n_e_m3 * kE * kE / (kEps0 * kMe));
+  ctx->t0 = p->t0_wpe > 0 ? p->t0_wpe : 4.0 * p->width_wpe;
+  for (int l = 0; l < kTabL; ++l) {
+    ctx->f[l] = coef_f(l, ctx->d, p->eps_D);
+    ctx->canti[l] = (l % 2 == 1 && l <= ctx->L) ? coef_cprime((l + 1) / 2) * coef_bP(l, ctx->d, p->eps_D) : 0.0;
+    if (l > ctx->L) ctx->f[l] = 0.0;
+  }
+  ctx->nc = 2 * ncomp(ctx->L);
+  cudaGetDevice(&ctx->device);
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete ctx; return IMRP_E_CUDA; }
+  ctx->stream = ctx->own_stream;
+  int rc = ctx->prec == 1 ? find_set<float>(ctx->L)->init(ctx->device)
+                          : find_set<double>(ctx->L)->init(ctx->device);
+  if (rc != 0) { free_all(ctx); delete ctx; return IMRP_E_CUDA; }
+  const size_t spw = ctx->prec == 1 ? find_set<float>(ctx->L)->smem_per_warp
+                                    : find_set<double>(ctx->L)->smem_per_warp;
+  ctx->wpb = int(std::min<size_t>(8, (227 * 1024) / spw));
+  if (ctx->wpb < 1) { free_all(ctx); delete ctx; return IMRP_E_INVAL; }
+  rc = alloc_ctx(ctx);
+  if (rc) {
+    free_all(ctx);
+    delete ctx;
+    return rc == IMRP_E_CUDA ? IMRP_E_NOMEM : rc;
+  }
+  ctx->cap = p->N;
+  *out = ctx;
+  return IMRP_OK;
+}
+
+int imrp_destroy(imrp_ctx* ctx) {
+  if (!ctx) return IMRP_OK;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  delete ctx;
+  return IMRP_OK;
+}
+
+const char* imrp_last_error(const imrp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int imrp_set_stream(imrp_ctx* ctx, void* stream) {
+  if (!ctx) return IMRP_E_INVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->stream = stream ? static_cast<cudaStream_t>(stream) : ctx->own_stream;
+  return IMRP_OK;
+}
+
+int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t n) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (!x || !v || n < 1 || n > ctx->cap) return ctx->fail(IMRP_E_INVAL, "load: n = %lld out of range [1, %lld]", (long long)n, (long long)ctx->cap);
+  // interleave on the device: copy x and v into the [n][6] staging layout
+  CK(cudaMemcpy2DAsync(ctx->stage, 6 * sizeof(double), x, 3 * sizeof(double), 3 * sizeof(double), n,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpy2DAsync(ctx->stage + 3, 6 * sizeof(double), v, 3 * sizeof(double), 3 * sizeof(double), n,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  ctx->cur = 0;
+  if (ctx->prec == 1)
+    launch_load<float>(ctx->stage, state_ptrs<float>(ctx, 0), ctx->id_buf[0], n, ctx->r_out, ctx->derr, ctx->stream);
+  else
+    launch_load<double>(ctx->stage, state_ptrs<double>(ctx, 0), ctx->id_buf[0], n, ctx->r_out, ctx->derr, ctx->stream);
+  StepState s0{};
+  s0.step = 0;
+  s0.next = 0;
+  s0.u = 0;
+  s0.kick = 0;
+  s0.sync = 1;
+  CK(cudaMemcpyAsync(ctx->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->stream));
+  int rc = check_err(ctx);
+  if (rc) { ctx->loaded = false; return rc; }
+  ctx->n = n;
+  ctx->n_tilde = double(n) / (4.0 * kPi / 3.0 * (ctx->r_out * ctx->r_out * ctx->r_out - 1.0));
+  ctx->n_ion = double(n);
+  ctx->ntiles = (n + 31) / 32;
+  ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
+  ctx->host_step = 0;
+  ctx->loaded = true;
+  ctx->keys_valid = false;
+  if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+  return IMRP_OK;
+}
+
+int imrp_step_async(imrp_ctx* ctx, int64_t n_steps) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "step before load");
+  if (n_steps < 0) return ctx->fail(IMRP_E_INVAL, "n_steps < 0");
+  if (n_steps == 0) return IMRP_OK;
+  return launch_steps(ctx, n_steps);
+}
+
+int imrp_sync(imrp_ctx* ctx) {
+  if (!ctx) return IMRP_E_INVAL;
+  CK(cudaGetLastError());
+  return check_err(ctx);
+}
+
+int imrp_get_qdiff(imrp_ctx* ctx, int64_t first, int64_t count, double* qd, double* ua) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (first < 0 || count < 0 || first + count > ctx->host_step)
+    return ctx->fail(IMRP_E_INVAL, "get_qdiff: range [%lld, %lld) outside the %lld recorded steps",
+                     (long long)first, (long long)(first + count), (long long)ctx->host_step);
+  if (count == 0) return IMRP_OK;
+  if (qd) CK(cudaMemcpyAsync(qd, ctx->qhist + first, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (ua) CK(cudaMemcpyAsync(ua, ctx->uhist + first, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return check_err(ctx);
+}
+
+int imrp_step(imrp_ctx* ctx, int64_t n_steps, double* qdiff_out, double* uasy_out) {
+  int rc = imrp_step_async(ctx, n_steps);
+  if (rc) return rc;
+  const int64_t first = ctx->host_step - n_steps;
+  if ((qdiff_out || uasy_out) && n_steps > 0) return imrp_get_qdiff(ctx, first, n_steps, qdiff_out, uasy_out);
+  return imrp_sync(ctx);
+}
+
+int imrp_get_field(imrp_ctx* ctx, double* E) {
+  if (!ctx || !E) return IMRP_E_INVAL;
+  if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "get_field before load");
+  int rc = enqueue_any(ctx, false);
+  if (rc) return rc;
+  CK(cudaGetLastError());
+  const int64_t n = ctx->n;
+  if (ctx->prec == 1) {
+    const float* e = static_cast<const float*>(ctx->eout);
+    const float* cs[3] = {e, e + n, e + 2 * n};
+    launch_scatter_by_id<float>(cs, 3, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
+  } else {
+    const double* e = static_cast<const double*>(ctx->eout);
+    const double* cs[3] = {e, e + n, e + 2 * n};
+    launch_scatter_by_id<double>(cs, 3, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
+  }
+  CK(cudaMemcpyAsync(E, ctx->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return check_err(ctx);
+}
+
+int imrp_get_particles(imrp_ctx* ctx, double* x, double* v) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "get_particles before load");
+  const int64_t n = ctx->n;
+  if (ctx->prec == 1) {
+    float** s = state_ptrs<float>(ctx, ctx->cur);
+    const float* cs[6] = {s[0], s[1], s[2], s[3], s[4], s[5]};
+    launch_scatter_by_id<float>(cs, 6, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
+  } else {
+    double** s = state_ptrs<double>(ctx, ctx->cur);
+    const double* cs[6] = {s[0], s[1], s[2], s[3], s[4], s[5]};
+    launch_scatter_by_id<double>(cs, 6, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
+  }
+  if (x) CK(cudaMemcpy2DAsync(x, 3 * sizeof(double), ctx->stage, 6 * sizeof(double), 3 * sizeof(double), n,
+                              cudaMemcpyDeviceToHost, ctx->stream));
+  if (v) CK(cudaMemcpy2DAsync(v, 3 * sizeof(double), ctx->stage + 3, 6 * sizeof(double), 3 * sizeof(double), n,
+                              cudaMemcpyDeviceToHost, ctx->stream));
+  return check_err(ctx);
+}
+
+int imrp_profile_steps(imrp_ctx* ctx, int64_t n_steps, double* ms) {
+  if (!ctx || !ms || n_steps < 1) return IMRP_E_INVAL;
+  if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "profile before load");
+  int rc = grow_history(ctx, ctx->host_step + n_steps + 1);
+  if (rc) return rc;
+  for (int k = 0; k < IMRP_N_STAGES; ++k) ms[k] = 0.0;
+  std::vector<cudaEvent_t> ev(size_t(n_steps) * (IMRP_N_STAGES + 1));
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  int err = IMRP_OK;
+  for (int64_t s = 0; s < n_steps && !err; ++s) {
+    cudaEvent_t* e = ev.data() + s * (IMRP_N_STAGES + 1);
+    err = enqueue_any(ctx, true, e);
+  }
+  if (!err) {
+    ctx->host_step += n_steps;
+    cudaError_t ce = cudaStreamSynchronize(ctx->stream);
+    if (ce != cudaSuccess) err = ctx->fail(IMRP_E_CUDA, "profile: %s", cudaGetErrorString(ce));
+    for (int64_t s = 0; s < n_steps && !err; ++s) {
+      cudaEvent_t* e = ev.data() + s * (IMRP_N_STAGES + 1);
+      for (int k = 0; k < IMRP_N_STAGES; ++k) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e[k], e[k + 1]);
+        ms[k] += t;
+      }
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (err) return err;
+  return check_err(ctx);
+}
+
+int imrp_get_info(const imrp_ctx* ctx, imrp_info* info) {
+  if (!ctx || !info) return IMRP_E_INVAL;
+  info->d = ctx->d;
+  info->r_out = ctx->r_out;
+  info->n_tilde = ctx->n_tilde;
+  info->n_ion = ctx->n_ion;
+  info->v_hat = ctx->v_hat;
+  info->lambda_D = ctx->lambda_D;
+  info->omega_pe = ctx->omega_pe;
+  info->n = ctx->n;
+  info->step = ctx->host_step;
+  info->l_max = ctx->L;
+  info->precision = ctx->prec;
+  return IMRP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Spectrum post-processing on the host (peak, width, damped-sine fit).
+// ---------------------------------------------------------------------------
+namespace {
+
+void peak_fwhm(const std::vector<double>& w, const std::vector<double>& re, double* wr, double* dw) {
+  const size_t nf = re.size();
+  size_t j = 0;
+  for (size_t k = 1; k < nf; ++k) if (re[k] > re[j]) j = k;
+  double res = w[j];
+  if (j > 0 && j + 1 < nf) {
+    const double y0 = re[j - 1], y1 = re[j], y2 = re[j + 1];
+    const double den = y0 - 2 * y1 + y2;
+    if (den != 0) res = w[j] + 0.5 * (y0 - y2) / den * (w[1] - w[0]);
+  }
+  const double half = 0.5 * re[j];
+  size_t lo = j, hi = j;
+  while (lo > 0 && re[lo] > half) --lo;
+  while (hi + 1 < nf && re[hi] > half) ++hi;
+  auto cross = [&](size_t a, size_t b) {
+    if (re[a] == re[b]) return w[a];
+    return w[a] + (half - re[a]) * (w[b] - w[a]) / (re[b] - re[a]);
+  };
+  const double wl = re[lo] <= half ? cross(lo, lo + 1) : w[lo];
+  const double wh = re[hi] <= half ? cross(hi - 1, hi) : w[hi];
+  *wr = res;
+  *dw = wh - wl;
+}
+
+// Levenberg-Marquardt for y(tau) = a e^{-b tau} sin(c tau + phi).
+double fit_model(const std::vector<double>& tau, const std::vector<double>& y, double p[4]) {
+  auto resid = [&](const double* q, double* jac, double* r2) {
+    double s = 0;
+    double JtJ[16] = {0}, Jtr[4] = {0};
+    for (size_t i = 0; i < tau.size(); ++i) {
+      const double t = tau[i], e = exp(-q[1] * t), sn = sin(q[2] * t + q[3]), cs = cos(q[2] * t + q[3]);
+      const double f = q[0] * e * sn, r = y[i] - f;
+      const double g[4] = {e * sn, -t * q[0] * e * sn, t * q[0] * e * cs, q[0] * e * cs};
+      s += r * r;
+      if (jac) {
+        for (int a = 0; a < 4; ++a) {
+          Jtr[a] += g[a] * r;
+          for (int b = 0; b < 4; ++b) JtJ[4 * a + b] += g[a] * g[b];
+        }
+      }
+    }
+    if (jac) { memcpy(jac, JtJ, sizeof(JtJ)); memcpy(jac + 16, Jtr, sizeof(Jtr)); }
+    *r2 = s;
+  };
+  double lam = 1e-3, cur;
+  double buf[20];
+  resid(p, buf, &cur);
+  for (int it = 0; it < 200; ++it) {
+    double A[16], g[4];
+    memcpy(A, buf, sizeof(A));
+    memcpy(g, buf + 16, sizeof(g));
+    for (int a = 0; a < 4; ++a) A[5 * a] *= (1.0 + lam);
+    // solve A dp = g (4x4 Gaussian elimination with partial pivoting)
+    double M[4][5];
+    for (int a = 0; a < 4; ++a) { for (int b = 0; b < 4; ++b) M[a][b] = A[4 * a + b]; M[a][4] = g[a]; }
+    bool ok = true;
+    for (int c = 0; c < 4 && ok; ++c) {
+      int pv = c;
+      for (int r = c + 1; r < 4; ++r) if (fabs(M[r][c]) > fabs(M[pv][c])) pv = r;
+      if (M[pv][c] == 0) { ok = false; break; }
+      for (int k = 0; k < 5; ++k) std::swap(M[c][k], M[pv][k]);
+      for (int r = 0; r < 4; ++r) if (r != c) {
+        const double fct = M[r][c] / M[c][c];
+        for (int k = c; k < 5; ++k) M[r][k] -= fct * M[c][k];
+      }
+    }
+    if (!ok) break;
+    double q[4];
+    for (int a = 0; a < 4; ++a) q[a] = p[a] + M[a][4] / M[a][a];
+    double nb[20], nr;
+    resid(q, nb, &nr);
+    if (nr < cur) {
+      const double rel = (cur - nr) / (cur + 1e-300);
+      memcpy(p, q, sizeof(q));
+      memcpy(buf, nb, sizeof(nb));
+      cur = nr;
+      lam = std::max(lam * 0.3, 1e-12);
+      if (rel < 1e-14) break;
+    } else {
+      lam *= 10.0;
+      if (lam > 1e12) break;
+    }
+  }
+  return cur;
+}
+
+}  // namespace
+
+extern "C" int imrp_spectrum(imrp_ctx* ctx, int64_t n_freq, double w_max, double* omega, double* reY,
+                             double* imY, double* w_res, double* dw, double* fit) {
+  if (!ctx) return IMRP_E_INVAL;
+  const int64_t ns = ctx->host_step;
+  if (ns < 8) return ctx->fail(IMRP_E_STATE, "spectrum needs at least 8 recorded steps (have %lld)", (long long)ns);
+  if (n_freq < 3 || !(w_max > 0)) return ctx->fail(IMRP_E_INVAL, "spectrum: n_freq >= 3 and w_max > 0 required");
+  if (n_freq > ctx->dft_cap) {
+    cudaFree(ctx->dft);
+    ctx->dft = nullptr;
+    CK(cudaMalloc(&ctx->dft, 4 * n_freq * sizeof(double)));
+    ctx->dft_cap = n_freq;
+  }
+  const double dt = ctx->p.dt;
+  launch_dft(ctx->qhist, ctx->uhist, ns, dt, 0.5 * dt, n_freq, w_max, ctx->dft, ctx->stream);
+  CK(cudaGetLastError());
+  std::vector<double> h(4 * n_freq), q(ns);
+  CK(cudaMemcpyAsync(h.data(), ctx->dft, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(q.data(), ctx->qhist, ns * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<double> w(n_freq), re(n_freq), im(n_freq);
+  for (int64_t j = 0; j < n_freq; ++j) {
+    w[j] = double(j + 1) * (w_max / double(n_freq));
+    // Y = i w Q / U
+    const double Qr = h[4 * j], Qi = h[4 * j + 1], Ur = h[4 * j + 2], Ui = h[4 * j + 3];
+    const double den = Ur * Ur + Ui * Ui;
+    const double Rr = (Qr * Ur + Qi * Ui) / den, Ri = (Qi * Ur - Qr * Ui) / den;  // Q/U
+    re[j] = -w[j] * Ri;
+    im[j] = w[j] * Rr;
+  }
+  double wr = 0, width = 0;
+  peak_fwhm(w, re, &wr, &width);
+  if (omega) memcpy(omega, w.data(), n_freq * sizeof(double));
+  if (reY) memcpy(reY, re.data(), n_freq * sizeof(double));
+  if (imY) memcpy(imY, im.data(), n_freq * sizeof(double));
+  if (w_res) *w_res = wr;
+  if (dw) *dw = width;
+  if (fit) {
+    const double tfit = ctx->p.drive_kind == 0 ? ctx->t0 + 3.0 * ctx->p.width_wpe : 0.0;
+    std::vector<double> tau, y;
+    double amax = 0;
+    for (int64_t k = 0; k < ns; ++k) {
+      const double t = k * dt;
+      if (t >= tfit) {
+        tau.push_back(t - tfit);
+        y.push_back(q[k] - q[0]);
+        amax = std::max(amax, fabs(q[k] - q[0]));
+      }
+    }
+    double best[4] = {NAN, NAN, NAN, NAN}, bres = INFINITY;
+    if (tau.size() >= 8) {
+      const double phs[4] = {0.0, kPi / 2, kPi, -kPi / 2};
+      for (double ph : phs) {
+        double pp[4] = {amax > 0 ? amax : 1.0, std::max(0.5 * width, 1e-3), wr, ph};
+        const double r = fit_model(tau, y, pp);
+        if (r < bres && std::isfinite(r)) { bres = r; memcpy(best, pp, sizeof(pp)); }
+      }
+      if (best[0] < 0) { best[0] = -best[0]; best[3] += kPi; }
+    }
+    memcpy(fit, best, sizeof(best));
+  }
+  return IMRP_OK;
+}
+
+// ---- registry of the instantiation units ------------------------------------
+namespace imrp {
+void register_f32_small(std::vector<KernelSet<float>>&);
+void register_f32_mid(std::vector<KernelSet<float>>&);
+void register_f32_24(std::vector<KernelSet<float>>&);
+void register_f64_small(std::vector<KernelSet<double>>&);
+void register_f64_mid(std::vector<KernelSet<double>>&);
+void register_f64_24(std::vector<KernelSet<double>>&);
+void register_all(std::vector<KernelSet<float>>& f, std::vector<KernelSet<double>>& d) {
+  register_f32_small(f);
+  register_f32_mid(f);
+  register_f32_24(f);
+  register_f64_small(d);
+  register_f64_mid(d);
+  register_f64_24(d);
+}
+}  // namespace imrp

@@ -1,0 +1,423 @@
+// Degree-independent kernels of the IMRP hot path: the radius radix sort, state
+// reorder, key generation, loading, the FP64 scans of the tile moments, the
+// per-step finalize (drive u_asy and the Q_diff tally), and the spectrum sums.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "imrp_internal.h"
+
+namespace imrp {
+
+// ============================================================================
+// Radix sort: stable LSD, 4 passes of 8-bit digits. Each CTA owns
+// kSortTile = 2048 consecutive keys in a striped layout (item i of thread t is
+// key base + i*256 + t), which keeps the slot order (item, warp, lane) equal
+// to the key order, so the local ranks below are stable.
+// ============================================================================
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys,
+                                                           int64_t n, int shift, int64_t nblk,
+                                                           uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(blockIdx.x) * kSortTile;
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const int64_t idx = base + int64_t(i) * kSortThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[int64_t(threadIdx.x) * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of one digit's row hist[d][0..nblk) in place; the row total
+// goes to rowtot[d]. One CTA per digit.
+__global__ void __launch_bounds__(256) k_sort_rowscan(uint32_t* __restrict__ hist, int64_t nblk,
+                                                     uint32_t* __restrict__ rowtot) {
+  __shared__ uint32_t wsum[8];
+  uint32_t* row = hist + int64_t(blockIdx.x) * nblk;
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t carry = 0;
+  for (int64_t b0 = 0; b0 < nblk; b0 += 256) {
+    const int64_t i = b0 + threadIdx.x;
+    const uint32_t v = i < nblk ? row[i] : 0u;
+    uint32_t s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= unsigned(o)) s += t;
+    }
+    if (lane == 31) wsum[warp] = s;
+    __syncthreads();
+    uint32_t woff = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const uint32_t ws = wsum[w];
+      if (unsigned(w) < warp) woff += ws;
+      tot += ws;
+    }
+    if (i < nblk) row[i] = carry + woff + s - v;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rowtot[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, int64_t n, int shift, int64_t nblk,
+    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ rowtot) {
+  constexpr int kSlots = kSortItems * (kSortThreads / 32);
+  __shared__ uint16_t cnt[kSlots][256];
+  __shared__ uint32_t dbase[256];
+  __shared__ uint32_t wsum[8];
+  const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int s = 0; s < kSlots; ++s) cnt[s][t] = 0;
+  // exclusive scan of the digit totals -> global start of each digit
+  {
+    const uint32_t v = rowtot[t];
+    uint32_t s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= unsigned(o)) s += x;
+    }
+    if (lane == 31) wsum[warp] = s;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (unsigned w = 0; w < warp; ++w) woff += wsum[w];
+    dbase[t] = woff + s - v + hist[int64_t(t) * nblk + blockIdx.x];
+  }
+  __syncthreads();
+  const int64_t base = int64_t(blockIdx.x) * kSortTile;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t key[kSortItems], rank[kSortItems];
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const int64_t idx = base + int64_t(i) * kSortThreads + t;
+    const bool ok = idx < n;
+    key[i] = ok ? kin[idx] : 0u;
+    const unsigned d = ok ? ((key[i] >> shift) & 255u) : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    rank[i] = __popc(peers & lt);
+    if (ok && lane == unsigned(__ffs(peers) - 1)) cnt[i * 8 + warp][d] = uint16_t(__popc(peers));
+  }
+  __syncthreads();
+  {
+    uint32_t run = 0;
+    for (int s = 0; s < kSlots; ++s) {
+      const uint32_t c = cnt[s][t];
+      cnt[s][t] = uint16_t(run);
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const int64_t idx = base + int64_t(i) * kSortThreads + t;
+    if (idx < n) {
+      const unsigned d = (key[i] >> shift) & 255u;
+      const uint32_t pos = dbase[d] + cnt[i * 8 + warp][d] + rank[i];
+      kout[pos] = key[i];
+      vout[pos] = vin[idx];
+    }
+  }
+}
+
+void launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
+                       int64_t n, cudaStream_t s) {
+  if (n <= 1) return;
+  const int64_t nblk = sort_blocks(n);
+  uint32_t* rowtot = hist + 256 * nblk;
+  uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 8 * pass;
+    k_sort_hist<<<unsigned(nblk), kSortThreads, 0, s>>>(ki, n, shift, nblk, hist);
+    k_sort_rowscan<<<256, 256, 0, s>>>(hist, nblk, rowtot);
+    k_sort_scatter<<<unsigned(nblk), kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, nblk, hist,
+                                                           rowtot);
+    uint32_t* tk = ki; ki = ko; ko = tk;
+    uint32_t* tv = vi; vi = vo; vo = tv;
+  }
+}
+
+// ============================================================================
+// State movement
+// ============================================================================
+template <class T> struct Ptr7 { const T* s[6]; T* d[6]; };
+
+template <class T>
+__global__ void k_reorder(Ptr7<T> p, const uint32_t* __restrict__ id_src, uint32_t* __restrict__ id_dst,
+                          const uint32_t* __restrict__ perm, int64_t n) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint32_t q = perm[j];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) p.d[c][j] = p.s[c][q];
+  id_dst[j] = id_src[q];
+}
+
+template <class T>
+void launch_reorder(const T* const* src, T* const* dst, const uint32_t* id_src, uint32_t* id_dst,
+                    const uint32_t* perm, int64_t n, cudaStream_t s) {
+  Ptr7<T> p;
+  for (int c = 0; c < 6; ++c) { p.s[c] = src[c]; p.d[c] = dst[c]; }
+  k_reorder<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(p, id_src, id_dst, perm, n);
+}
+
+template <class T>
+__global__ void k_keys(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z,
+                       uint32_t* __restrict__ key, uint32_t* __restrict__ kidx, int64_t n,
+                       double kscale) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double xd = x[j], yd = y[j], zd = z[j];
+  double kf = (xd * xd + yd * yd + zd * zd - 1.0) * kscale;
+  kf = kf < 0.0 ? 0.0 : (kf > 4294967295.0 ? 4294967295.0 : kf);
+  key[j] = uint32_t(kf);
+  kidx[j] = uint32_t(j);
+}
+
+template <class T>
+void launch_keys(const T* x, const T* y, const T* z, uint32_t* key, uint32_t* kidx, int64_t n,
+                 double kscale, cudaStream_t s) {
+  k_keys<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, y, z, key, kidx, n, kscale);
+}
+
+template <class T> struct Ptr6 { T* d[6]; };
+
+// AoS FP64 [n][6] -> SoA T, ids = 0..n-1; flags positions outside 1 < r < r_out
+// or non-finite values.
+template <class T>
+__global__ void k_load(const double* __restrict__ xv, Ptr6<T> p, uint32_t* __restrict__ id, int64_t n,
+                       double r_out, int* err) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double v[6];
+  bool fin = true;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    v[c] = xv[6 * j + c];
+    fin = fin && isfinite(v[c]);
+  }
+  T t[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) t[c] = T(v[c]);
+  const double r2 = double(t[0]) * double(t[0]) + double(t[1]) * double(t[1]) + double(t[2]) * double(t[2]);
+  if (!fin) atomicOr(err, kErrNaN);
+  else if (!(r2 > 1.0 && r2 < r_out * r_out)) atomicOr(err, kErrRange);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) p.d[c][j] = t[c];
+  id[j] = uint32_t(j);
+}
+
+template <class T>
+void launch_load(const double* xv, T* const* dst, uint32_t* id, int64_t n, double r_out, int* err,
+                 cudaStream_t s) {
+  Ptr6<T> p;
+  for (int c = 0; c < 6; ++c) p.d[c] = dst[c];
+  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(xv, p, id, n, r_out, err);
+}
+
+template <class T>
+__global__ void k_scatter_by_id(Ptr6<const T> p, int nc, const uint32_t* __restrict__ id,
+                                double* __restrict__ out, int64_t n) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int64_t k = id[j];
+  for (int c = 0; c < nc; ++c) out[k * nc + c] = double(p.d[c][j]);
+}
+
+template <class T>
+void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, double* out,
+                          int64_t n, cudaStream_t s) {
+  Ptr6<const T> p;
+  for (int c = 0; c < 6; ++c) p.d[c] = c < ncomp ? comps[c] : nullptr;
+  k_scatter_by_id<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(p, ncomp, id, out, n);
+}
+
+// ============================================================================
+// Scans of the tile moments (FP64 accumulation)
+// ============================================================================
+// Grid (ngroups, ceil(nc/32)), 256 threads: lane = component, warp w owns tiles
+// 16w .. 16w+15 of the group. Writes the in-group prefix (Rs components
+// exclusive, Is components inclusive) and the group totals.
+template <class T>
+__global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T* __restrict__ pfx,
+                                                  double* __restrict__ gagg, int64_t ntiles, int nc) {
+  __shared__ double tot[8][32];
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.y * 32 + lane;
+  const bool okc = c < nc;
+  const int64_t t0 = int64_t(blockIdx.x) * kTilesPerGroup + warp * 16;
+  double run = 0.0;
+  for (int k = 0; k < 16; ++k) {
+    const int64_t t = t0 + k;
+    if (okc && t < ntiles) run += double(agg[t * nc + c]);
+  }
+  tot[warp][lane] = run;
+  __syncthreads();
+  double off = 0.0, all = 0.0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const double v = tot[w][lane];
+    if (unsigned(w) < warp) off += v;
+    all += v;
+  }
+  if (warp == 0 && okc) gagg[int64_t(blockIdx.x) * nc + c] = all;
+  const bool incl = (c & 1) != 0;
+  run = off;
+  for (int k = 0; k < 16; ++k) {
+    const int64_t t = t0 + k;
+    if (okc && t < ntiles) {
+      const double v = double(agg[t * nc + c]);
+      if (incl) run += v;
+      pfx[t * nc + c] = T(run);
+      if (!incl) run += v;
+    }
+  }
+}
+
+template <class T>
+void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s) {
+  const int64_t ng = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
+  dim3 grid(unsigned(ng), unsigned((nc + 31) / 32));
+  k_tile_scan<T><<<grid, 256, 0, s>>>(agg, pfx, gagg, ntiles, nc);
+}
+
+// Grid ceil(nc/32), 256 threads: warp w owns a contiguous segment of groups.
+// gbase: Rs components -> exclusive prefix over groups; Is components -> sum
+// over this group and all later ones. tot/totd: totals.
+template <class T>
+__global__ void __launch_bounds__(256) k_group_scan(const double* __restrict__ gagg, T* __restrict__ gbase,
+                                                   T* __restrict__ tot, double* __restrict__ totd,
+                                                   int64_t ngroups, int nc) {
+  __shared__ double ws[8][32];
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  const bool okc = c < nc;
+  const int64_t seg = (ngroups + 7) / 8;
+  const int64_t g0 = int64_t(warp) * seg;
+  const int64_t g1 = g0 + seg < ngroups ? g0 + seg : ngroups;
+  double run = 0.0;
+  for (int64_t g = g0; g < g1; ++g)
+    if (okc) run += gagg[g * nc + c];
+  ws[warp][lane] = run;
+  __syncthreads();
+  double off = 0.0, all = 0.0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const double v = ws[w][lane];
+    if (unsigned(w) < warp) off += v;
+    all += v;
+  }
+  const bool isI = (c & 1) != 0;
+  run = off;
+  for (int64_t g = g0; g < g1; ++g) {
+    if (!okc) break;
+    gbase[g * nc + c] = isI ? T(all - run) : T(run);
+    run += gagg[g * nc + c];
+  }
+  if (warp == 0 && okc) {
+    tot[c] = T(all);
+    totd[c] = all;
+  }
+}
+
+template <class T>
+void launch_group_scan(const double* gagg, T* gbase, T* tot, double* totd, int64_t ngroups, int nc,
+                       cudaStream_t s) {
+  k_group_scan<T><<<unsigned((nc + 31) / 32), 256, 0, s>>>(gagg, gbase, tot, totd, ngroups, nc);
+}
+
+// ============================================================================
+// Finalize: u_asy(t_n), the kick weight, and Q_diff(t_n) = -(1/n~) sum over odd
+// l of c_l' b^P_l * (sum_i q_i Is_l^0(x_i)) (Sec. 4; Is_l^0 = P_l(cos t)/r^{l+1}).
+// ============================================================================
+__global__ void k_finalize(FinalizeArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  StepState* st = a.st;
+  const int64_t n = st->next;
+  const double t = double(n) * a.dt;
+  double u = 0.0;
+  if (a.drive_kind == 0) {
+    const double z = (t - a.t0) / a.sigma;
+    u = a.v_hat * exp(-0.5 * z * z);
+  } else if (a.drive_kind == 1) {
+    u = n == 0 ? a.v_hat : 0.0;
+  }
+  st->step = n;
+  st->u = u;
+  st->kick = st->sync ? 0.5 * a.dt : a.dt;
+  if (a.record) {
+    double q = 0.0;
+    for (int l = 1; l <= a.L; l += 2) q += a.canti[l] * a.totd[2 * (l - 1) + 1];
+    q *= -a.inv_ntilde;
+    if (n < a.cap) {
+      a.qhist[n] = q;
+      a.uhist[n] = u;
+    }
+    st->next = n + 1;
+    st->sync = 0;
+  }
+}
+
+void launch_finalize(const FinalizeArgs& a, cudaStream_t s) { k_finalize<<<1, 32, 0, s>>>(a); }
+
+// ============================================================================
+// Spectrum sums (FP64). One thread per frequency; the phase factor advances
+// by a rotation and is recomputed exactly every 256 steps.
+// ============================================================================
+__global__ void k_dft(const double* __restrict__ q, const double* __restrict__ u, int64_t ns, double dt,
+                      double first_kick, int64_t nf, double w_max, double* __restrict__ out) {
+  const int64_t jf = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (jf >= nf) return;
+  const double w = double(jf + 1) * (w_max / double(nf));
+  double sr, cr;
+  sincos(w * dt, &sr, &cr);  // rotation by e^{-i w dt}
+  const double q0 = q[0];
+  double Qr = 0, Qi = 0, Ur = 0, Ui = 0, pr = 1.0, pi = 0.0;
+  for (int64_t k = 0; k < ns; ++k) {
+    if ((k & 255) == 0) {
+      double s, c;
+      sincos(w * dt * double(k), &s, &c);
+      pr = c;
+      pi = -s;
+    }
+    const double dq = q[k] - q0;
+    const double kw = k == 0 ? first_kick : dt;
+    const double uu = kw * u[k];
+    Qr += dq * pr; Qi += dq * pi;
+    Ur += uu * pr; Ui += uu * pi;
+    const double npr = pr * cr + pi * sr, npi = pi * cr - pr * sr;
+    pr = npr;
+    pi = npi;
+  }
+  out[4 * jf + 0] = dt * Qr;
+  out[4 * jf + 1] = dt * Qi;
+  out[4 * jf + 2] = Ur;
+  out[4 * jf + 3] = Ui;
+}
+
+void launch_dft(const double* q, const double* u, int64_t ns, double dt, double first_kick, int64_t nf,
+                double w_max, double* out, cudaStream_t s) {
+  k_dft<<<unsigned((nf + 127) / 128), 128, 0, s>>>(q, u, ns, dt, first_kick, nf, w_max, out);
+}
+
+// explicit instantiations
+#define IMRP_INST_CORE(T)                                                                          \
+  template void launch_reorder<T>(const T* const*, T* const*, const uint32_t*, uint32_t*,         \
+                                  const uint32_t*, int64_t, cudaStream_t);                         \
+  template void launch_keys<T>(const T*, const T*, const T*, uint32_t*, uint32_t*, int64_t, double, \
+                               cudaStream_t);                                                      \
+  template void launch_load<T>(const double*, T* const*, uint32_t*, int64_t, double, int*,         \
+                               cudaStream_t);                                                      \
+  template void launch_scatter_by_id<T>(const T* const*, int, const uint32_t*, double*, int64_t,   \
+                                        cudaStream_t);                                             \
+  template void launch_tile_scan<T>(const T*, T*, double*, int64_t, int, cudaStream_t);            \
+  template void launch_group_scan<T>(const double*, T*, T*, double*, int64_t, int, cudaStream_t);
+IMRP_INST_CORE(float)
+IMRP_INST_CORE(double)
+
+}  // namespace imrp

@@ -1,0 +1,168 @@
+// Device-side building blocks shared by the IMRP kernels (sm_103a).
+//
+// Notation: Rs_l^m(x) and Is_l^m(x) are complex solid harmonics, m >= 0, with
+// the symmetric scaling
+//   Rs_l^m = r^l sqrt((l-m)!/(l+m)!) P_l^m(cos t) e^{i m phi}
+//   Is_l^m = sqrt((l-m)!/(l+m)!) P_l^m(cos t) e^{i m phi} / r^{l+1}
+// (Condon-Shortley phase), so that |Rs| <= r^l, |Is| <= r^{-(l+1)} and the
+// addition theorem reads, for |y| < |x|,
+//   r_<^l / r_>^{l+1} P_l(cos g) = Rs_l^0(y) Is_l^0(x) + 2 sum_{m>0} Re(conj(Rs_l^m(y)) Is_l^m(x))
+// and P_l(cos g)/(|x||y|)^{l+1} is the same sum with Is(y) in place of Rs(y).
+// This is how the series of G~ (Sec. 3: sum_l sum_m R_l(r,r') Y*_lm Y_lm with
+// R^(p,p)_l) separates into prefix sums over inner and suffix sums over outer
+// particles once they are ordered by radius.
+//
+// Both families follow the Cartesian recurrences (a_lm = (2l-1)/sqrt((l+m)(l-m)),
+// b_lm = sqrt((l+m-1)(l-m-1)/((l+m)(l-m)))):
+//   Rs_m^m = -sqrt((2m-1)/(2m)) (x+iy) Rs_{m-1}^{m-1},   Rs_0^0 = 1
+//   Rs_l^m = a_lm z Rs_{l-1}^m - b_lm r^2 Rs_{l-2}^m
+//   Is_m^m = -sqrt((2m-1)/(2m)) (x+iy)/r^2 Is_{m-1}^{m-1}, Is_0^0 = 1/r
+//   Is_l^m = (a_lm z Is_{l-1}^m - b_lm Is_{l-2}^m) / r^2
+// Derivatives (the ladder identities of these functions):
+//   d_z Rs_l^m = sqrt((l+m)(l-m)) Rs_{l-1}^m
+//   (d_x + i d_y) Rs_l^m = sqrt((l-m)(l-m-1)) Rs_{l-1}^{m+1}
+//   (d_x - i d_y) Rs_l^m = -sqrt((l+m)(l+m-1)) Rs_{l-1}^{m-1}
+//   d_z Is_l^m = -sqrt((l+1+m)(l+1-m)) Is_{l+1}^m
+//   (d_x + i d_y) Is_l^m = sqrt((l+m+2)(l+m+1)) Is_{l+1}^{m+1}
+//   (d_x - i d_y) Is_l^m = -sqrt((l-m+2)(l-m+1)) Is_{l+1}^{m-1}
+// with X^{-m} = (-1)^m conj(X^m).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace imrp {
+
+constexpr int kTabL = 27;  // recurrence tables cover degrees 0..26
+
+// Number of packed real components of one moment set for degrees 1..L:
+// column m = 0 holds Re for l = 1..L; columns m >= 1 hold (Re, Im) for l = m..L.
+__host__ __device__ constexpr int ncomp(int L) { return L * (L + 2); }
+// Index of the first component of column m (degrees 1..L).
+__host__ __device__ constexpr int col_off(int L, int m) {
+  return m == 0 ? 0 : L + 2 * ((m - 1) * (L + 1) - (m - 1) * m / 2);
+}
+// Index of (l, m, part) in a set, part 0 = Re, 1 = Im (m >= 1 only).
+__host__ __device__ constexpr int comp_idx(int L, int l, int m, int part) {
+  return m == 0 ? (l - 1) : col_off(L, m) + 2 * (l - m) + part;
+}
+
+// Per-step scalars written by the finalize kernel and read by the field kernel.
+struct StepState {
+  int64_t step;     // absolute index of the step being taken (since the last load)
+  int64_t next;     // index of the next step to record
+  double u;         // u_asy(t_step)
+  double kick;      // kick weight of this step (dt, or dt/2 right after a load)
+  int32_t sync;     // 1: velocities synchronous with x (next kick is dt/2)
+  int32_t pad;
+};
+
+// Device error flags (bitwise or).
+enum : int { kErrNaN = 1, kErrTimeout = 2, kErrRange = 4 };
+
+template <class T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+
+// Recurrence tables in constant memory, one copy per translation unit.
+template <class T> struct Tables {
+  T a[kTabL * kTabL];
+  T b[kTabL * kTabL];
+  T dg[kTabL];
+};
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Transpose reduction of 32 registers over the warp: on return lane i holds
+// sum over all lanes of v[i]. 31 shuffles instead of 32 x 5.
+template <class T>
+__device__ __forceinline__ T warp_transpose_reduce(T (&v)[32]) {
+  const unsigned lane = lane_id();
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < off; ++k) {
+      T send = up ? v[k] : v[k + off];
+      T keep = up ? v[k + off] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0];
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011) and the branchless
+// orthonormal basis of Duff et al., JCGT 2017, used by the diffuse wall.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+constexpr int kTilesPerGroup = 128;  // tiles (of 32 particles) per scan group
+
+template <class T> struct MomArgs {
+  const T* x;
+  const T* y;
+  const T* z;
+  int64_t n;
+  T rho_inv;   // 1 / r_out: regular harmonics use x / r_out so |Rs| <= 1
+  T* agg;      // [ntiles][2 ncomp(L)], component u = 2 e + s, s = 0 Rs, s = 1 Is
+};
+
+// Entry tables of the gradient coefficients held in shared memory per warp.
+// I part: degrees 1..L+1 (gradient of the multipole expansion in Is);
+// R part: degrees 0..L-1 (gradient of the local expansion in Rs).
+__host__ __device__ constexpr int nI(int L) { return (L + 1) * (L + 4) / 2; }
+__host__ __device__ constexpr int nR(int L) { return L * (L + 1) / 2; }
+__host__ __device__ constexpr int offI(int L, int m) {
+  return m == 0 ? 0 : (L + 1) + (m - 1) * (L + 2) - (m - 1) * m / 2;
+}
+__host__ __device__ constexpr int offR(int L, int m) { return m * L - m * (m - 1) / 2; }
+__host__ __device__ constexpr int idxI(int L, int l, int m) { return offI(L, m) + l - (m > 1 ? m : 1); }
+__host__ __device__ constexpr int idxR(int L, int l, int m) { return offR(L, m) + l - m; }
+
+template <class T> struct FieldArgs {
+  T *x, *y, *z, *vx, *vy, *vz;
+  const uint32_t* id;
+  uint32_t* key;      // next radius key (push mode)
+  uint32_t* kidx;     // identity payload for the next sort (push mode)
+  int64_t n;
+  const T* pfx;       // [ntiles][NC] in-group prefix: Rs exclusive, Is inclusive
+  const T* gbase;     // [ngroups][NC] Rs: exclusive prefix of the group; Is: sum from the group on
+  const T* tot;       // [NC] totals (Is components used)
+  const StepState* st;
+  T* Eout;            // field mode: E in sorted order [3][n]
+  int* err;
+  int mode;           // 0 push, 1 field only
+  int L;              // degree (equals the template L)
+  T rho, rho_inv;     // r_out and 1 / r_out
+  double pf;          // 1 / (4 pi n~)
+  double ion_coef;    // n_ion / (r_out^3 - 1)
+  double q_s;         // surface charge
+  double r_out2;      // r_out^2
+  double kscale;      // 2^32 / (r_out^2 - 1)
+  T dt;
+  T r_out;
+  int wall_rule;
+  int self_image;
+  uint64_t seed;
+  T f[kTabL];         // f_l of App. A
+  T rhol[kTabL];      // r_out^l
+  double cdrive[kTabL];  // 4 pi n~ * c_l' b^P_l for odd l (drive in units of pf)
+};
+
+template <class T>
+__host__ __device__ constexpr size_t field_smem_per_warp(int L) {
+  return sizeof(typename Vec4<T>::type) * 2 * (nI(L) + nR(L)) + sizeof(T) * 2 * ncomp(L);
+}
+
+}  // namespace imrp

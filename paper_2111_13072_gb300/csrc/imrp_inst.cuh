@@ -1,0 +1,81 @@
+// Instantiation of the per-degree kernels for one precision and a list of
+// degrees. Each unit that includes this file owns its constant-memory
+// recurrence tables and fills them once per device.
+#pragma once
+
+#include <math.h>
+
+#include <mutex>
+
+#include "imrp_internal.h"
+#include "imrp_kernels.cuh"
+
+namespace imrp {
+namespace {
+
+template <class T> void fill_tables(Tables<T>& t) {
+  for (int l = 0; l < kTabL; ++l)
+    for (int m = 0; m < kTabL; ++m) {
+      double a = 0.0, b = 0.0;
+      if (m < l) {
+        const double den = double(l + m) * double(l - m);
+        a = (2.0 * l - 1.0) / sqrt(den);
+        b = sqrt(double(l + m - 1) * double(l - m - 1) / den);
+      }
+      t.a[l * kTabL + m] = T(a);
+      t.b[l * kTabL + m] = T(b);
+    }
+  for (int m = 0; m < kTabL; ++m) t.dg[m] = m == 0 ? T(1) : T(-sqrt((2.0 * m - 1.0) / (2.0 * m)));
+}
+
+template <class T, int L> void mom_launch(const MomArgs<T>& a, cudaStream_t s) {
+  const int64_t ntiles = (a.n + 31) / 32;
+  const int64_t blocks = (ntiles + 7) / 8;
+  if (blocks > 0) k_moments<T, L><<<unsigned(blocks), 256, 0, s>>>(a);
+}
+
+template <class T, int L> void field_launch(const FieldArgs<T>& a, int wpb, cudaStream_t s) {
+  const int64_t ntiles = (a.n + 31) / 32;
+  const int64_t blocks = (ntiles + wpb - 1) / wpb;
+  const size_t smem = size_t(wpb) * field_smem_per_warp<T>(L);
+  if (blocks > 0) k_field<T, L><<<unsigned(blocks), wpb * 32, smem, s>>>(a);
+}
+
+template <class T, int L> cudaError_t set_attr() {
+  return cudaFuncSetAttribute(k_field<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(8 * field_smem_per_warp<T>(L) > 227 * 1024 ? 227 * 1024
+                                                                             : 8 * field_smem_per_warp<T>(L)));
+}
+
+}  // namespace
+}  // namespace imrp
+
+// IMRP_UNIT(name, T, L...) defines register function `name` for the degrees L...
+#define IMRP_UNIT(NAME, T, ...)                                                              \
+  namespace imrp {                                                                           \
+  namespace {                                                                                \
+  template <int... Ls> int unit_init(int dev) {                                              \
+    static std::mutex mu;                                                                    \
+    static bool done[64] = {false};                                                          \
+    std::lock_guard<std::mutex> g(mu);                                                       \
+    if (dev < 0 || dev >= 64) return -1;                                                     \
+    if (done[dev]) return 0;                                                                 \
+    Tables<T> t;                                                                             \
+    fill_tables(t);                                                                          \
+    cudaError_t e = sizeof(T) == 4 ? cudaMemcpyToSymbol(c_tab_f, &t, sizeof(t))              \
+                                   : cudaMemcpyToSymbol(c_tab_d, &t, sizeof(t));             \
+    if (e != cudaSuccess) return int(e);                                                     \
+    cudaError_t es[] = {set_attr<T, Ls>()...};                                               \
+    for (cudaError_t x : es)                                                                 \
+      if (x != cudaSuccess) return int(x);                                                   \
+    done[dev] = true;                                                                        \
+    return 0;                                                                                \
+  }                                                                                          \
+  template <int... Ls> void unit_register(std::vector<KernelSet<T>>& v) {                   \
+    KernelSet<T> ks[] = {KernelSet<T>{Ls, &mom_launch<T, Ls>, &field_launch<T, Ls>,         \
+                                      &unit_init<Ls...>, field_smem_per_warp<T>(Ls)}...};   \
+    for (auto& k : ks) v.push_back(k);                                                       \
+  }                                                                                          \
+  }                                                                                          \
+  void NAME(std::vector<KernelSet<T>>& v) { unit_register<__VA_ARGS__>(v); }                 \
+  }

@@ -1,0 +1,77 @@
+// Internal interfaces between the host API (imrp_api.cu), the generic kernels
+// (imrp_core.cu) and the per-degree instantiation units (imrp_inst_*.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "imrp_device.cuh"
+
+namespace imrp {
+
+// ---- radix sort (imrp_core.cu) ---------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per CTA
+inline int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+// Sorts (key, val) pairs by key (stable LSD radix sort, 4 passes of 8 bits).
+// k0/v0 hold the input and receive the output; k1/v1 are scratch of n;
+// hist: 256 * sort_blocks(n) + 256 words.
+void launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
+                       int64_t n, cudaStream_t s);
+
+// ---- state movement and keys (imrp_core.cu) ---------------------------------
+template <class T>
+void launch_reorder(const T* const* src, T* const* dst, const uint32_t* id_src, uint32_t* id_dst,
+                    const uint32_t* perm, int64_t n, cudaStream_t s);
+template <class T>
+void launch_keys(const T* x, const T* y, const T* z, uint32_t* key, uint32_t* kidx, int64_t n,
+                 double kscale, cudaStream_t s);
+template <class T>
+void launch_load(const double* xv /* [n][6]: x y z vx vy vz */, T* const* dst, uint32_t* id,
+                 int64_t n, double r_out, int* err, cudaStream_t s);
+// out[id[j]][c] = comp_c[j] for c < 3 (and c < 6 with the velocity arrays)
+template <class T>
+void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, double* out,
+                          int64_t n, cudaStream_t s);
+
+// ---- scans (imrp_core.cu) ---------------------------------------------------
+template <class T>
+void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s);
+template <class T>
+void launch_group_scan(const double* gagg, T* gbase, T* tot, double* totd, int64_t ngroups,
+                       int nc, cudaStream_t s);
+
+struct FinalizeArgs {
+  StepState* st;
+  const double* totd;
+  double* qhist;
+  double* uhist;
+  int64_t cap;
+  int record;
+  int L;
+  int drive_kind;
+  double inv_ntilde;
+  double v_hat, sigma, t0, dt;
+  double canti[kTabL];
+};
+void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+
+// Spectrum sums: Qh[j] = dt sum_n (q_n - q_0) e^{-i w_j t_n},
+// Uh[j] = sum_n kw_n u_n e^{-i w_j t_n}, w_j = (j+1) w_max / nf; out [nf][4].
+void launch_dft(const double* q, const double* u, int64_t ns, double dt, double first_kick,
+                int64_t nf, double w_max, double* out, cudaStream_t s);
+
+// ---- per-degree kernels (imrp_inst_*.cu) ------------------------------------
+template <class T> struct KernelSet {
+  int L;
+  void (*moments)(const MomArgs<T>&, cudaStream_t);
+  void (*field)(const FieldArgs<T>&, int wpb, cudaStream_t);
+  int (*init)(int device);  // tables + attributes, once per device
+  size_t smem_per_warp;
+};
+void register_all(std::vector<KernelSet<float>>& f, std::vector<KernelSet<double>>& d);
+
+}  // namespace imrp

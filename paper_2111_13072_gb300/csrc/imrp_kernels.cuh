@@ -1,0 +1,441 @@
+// Per-degree kernel templates of the IMRP hot path: tile moments and the fused
+// field gather + leapfrog push + wall + next radius key. Included by the
+// instantiation units imrp_inst_*.cu, each of which owns its copy of the
+// recurrence tables in constant memory.
+#pragma once
+
+#include "imrp_device.cuh"
+
+namespace imrp {
+
+// Recurrence tables of this translation unit (filled by init_tables<T>()).
+static __constant__ Tables<float> c_tab_f;
+static __constant__ Tables<double> c_tab_d;
+template <class T> __device__ __forceinline__ const Tables<T>& tab();
+template <> __device__ __forceinline__ const Tables<float>& tab<float>() { return c_tab_f; }
+template <> __device__ __forceinline__ const Tables<double>& tab<double>() { return c_tab_d; }
+
+template <class T> __device__ __forceinline__ T rsqrt_t(T v);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double v) { return rsqrt(v); }
+
+// One warp per tile of 32 radius-sorted particles: q Rs_l^m(x/r_out) and
+// q Is_l^m(x), 1 <= l <= L, summed over the tile (q = -1 per electron).
+template <class T, int L>
+__global__ void __launch_bounds__(256) k_moments(MomArgs<T> a) {
+  constexpr int NC = 2 * ncomp(L);
+  const Tables<T>& tb = tab<T>();
+  const unsigned lane = lane_id();
+  const int64_t tile = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t ntiles = (a.n + 31) >> 5;
+  if (tile >= ntiles) return;  // warp-uniform
+  const int64_t j = tile * 32 + lane;
+  const bool valid = j < a.n;
+  const T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
+  const T q = valid ? T(-1) : T(0);
+  const T r2 = X * X + Y * Y + Z * Z;
+  const T ir2 = T(1) / r2;
+  const T ir = rsqrt_t(r2);
+  const T Xs = X * a.rho_inv, Ys = Y * a.rho_inv, Zs = Z * a.rho_inv;
+  const T rs2 = r2 * a.rho_inv * a.rho_inv;
+  const T Zir2 = Z * ir2;
+  T* out = a.agg + tile * NC;
+
+  T buf[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) buf[k] = T(0);
+
+  // The charge q is folded into the seeds Rs_0^0 = q, Is_0^0 = q / r.
+  T dRr = q, dRi = T(0), dIr = q * ir, dIi = T(0);
+#pragma unroll
+  for (int m = 0; m <= L; ++m) {
+    if (m > 0) {
+      const T c = tb.dg[m];
+      const T cx = c * Xs, cy = c * Ys;
+      const T nr = cx * dRr - cy * dRi, ni = cx * dRi + cy * dRr;
+      dRr = nr;
+      dRi = ni;
+      const T ex = c * X * ir2, ey = c * Y * ir2;
+      const T mr = ex * dIr - ey * dIi, mi = ex * dIi + ey * dIr;
+      dIr = mr;
+      dIi = mi;
+    }
+    T R1r = dRr, R1i = dRi, R0r = T(0), R0i = T(0);
+    T I1r = dIr, I1i = dIi, I0r = T(0), I0i = T(0);
+#pragma unroll
+    for (int l = m; l <= L; ++l) {
+      if (l > m) {
+        const T A = tb.a[l * kTabL + m], B = tb.b[l * kTabL + m];
+        const T az = A * Zs, br = B * rs2;
+        const T nr = az * R1r - br * R0r, ni = az * R1i - br * R0i;
+        R0r = R1r; R0i = R1i; R1r = nr; R1i = ni;
+        const T ai = A * Zir2, bi = B * ir2;
+        const T mr = ai * I1r - bi * I0r, mi = ai * I1i - bi * I0i;
+        I0r = I1r; I0i = I1i; I1r = mr; I1i = mi;
+      }
+      if (l >= 1) {
+#pragma unroll
+        for (int part = 0; part < (m > 0 ? 2 : 1); ++part) {
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const int u = 2 * comp_idx(L, l, m, part) + s;
+            buf[u & 31] = s == 0 ? (part == 0 ? R1r : R1i) : (part == 0 ? I1r : I1i);
+            if ((u & 31) == 31) {
+              const T sum = warp_transpose_reduce(buf);
+              out[(u & ~31) + lane] = sum;
+#pragma unroll
+              for (int k = 0; k < 32; ++k) buf[k] = T(0);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (NC & 31) {
+    const T sum = warp_transpose_reduce(buf);
+    if (lane < unsigned(NC & 31)) out[(NC & ~31) + lane] = sum;
+  }
+}
+
+// Decodes packed component e (0 <= e < ncomp(L)) into (l, m, part).
+__device__ __forceinline__ void decode_comp(int L, int e, int& l, int& m, int& part) {
+  if (e < L) { l = e + 1; m = 0; part = 0; return; }
+  int mm = 1;
+  while (mm < L && e >= col_off(L, mm + 1)) ++mm;
+  const int r = e - col_off(L, mm);
+  m = mm;
+  l = mm + (r >> 1);
+  part = r & 1;
+}
+
+// Fetch of a complex coefficient c_l^m (any sign of m) from the packed real
+// set (stride 2, offset s) with X^{-m} = (-1)^m conj(X^m); zero outside
+// 1 <= l <= L, |m| <= l.
+template <class T>
+__device__ __forceinline__ void fetch_c(const T* sc, int s, int L, int l, int m, T& re, T& im) {
+  const int am = m < 0 ? -m : m;
+  if (l < 1 || l > L || am > l) { re = T(0); im = T(0); return; }
+  re = sc[2 * comp_idx(L, l, am, 0) + s];
+  im = am > 0 ? sc[2 * comp_idx(L, l, am, 1) + s] : T(0);
+  if (m < 0) {
+    im = -im;
+    if (am & 1) { re = -re; im = -im; }
+  }
+}
+
+// One warp per tile. Phase 1 forms the tile's expansion coefficients, phase 2
+// their gradients (ladder identities) in shared memory, phase 3 evaluates the
+// far field of all other tiles, the near field of the pairs inside the tile,
+// the l = 0 terms, and then pushes the particle.
+template <class T, int L>
+__global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
+  using V4 = typename Vec4<T>::type;
+  constexpr int NC = 2 * ncomp(L);
+  constexpr int NI = nI(L), NR = nR(L);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Tables<T>& tb = tab<T>();
+  const unsigned lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int64_t tile = int64_t(blockIdx.x) * wpb + warp;
+  const int64_t ntiles = (a.n + 31) >> 5;
+  if (tile >= ntiles) return;  // warp-uniform; no block-wide barrier below
+  V4* coef = reinterpret_cast<V4*>(smem_raw) + size_t(warp) * 2 * (NI + NR);
+  T* sc = reinterpret_cast<T*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * 2 * (NI + NR)) +
+          size_t(warp) * NC;
+  const int64_t g = tile / kTilesPerGroup;
+  const double u_drive = a.st->u;
+  const T kick = T(a.st->kick);
+
+  // ---- phase 1: cI (coefficients of Is, s = 0) and cR (of Rs(x/r_out), s = 1)
+  {
+    const T* pt = a.pfx + tile * NC;
+    const T* gb = a.gbase + g * NC;
+    for (int e = lane; e < NC / 2; e += 32) {
+      int l, m, part;
+      decode_comp(L, e, l, m, part);
+      const T rl = a.rhol[l];  // r_out^l
+      const T A = gb[2 * e] + pt[2 * e];                 // sum_inner q Rs(x_i / r_out)
+      const T B = gb[2 * e + 1] - pt[2 * e + 1];         // sum_outer q Is(x_i)
+      const T W = a.tot[2 * e + 1];                      // sum_all q Is(x_i)
+      T cI = rl * A - a.f[l] * W;
+      if (m == 0 && (l & 1)) cI += T(u_drive * a.cdrive[l]);
+      sc[2 * e] = cI;
+      sc[2 * e + 1] = rl * B;
+    }
+  }
+  __syncwarp();
+  // ---- phase 2: gradient coefficients, scaled by -pf, x2 for m > 0
+  {
+    const T mpf = T(-a.pf);
+    for (int k = lane; k < NI + NR; k += 32) {
+      const bool isI = k < NI;
+      int Lp, M;
+      {
+        int kk = isI ? k : k - NI;
+        int mm = 0;
+        if (isI) {
+          while (mm < L + 1 && kk >= offI(L, mm + 1)) ++mm;
+          Lp = kk - offI(L, mm) + (mm > 1 ? mm : 1);
+        } else {
+          while (mm < L - 1 && kk >= offR(L, mm + 1)) ++mm;
+          Lp = kk - offR(L, mm) + mm;
+        }
+        M = mm;
+      }
+      T c1r, c1i, c2r, c2i, c0r, c0i, s1, s2, sz;
+      if (isI) {
+        fetch_c(sc, 0, L, Lp - 1, M - 1, c1r, c1i);
+        fetch_c(sc, 0, L, Lp - 1, M + 1, c2r, c2i);
+        fetch_c(sc, 0, L, Lp - 1, M, c0r, c0i);
+        s1 = sqrt(T((Lp + M) * (Lp + M - 1)));
+        s2 = -sqrt(T((Lp - M) * (Lp - M - 1)));
+        sz = -sqrt(T((Lp + M) * (Lp - M)));
+      } else {
+        fetch_c(sc, 1, L, Lp + 1, M - 1, c1r, c1i);
+        fetch_c(sc, 1, L, Lp + 1, M + 1, c2r, c2i);
+        fetch_c(sc, 1, L, Lp + 1, M, c0r, c0i);
+        s1 = sqrt(T((Lp - M + 2) * (Lp - M + 1)));
+        s2 = -sqrt(T((Lp + M + 2) * (Lp + M + 1)));
+        sz = sqrt(T((Lp + 1 + M) * (Lp + 1 - M)));
+      }
+      // dx = (s1 c1 + s2 c2)/2 ; dy = (i/2)(s1 c1 - s2 c2) ; dz = sz c0
+      const T dxr = T(0.5) * (s1 * c1r + s2 * c2r), dxi = T(0.5) * (s1 * c1i + s2 * c2i);
+      const T tr = s1 * c1r - s2 * c2r, ti = s1 * c1i - s2 * c2i;
+      const T dyr = T(-0.5) * ti, dyi = T(0.5) * tr;
+      const T dzr = sz * c0r, dzi = sz * c0i;
+      T w = (M > 0 ? T(2) : T(1)) * mpf;
+      if (!isI) w *= a.rho_inv;
+      V4 re, im;
+      re.x = w * dxr; re.y = w * dyr; re.z = w * dzr; re.w = T(0);
+      im.x = w * dxi; im.y = w * dyi; im.z = w * dzi; im.w = T(0);
+      coef[2 * k] = re;
+      coef[2 * k + 1] = im;
+    }
+  }
+  __syncwarp();
+
+  // ---- phase 3: the particle of this lane
+  const int64_t j = tile * 32 + lane;
+  const bool valid = j < a.n;
+  T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
+  const T r2 = X * X + Y * Y + Z * Z;
+  const T ir2 = T(1) / r2;
+  const T ir = rsqrt_t(r2);
+  T Ex = T(0), Ey = T(0), Ez = T(0);
+
+  // far field, multipole part: sum over Is_l^m(x), 1 <= l <= L+1
+  {
+    const T Zir2 = Z * ir2;
+    T dr = ir, di = T(0);
+#pragma unroll
+    for (int m = 0; m <= L + 1; ++m) {
+      if (m > 0) {
+        const T c = tb.dg[m];
+        const T ex = c * X * ir2, ey = c * Y * ir2;
+        const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
+        dr = nr;
+        di = ni;
+      }
+      T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+#pragma unroll
+      for (int l = m; l <= L + 1; ++l) {
+        if (l > m) {
+          const T A = tb.a[l * kTabL + m] * Zir2, B = tb.b[l * kTabL + m] * ir2;
+          const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
+          c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+        }
+        if (l >= 1) {
+          const V4 cr = coef[2 * idxI(L, l, m)];
+          Ex += cr.x * c1r; Ey += cr.y * c1r; Ez += cr.z * c1r;
+          if (m > 0) {
+            const V4 ci = coef[2 * idxI(L, l, m) + 1];
+            Ex += ci.x * c1i; Ey += ci.y * c1i; Ez += ci.z * c1i;
+          }
+        }
+      }
+    }
+  }
+  // far field, local part: sum over Rs_l^m(x / r_out), 0 <= l <= L-1
+  {
+    const T Xs = X * a.rho_inv, Ys = Y * a.rho_inv, Zs = Z * a.rho_inv;
+    const T rs2 = r2 * a.rho_inv * a.rho_inv;
+    T dr = T(1), di = T(0);
+#pragma unroll
+    for (int m = 0; m <= L - 1; ++m) {
+      if (m > 0) {
+        const T c = tb.dg[m];
+        const T ex = c * Xs, ey = c * Ys;
+        const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
+        dr = nr;
+        di = ni;
+      }
+      T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+#pragma unroll
+      for (int l = m; l <= L - 1; ++l) {
+        if (l > m) {
+          const T A = tb.a[l * kTabL + m] * Zs, B = tb.b[l * kTabL + m] * rs2;
+          const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
+          c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+        }
+        const V4 cr = coef[2 * (NI + idxR(L, l, m))];
+        Ex += cr.x * c1r; Ey += cr.y * c1r; Ez += cr.z * c1r;
+        if (m > 0) {
+          const V4 ci = coef[2 * (NI + idxR(L, l, m)) + 1];
+          Ex += ci.x * c1i; Ey += ci.y * c1i; Ez += ci.z * c1i;
+        }
+      }
+    }
+  }
+
+  // near field: direct pair terms (l >= 1) of the particles of this tile.
+  // Lower lane = smaller sorted radius = inner.
+  {
+    const T rk = r2 * ir;
+    const T ex = X * ir, ey = Y * ir, ez = Z * ir;
+    T Nx = T(0), Ny = T(0), Nz = T(0);  // sum of grad phi (phi = sum_l r_<^l/r_>^{l+1} P_l)
+    const T vmask = valid ? T(1) : T(0);
+#pragma unroll 1
+    for (int s = 1; s <= 16; ++s) {
+      const int src = (lane + s) & 31;
+      const T pex = __shfl_sync(0xffffffffu, ex, src);
+      const T pey = __shfl_sync(0xffffffffu, ey, src);
+      const T pez = __shfl_sync(0xffffffffu, ez, src);
+      const T prk = __shfl_sync(0xffffffffu, rk, src);
+      const T pm = __shfl_sync(0xffffffffu, vmask, src);
+      const bool me_inner = int(lane) < src;
+      const T ri = me_inner ? rk : prk, ro = me_inner ? prk : rk;
+      const T xix = me_inner ? ex : pex, xiy = me_inner ? ey : pey, xiz = me_inner ? ez : pez;
+      const T xox = me_inner ? pex : ex, xoy = me_inner ? pey : ey, xoz = me_inner ? pez : ez;
+      const T iro = T(1) / ro;
+      const T sr = ri * iro;
+      const T uu = xix * xox + xiy * xoy + xiz * xoz;
+      // Q_l = s^l P_l(u), D_l = s^l P'_l(u)
+      const T s2r = sr * sr, su = sr * uu;
+      T Qm = T(1), Q = su, Dm = T(0), D = sr;
+      T S0 = Q, S1 = Q, S2 = D;
+#pragma unroll
+      for (int l = 1; l < L; ++l) {
+        const T Qn = (T(2 * l + 1) * su * Q - T(l) * s2r * Qm) * T(1.0 / (l + 1));
+        const T Dn = s2r * Dm + T(2 * l + 1) * sr * Q;
+        Qm = Q; Q = Qn; Dm = D; D = Dn;
+        S0 += Q;
+        S1 += T(l + 1) * Q;
+        S2 += D;
+      }
+      const T iro2 = iro * iro;
+      const T gko = -(S0 + S1) * iro2, gka = S2 * iro2;      // grad at the outer point
+      const T gio = S1 / (ri * ro), gia = S2 / (ri * ro);    // grad at the inner point
+      // outer: gko x^_o + gka (x^_i - u x^_o); inner: gio x^_i + gia (x^_o - u x^_i)
+      const T ogx = gko * xox + gka * (xix - uu * xox), ogy = gko * xoy + gka * (xiy - uu * xoy),
+              ogz = gko * xoz + gka * (xiz - uu * xoz);
+      const T igx = gio * xix + gia * (xox - uu * xix), igy = gio * xiy + gia * (xoy - uu * xiy),
+              igz = gio * xiz + gia * (xoz - uu * xiz);
+      const T w = pm * vmask;
+      const T mx = w * (me_inner ? igx : ogx), my = w * (me_inner ? igy : ogy),
+              mz = w * (me_inner ? igz : ogz);
+      Nx += mx; Ny += my; Nz += mz;
+      if (s < 16) {
+        const T tx = w * (me_inner ? ogx : igx), ty = w * (me_inner ? ogy : igy),
+                tz = w * (me_inner ? ogz : igz);
+        const int dst = (lane - s) & 31;
+        Nx += __shfl_sync(0xffffffffu, tx, dst);
+        Ny += __shfl_sync(0xffffffffu, ty, dst);
+        Nz += __shfl_sync(0xffffffffu, tz, dst);
+      }
+    }
+    // E = -pf sum_i q_i grad phi = +pf grad phi (q_i = -1)
+    const T pfT = T(a.pf);
+    Ex += pfT * Nx; Ey += pfT * Ny; Ez += pfT * Nz;
+  }
+
+  // l = 0: electrons inside (sorted index j), ions inside, surface charge;
+  // then the self-image correction. The count difference is formed in FP64
+  // from the exact FP64 radius of the (FP32 or FP64) position.
+  double r2d = 0.0;
+  {
+    const double xd = double(X), yd = double(Y), zd = double(Z);
+    r2d = xd * xd + yd * yd + zd * zd;
+    const double rd = sqrt(r2d);
+    const double qin = a.ion_coef * (r2d * rd - 1.0) - double(j) + a.q_s;
+    const T er = T(a.pf * qin / (r2d * rd));  // multiplies x (gives r^ / r^2)
+    Ex += er * X; Ey += er * Y; Ez += er * Z;
+    if (!a.self_image) {
+      // remove the image of the particle itself: pf sum_l f_l (l+1) r^{-(2l+3)} r^
+      T h = T(0);
+#pragma unroll
+      for (int l = L; l >= 1; --l) h = h * ir2 + a.f[l] * T(l + 1);
+      const T es = -T(a.pf) * h * ir2 * ir2 * ir2;  // r^{-(2l+3)} r^ = ir2^{l-1} ir2^3 x
+      Ex += es * X; Ey += es * Y; Ez += es * Z;
+    }
+  }
+
+  if (a.mode == 1) {
+    if (valid) {
+      a.Eout[j] = Ex;
+      a.Eout[a.n + j] = Ey;
+      a.Eout[2 * a.n + j] = Ez;
+    }
+    return;
+  }
+  if (!valid) return;
+
+  // ---- leapfrog: v += kick (q/m) E with q/m = -1; x += dt v
+  T VX = a.vx[j] - kick * Ex, VY = a.vy[j] - kick * Ey, VZ = a.vz[j] - kick * Ez;
+  X += a.dt * VX; Y += a.dt * VY; Z += a.dt * VZ;
+
+  // ---- walls (Sec. 4): mirror the radius back, keep the speed
+  {
+    const double xd = double(X), yd = double(Y), zd = double(Z);
+    double rr = xd * xd + yd * yd + zd * zd;
+    if (rr < 1.0 || rr > a.r_out2) {
+      const double rd = sqrt(rr);
+      const bool inner = rr < 1.0;
+      double rn = inner ? 2.0 - rd : 2.0 * double(a.r_out) - rd;
+      rn = rn < 1.0 ? 1.0 : (rn > double(a.r_out) ? double(a.r_out) : rn);
+      const double e0 = xd / rd, e1 = yd / rd, e2 = zd / rd;
+      X = T(e0 * rn); Y = T(e1 * rn); Z = T(e2 * rn);
+      if (a.wall_rule == 1) {
+        const T vr = VX * T(e0) + VY * T(e1) + VZ * T(e2);
+        VX -= T(2) * vr * T(e0); VY -= T(2) * vr * T(e1); VZ -= T(2) * vr * T(e2);
+      } else {
+        const T sgn = inner ? T(1) : T(-1);
+        const T n0 = sgn * T(e0), n1 = sgn * T(e1), n2 = sgn * T(e2);
+        const T speed = sqrt(VX * VX + VY * VY + VZ * VZ);
+        const uint64_t stp = uint64_t(a.st->step);
+        const uint4 o = philox4x32_10(
+            make_uint4(uint32_t(stp), uint32_t(stp >> 32), a.id[j], 0x494D5250u),
+            make_uint2(uint32_t(a.seed), uint32_t(a.seed >> 32)));
+        const T u1 = T(o.x >> 8) * T(1.0 / 16777216.0);
+        const T u2 = T(o.y >> 8) * T(1.0 / 16777216.0);
+        const T ca = T(1) - u1;
+        const T sa = sqrt(T(1) - ca * ca);
+        T sp, cp;
+        if constexpr (sizeof(T) == 4) sincospif(T(2) * u2, &sp, &cp);
+        else sincospi(T(2) * u2, &sp, &cp);
+        const T sg = n2 >= T(0) ? T(1) : T(-1);
+        const T aa = T(-1) / (sg + n2);
+        const T bb = n0 * n1 * aa;
+        const T t10 = T(1) + sg * n0 * n0 * aa, t11 = sg * bb, t12 = -sg * n0;
+        const T t20 = bb, t21 = sg + n1 * n1 * aa, t22 = -n1;
+        VX = speed * (ca * n0 + sa * (cp * t10 + sp * t20));
+        VY = speed * (ca * n1 + sa * (cp * t11 + sp * t21));
+        VZ = speed * (ca * n2 + sa * (cp * t12 + sp * t22));
+      }
+      rr = double(X) * double(X) + double(Y) * double(Y) + double(Z) * double(Z);
+    }
+    if (!(isfinite(double(X)) && isfinite(double(Y)) && isfinite(double(Z)) &&
+          isfinite(double(VX)) && isfinite(double(VY)) && isfinite(double(VZ)))) {
+      atomicOr(a.err, kErrNaN);
+      rr = 1.0;
+    }
+    double kf = (rr - 1.0) * a.kscale;
+    kf = kf < 0.0 ? 0.0 : (kf > 4294967295.0 ? 4294967295.0 : kf);
+    a.key[j] = uint32_t(kf);
+    a.kidx[j] = uint32_t(j);
+  }
+  a.x[j] = X; a.y[j] = Y; a.z[j] = Z;
+  a.vx[j] = VX; a.vy[j] = VY; a.vz[j] = VZ;
+}
+
+}  // namespace imrp

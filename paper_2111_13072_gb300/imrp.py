@@ -1,0 +1,218 @@
+"""Thin ctypes binding of the C ABI in include/imrp.h (argument marshalling only).
+
+Every step of the hot path runs in the CUDA kernels of ``libimrp.so``; this
+module only converts numpy arrays to pointers and error codes to exceptions.
+It raises ImportError-like ``RuntimeError`` when the library is missing: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libimrp.so")
+
+# Entry points declared in include/imrp.h (checked by the tests).
+EXPORTS = [
+    "imrp_default_params", "imrp_create", "imrp_destroy", "imrp_last_error", "imrp_set_stream",
+    "imrp_load_particles", "imrp_step", "imrp_step_async", "imrp_sync", "imrp_get_qdiff",
+    "imrp_get_field", "imrp_get_particles", "imrp_spectrum", "imrp_get_info", "imrp_profile_steps",
+]
+STAGES = ["sort", "reorder", "moments", "scans", "field"]
+
+ERRORS = {-1: "IMRP_E_INVAL", -2: "IMRP_E_NOMEM", -3: "IMRP_E_CUDA", -4: "IMRP_E_TIMEOUT",
+          -5: "IMRP_E_NAN", -6: "IMRP_E_STATE"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("R_E_m", ctypes.c_double), ("R_D_m", ctypes.c_double), ("eps_D", ctypes.c_double),
+        ("R_out_m", ctypes.c_double), ("n_e_m3", ctypes.c_double), ("T_e_eV", ctypes.c_double),
+        ("N", ctypes.c_int64), ("l_max", ctypes.c_int32), ("m0_only", ctypes.c_int32),
+        ("dt", ctypes.c_double), ("drive_kind", ctypes.c_int32), ("wall_rule", ctypes.c_int32),
+        ("V_volts", ctypes.c_double), ("width_wpe", ctypes.c_double), ("t0_wpe", ctypes.c_double),
+        ("self_image", ctypes.c_int32), ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
+        ("q_s", ctypes.c_double),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_double), ("r_out", ctypes.c_double), ("n_tilde", ctypes.c_double),
+        ("n_ion", ctypes.c_double), ("v_hat", ctypes.c_double), ("lambda_D", ctypes.c_double),
+        ("omega_pe", ctypes.c_double), ("n", ctypes.c_int64), ("step", ctypes.c_int64),
+        ("l_max", ctypes.c_int32), ("precision", ctypes.c_int32),
+    ]
+
+
+class IMRPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libimrp.so and declares the signatures of every entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libimrp.so not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P, c_void_p = ctypes.POINTER, ctypes.c_void_p
+    pd = P(ctypes.c_double)
+    L.imrp_default_params.argtypes = [P(Params)]
+    L.imrp_default_params.restype = None
+    L.imrp_create.argtypes = [P(Params), P(c_void_p)]
+    L.imrp_destroy.argtypes = [c_void_p]
+    L.imrp_last_error.argtypes = [c_void_p]
+    L.imrp_last_error.restype = ctypes.c_char_p
+    L.imrp_set_stream.argtypes = [c_void_p, c_void_p]
+    L.imrp_load_particles.argtypes = [c_void_p, pd, pd, ctypes.c_int64]
+    L.imrp_step.argtypes = [c_void_p, ctypes.c_int64, pd, pd]
+    L.imrp_step_async.argtypes = [c_void_p, ctypes.c_int64]
+    L.imrp_sync.argtypes = [c_void_p]
+    L.imrp_get_qdiff.argtypes = [c_void_p, ctypes.c_int64, ctypes.c_int64, pd, pd]
+    L.imrp_get_field.argtypes = [c_void_p, pd]
+    L.imrp_get_particles.argtypes = [c_void_p, pd, pd]
+    L.imrp_spectrum.argtypes = [c_void_p, ctypes.c_int64, ctypes.c_double, pd, pd, pd, pd, pd, pd]
+    L.imrp_get_info.argtypes = [c_void_p, P(Info)]
+    L.imrp_profile_steps.argtypes = [c_void_p, ctypes.c_int64, pd]
+    for name in EXPORTS:
+        if name != "imrp_default_params" and name != "imrp_last_error":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def default_params() -> Params:
+    p = Params()
+    load_library().imrp_default_params(ctypes.byref(p))
+    return p
+
+
+def params_from_workload(w, **overrides) -> Params:
+    """Copies a paper_2111_13072_gb300.inputs.Workload into Params."""
+    p = default_params()
+    p.R_E_m, p.R_D_m, p.eps_D = w.R_E_m, w.R_D_m, w.eps_D
+    p.R_out_m, p.n_e_m3, p.T_e_eV = w.R_out_m, w.n_e_m3, w.T_e_eV
+    p.N, p.l_max, p.dt = w.N, w.l_max, w.dt
+    p.drive_kind, p.wall_rule, p.V_volts, p.width_wpe = w.drive_kind, w.wall_rule, w.V_volts, w.width_wpe
+    p.self_image, p.precision, p.seed, p.m0_only = w.self_image, w.precision, w.seed, w.m0_only
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Sim:
+    """One plasma instance on the current CUDA device."""
+
+    def __init__(self, params: Params):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self._lib.imrp_create(ctypes.byref(params), ctypes.byref(h))
+        if rc != 0:
+            raise IMRPError(rc, "imrp_create failed")
+        self._h = h
+        self.params = params
+
+    def _check(self, rc):
+        if rc != 0:
+            raise IMRPError(rc, self._lib.imrp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.imrp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream_ptr: int | None):
+        self._check(self._lib.imrp_set_stream(self._h, ctypes.c_void_p(stream_ptr or 0)))
+
+    def load(self, x, v):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        assert x.shape == v.shape and x.ndim == 2 and x.shape[1] == 3
+        self._check(self._lib.imrp_load_particles(self._h, _ptr(x), _ptr(v), x.shape[0]))
+
+    def load_ptr(self, x_ptr: int, v_ptr: int, n: int):
+        """Loads from host pointers (e.g. pinned torch tensors)."""
+        P = ctypes.POINTER(ctypes.c_double)
+        self._check(self._lib.imrp_load_particles(self._h, ctypes.cast(x_ptr, P), ctypes.cast(v_ptr, P), n))
+
+    def step(self, n: int, record: bool = True):
+        q = np.zeros(n) if record else None
+        u = np.zeros(n) if record else None
+        self._check(self._lib.imrp_step(self._h, n, _ptr(q), _ptr(u)))
+        return q, u
+
+    def step_ptr(self, n: int, q_ptr: int):
+        P = ctypes.POINTER(ctypes.c_double)
+        self._check(self._lib.imrp_step(self._h, n, ctypes.cast(q_ptr, P), None))
+
+    def step_async(self, n: int):
+        self._check(self._lib.imrp_step_async(self._h, n))
+
+    def sync(self):
+        self._check(self._lib.imrp_sync(self._h))
+
+    def qdiff(self, first=0, count=None):
+        info = self.info()
+        count = info.step - first if count is None else count
+        q, u = np.zeros(count), np.zeros(count)
+        self._check(self._lib.imrp_get_qdiff(self._h, first, count, _ptr(q), _ptr(u)))
+        return q, u
+
+    def field(self):
+        n = self.info().n
+        E = np.zeros((n, 3))
+        self._check(self._lib.imrp_get_field(self._h, _ptr(E)))
+        return E
+
+    def particles(self):
+        n = self.info().n
+        x, v = np.zeros((n, 3)), np.zeros((n, 3))
+        self._check(self._lib.imrp_get_particles(self._h, _ptr(x), _ptr(v)))
+        return x, v
+
+    def spectrum(self, n_freq: int = 1000, w_max: float = 2.0, fit: bool = True):
+        om, re, im = np.zeros(n_freq), np.zeros(n_freq), np.zeros(n_freq)
+        wr, dw = ctypes.c_double(), ctypes.c_double()
+        f = np.zeros(4)
+        self._check(self._lib.imrp_spectrum(self._h, n_freq, w_max, _ptr(om), _ptr(re), _ptr(im),
+                                            ctypes.pointer(wr), ctypes.pointer(dw),
+                                            _ptr(f) if fit else None))
+        return {"omega": om, "reY": re, "imY": im, "w_res": wr.value, "dw": dw.value,
+                "fit": f if fit else None}
+
+    def profile_steps(self, n: int) -> dict:
+        """Takes n real steps with per-stage CUDA events; returns summed ms per stage."""
+        ms = np.zeros(len(STAGES))
+        self._check(self._lib.imrp_profile_steps(self._h, n, _ptr(ms)))
+        return dict(zip(STAGES, ms.tolist()))
+
+    def info(self) -> Info:
+        i = Info()
+        self._check(self._lib.imrp_get_info(self._h, ctypes.byref(i)))
+        return i

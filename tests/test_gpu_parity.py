@@ -1,0 +1,158 @@
+"""GPU path (C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (stated by the method's precision contract): the field E at every
+particle matches to 1e-5 relative (||dE|| / ||E|| over all particles) on the
+FP64 path and to 1e-4 on the mixed path (FP32 state, harmonics and push with
+FP64 carries). The inputs are float32-representable, so both paths and the
+oracle start from identical states.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_13072_gb300.inputs import WORKLOADS, Workload, maxwellian_shell, workload_state
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def imrp():
+    import torch
+    assert torch.cuda.is_available(), "these tests need the GPU"
+    from paper_2111_13072_gb300 import build, imrp as m
+    build.build()
+    m.load_library()
+    return m
+
+
+def _pair(imrp, w: Workload, n, **over):
+    """GPU params and oracle params of workload w with n particles."""
+    p = imrp.params_from_workload(w, N=n, **{k: v for k, v in over.items() if k != "t0_wpe"})
+    op = oracle.from_physical(w.R_E_m, w.R_D_m, w.eps_D, w.R_out_m, w.n_e_m3, w.T_e_eV, n,
+                              p.l_max, p.dt, drive_kind=p.drive_kind, V_volts=p.V_volts,
+                              width_wpe=p.width_wpe, wall_rule=p.wall_rule,
+                              self_image=p.self_image, seed=p.seed)
+    return p, op
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+BASE = WORKLOADS["fp64_n2e4_l8"]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,L", [(1, 8), (2, 4), (31, 8), (33, 2), (1000, 1), (4103, 12),
+                                 (8269, 8), (3001, 16), (1500, 24)])
+def test_field_matches_oracle(imrp, prec, n, L):
+    x, v = workload_state(BASE, N=n)
+    p, op = _pair(imrp, BASE, n, precision=prec, l_max=L)
+    with imrp.Sim(p) as sim:
+        sim.load(x, v)
+        E = sim.field()
+    Eo = oracle.field_scan(op, x, u=oracle.drive(op, 0))
+    if n == 1:
+        # a lone electron feels only the ions, its image is excluded: compare directly
+        np.testing.assert_allclose(E, Eo, rtol=TOL[prec], atol=0)
+    else:
+        assert _rel(E, Eo) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("self_image,drive,V,qs", [(1, 1, 300.0, 0.0), (0, 1, 300.0, 0.0),
+                                                   (1, 2, 1.0, 0.0)])
+def test_field_terms(imrp, prec, self_image, drive, V, qs):
+    """Self image on/off and a strong impulse drive (u_asy Psi_anti term)."""
+    n = 2500
+    x, v = workload_state(BASE, N=n)
+    p, op = _pair(imrp, BASE, n, precision=prec, self_image=self_image, drive_kind=drive,
+                  V_volts=V)
+    with imrp.Sim(p) as sim:
+        sim.load(x, v)
+        E = sim.field()
+    Eo = oracle.field_scan(op, x, u=oracle.drive(op, 0))
+    assert _rel(E, Eo) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_steps_match_oracle(imrp, prec):
+    """Three leapfrog steps with diffuse walls: velocity changes, positions,
+    wall hits and Q_diff against the oracle's run."""
+    n = 3000
+    w = Workload("walls", N=n, l_max=8, T_e_eV=20.0, n_e_m3=1e15, drive_kind=1, V_volts=50.0)
+    x, v = workload_state(w, N=n)
+    p, op = _pair(imrp, w, n, precision=prec)
+    with imrp.Sim(p) as sim:
+        sim.load(x, v)
+        q, u = sim.step(3)
+        xg, vg = sim.particles()
+    xo, vo, qo, uo, hits = oracle.run(op, x, v, 3)
+    assert hits > 0
+    np.testing.assert_allclose(u, uo, rtol=1e-12, atol=0)
+    dv_g, dv_o = vg - v, vo - v
+    per = np.linalg.norm(dv_g - dv_o, axis=1) / (np.linalg.norm(dv_o, axis=1) + 1e-30)
+    bad = np.sum(per > 10 * TOL[prec])
+    assert bad <= (0 if prec == 0 else 2), f"{bad} particles differ"
+    good = per <= 10 * TOL[prec]
+    assert _rel(dv_g[good], dv_o[good]) < TOL[prec] * 10
+    assert _rel(xg[good], xo[good]) < TOL[prec]
+    np.testing.assert_allclose(q, qo, rtol=10 * TOL[prec], atol=10 * TOL[prec] * np.max(np.abs(qo)))
+
+
+def test_qdiff_and_drive_sequence(imrp):
+    """FP64 path: 40 steps of the Gaussian pulse stay on the oracle trajectory."""
+    n = 1200
+    x, v = workload_state(BASE, N=n)
+    p, op = _pair(imrp, BASE, n, precision=0, l_max=4)
+    with imrp.Sim(p) as sim:
+        sim.load(x, v)
+        q1, u1 = sim.step(17)   # odd: eager steps and graph pairs
+        q2, u2 = sim.step(23)
+        qa, ua = sim.qdiff()
+    xo, vo, qo, uo, _ = oracle.run(op, x, v, 40)
+    np.testing.assert_allclose(np.concatenate([u1, u2]), uo, rtol=1e-12)
+    np.testing.assert_allclose(qa, np.concatenate([q1, q2]), rtol=0, atol=0)
+    np.testing.assert_allclose(qa, qo, rtol=1e-6, atol=1e-9 * np.max(np.abs(qo)))
+
+
+def test_errors_are_reported(imrp):
+    p = imrp.params_from_workload(BASE, N=100)
+    with imrp.Sim(p) as sim:
+        with pytest.raises(imrp.IMRPError) as e:
+            sim.step(1)
+        assert e.value.code == -6
+        x, v = workload_state(BASE, N=100)
+        x[5] *= 0.5  # inside the probe
+        with pytest.raises(imrp.IMRPError) as e:
+            sim.load(x, v)
+        assert e.value.code == -1
+        with pytest.raises(imrp.IMRPError):
+            sim.load(np.zeros((200, 3)), np.zeros((200, 3)))
+    bad = imrp.params_from_workload(BASE, N=100, l_max=7)
+    with pytest.raises(imrp.IMRPError):
+        imrp.Sim(bad)
+
+
+def test_large_sampled_parity(imrp):
+    """The mixed-precision workload at full size (N = 2e6, l_max = 16): sampled
+    particles against the oracle's direct pair sum, and invariants after a step."""
+    w = WORKLOADS["mixed_n2e6_l16"]
+    x, v = workload_state(w)
+    p, op = _pair(imrp, w, w.N)
+    with imrp.Sim(p) as sim:
+        sim.load(x, v)
+        E = sim.field()
+        q, _ = sim.step(2)
+        xg, vg = sim.particles()
+    rng = np.random.default_rng(0)
+    # spread the samples over the radius order (inner, middle and outer tiles)
+    order = np.argsort(np.linalg.norm(x, axis=1))
+    sample = np.unique(np.concatenate([order[:3], order[-3:], rng.choice(w.N, 10, replace=False)]))
+    Eo = oracle.field_brute(op, x, u=oracle.drive(op, 0), sample=sample)
+    assert _rel(E[sample], Eo) < TOL[1]
+    r = np.linalg.norm(xg, axis=1)
+    assert np.all(r >= 1.0) and np.all(r <= op.r_out)
+    assert np.all(np.isfinite(vg)) and np.all(np.isfinite(q))
