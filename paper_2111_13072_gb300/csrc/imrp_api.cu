@@ -229,6 +229,7 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   a.pfx = static_cast<const T*>(ctx->pfx);
   a.gbase = static_cast<const T*>(ctx->gbase);
   a.tot = static_cast<const T*>(ctx->tot);
+  a.agg = static_cast<const T*>(ctx->agg);
   a.st = ctx->st;
   a.Eout = static_cast<T*>(ctx->eout);
   a.err = ctx->derr;

@@ -241,8 +241,11 @@ void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, 
 // Scans of the tile moments (FP64 accumulation)
 // ============================================================================
 // Grid (ngroups, ceil(nc/32)), 256 threads: lane = component, warp w owns tiles
-// 16w .. 16w+15 of the group. Writes the in-group prefix (Rs components
-// exclusive, Is components inclusive) and the group totals.
+// 16w .. 16w+15 of the group. Writes, relative to the group, the exclusive
+// prefix of the Rs components (tiles before t) and the exclusive suffix of the
+// Is components (tiles after t), each summed directly in its own direction so
+// that no partial sum is formed as a difference of larger sums; and the group
+// totals.
 template <class T>
 __global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T* __restrict__ pfx,
                                                   double* __restrict__ gagg, int64_t ntiles, int nc) {
@@ -258,23 +261,22 @@ __global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T*
   }
   tot[warp][lane] = run;
   __syncthreads();
+  const bool suffix = (c & 1) != 0;
   double off = 0.0, all = 0.0;
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
     const double v = tot[w][lane];
-    if (unsigned(w) < warp) off += v;
+    if (suffix ? unsigned(w) > warp : unsigned(w) < warp) off += v;
     all += v;
   }
   if (warp == 0 && okc) gagg[int64_t(blockIdx.x) * nc + c] = all;
-  const bool incl = (c & 1) != 0;
   run = off;
-  for (int k = 0; k < 16; ++k) {
-    const int64_t t = t0 + k;
+  for (int kk = 0; kk < 16; ++kk) {
+    const int64_t t = t0 + (suffix ? 15 - kk : kk);
     if (okc && t < ntiles) {
       const double v = double(agg[t * nc + c]);
-      if (incl) run += v;
       pfx[t * nc + c] = T(run);
-      if (!incl) run += v;
+      run += v;
     }
   }
 }
@@ -287,8 +289,8 @@ void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc
 }
 
 // Grid ceil(nc/32), 256 threads: warp w owns a contiguous segment of groups.
-// gbase: Rs components -> exclusive prefix over groups; Is components -> sum
-// over this group and all later ones. tot/totd: totals.
+// gbase: Rs components -> exclusive prefix over earlier groups; Is components
+// -> exclusive suffix over later groups (summed from the end). tot/totd: totals.
 template <class T>
 __global__ void __launch_bounds__(256) k_group_scan(const double* __restrict__ gagg, T* __restrict__ gbase,
                                                    T* __restrict__ tot, double* __restrict__ totd,
@@ -298,26 +300,28 @@ __global__ void __launch_bounds__(256) k_group_scan(const double* __restrict__ g
   const int c = blockIdx.x * 32 + lane;
   const bool okc = c < nc;
   const int64_t seg = (ngroups + 7) / 8;
-  const int64_t g0 = int64_t(warp) * seg;
+  const int64_t g0 = int64_t(warp) * seg < ngroups ? int64_t(warp) * seg : ngroups;
   const int64_t g1 = g0 + seg < ngroups ? g0 + seg : ngroups;
   double run = 0.0;
   for (int64_t g = g0; g < g1; ++g)
     if (okc) run += gagg[g * nc + c];
   ws[warp][lane] = run;
   __syncthreads();
+  const bool suffix = (c & 1) != 0;
   double off = 0.0, all = 0.0;
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
     const double v = ws[w][lane];
-    if (unsigned(w) < warp) off += v;
+    if (suffix ? unsigned(w) > warp : unsigned(w) < warp) off += v;
     all += v;
   }
-  const bool isI = (c & 1) != 0;
   run = off;
-  for (int64_t g = g0; g < g1; ++g) {
-    if (!okc) break;
-    gbase[g * nc + c] = isI ? T(all - run) : T(run);
-    run += gagg[g * nc + c];
+  if (okc) {
+    for (int64_t k = 0; k < g1 - g0; ++k) {
+      const int64_t g = suffix ? g1 - 1 - k : g0 + k;
+      gbase[g * nc + c] = T(run);
+      run += gagg[g * nc + c];
+    }
   }
   if (warp == 0 && okc) {
     tot[c] = T(all);

@@ -136,9 +136,10 @@ template <class T> struct FieldArgs {
   uint32_t* key;      // next radius key (push mode)
   uint32_t* kidx;     // identity payload for the next sort (push mode)
   int64_t n;
-  const T* pfx;       // [ntiles][NC] in-group prefix: Rs exclusive, Is inclusive
-  const T* gbase;     // [ngroups][NC] Rs: exclusive prefix of the group; Is: sum from the group on
+  const T* pfx;       // [ntiles][NC] in-group: Rs exclusive prefix, Is exclusive suffix
+  const T* gbase;     // [ngroups][NC] Rs: sum over earlier groups; Is: sum over later groups
   const T* tot;       // [NC] totals (Is components used)
+  const T* agg;       // [ntiles][NC] tile sums (own tile removed from the image moments)
   const StepState* st;
   T* Eout;            // field mode: E in sorted order [3][n]
   int* err;

@@ -151,13 +151,14 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   {
     const T* pt = a.pfx + tile * NC;
     const T* gb = a.gbase + g * NC;
+    const T* at = a.agg + tile * NC;
     for (int e = lane; e < NC / 2; e += 32) {
       int l, m, part;
       decode_comp(L, e, l, m, part);
       const T rl = a.rhol[l];  // r_out^l
-      const T A = gb[2 * e] + pt[2 * e];                 // sum_inner q Rs(x_i / r_out)
-      const T B = gb[2 * e + 1] - pt[2 * e + 1];         // sum_outer q Is(x_i)
-      const T W = a.tot[2 * e + 1];                      // sum_all q Is(x_i)
+      const T A = gb[2 * e] + pt[2 * e];                 // sum over inner tiles of q Rs(x_i / r_out)
+      const T B = gb[2 * e + 1] + pt[2 * e + 1];         // sum over outer tiles of q Is(x_i)
+      const T W = a.tot[2 * e + 1] - at[2 * e + 1];      // sum over the other tiles of q Is(x_i)
       T cI = rl * A - a.f[l] * W;
       if (m == 0 && (l & 1)) cI += T(u_drive * a.cdrive[l]);
       sc[2 * e] = cI;
@@ -288,7 +289,8 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     }
   }
 
-  // near field: direct pair terms (l >= 1) of the particles of this tile.
+  // near field: pair terms (l >= 1) of the particles of this tile, direct
+  // r_<^l / r_>^{l+1} P_l and image -f_l P_l / (r r')^{l+1}.
   // Lower lane = smaller sorted radius = inner.
   {
     const T rk = r2 * ir;
@@ -310,10 +312,16 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T iro = T(1) / ro;
       const T sr = ri * iro;
       const T uu = xix * xox + xiy * xoy + xiz * xoz;
-      // Q_l = s^l P_l(u), D_l = s^l P'_l(u)
+      // Q_l = s^l P_l(u), D_l = s^l P'_l(u); image weights f_l h^l, h = 1/r_i^2,
+      // so that f_l P_l/(r_i r_o)^{l+1} = t f_l h^l Q_l with t = 1/(r_i r_o)
       const T s2r = sr * sr, su = sr * uu;
+      const T iri = T(1) / ri;
+      const T hh = iri * iri;
       T Qm = T(1), Q = su, Dm = T(0), D = sr;
       T S0 = Q, S1 = Q, S2 = D;
+      T hp = hh;
+      T wq = a.f[1] * hp;
+      T T1 = T(2) * wq * Q, T2 = wq * D;
 #pragma unroll
       for (int l = 1; l < L; ++l) {
         const T Qn = (T(2 * l + 1) * su * Q - T(l) * s2r * Qm) * T(1.0 / (l + 1));
@@ -322,10 +330,18 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
         S0 += Q;
         S1 += T(l + 1) * Q;
         S2 += D;
+        hp *= hh;
+        wq = a.f[l + 1] * hp;
+        T1 += T(l + 2) * (wq * Q);
+        T2 += wq * D;
       }
+      const T tt = iri * iro;
+      T1 *= tt;
+      T2 *= tt;
       const T iro2 = iro * iro;
-      const T gko = -(S0 + S1) * iro2, gka = S2 * iro2;      // grad at the outer point
-      const T gio = S1 / (ri * ro), gia = S2 / (ri * ro);    // grad at the inner point
+      // grad of phi = sum_l [r_i^l/r_o^{l+1} - f_l/(r_i r_o)^{l+1}] P_l(u)
+      const T gko = -(S0 + S1) * iro2 + T1 * iro, gka = S2 * iro2 - T2 * iro;   // outer point
+      const T gio = (S1 * iro + T1) * iri, gia = (S2 * iro - T2) * iri;        // inner point
       // outer: gko x^_o + gka (x^_i - u x^_o); inner: gio x^_i + gia (x^_o - u x^_i)
       const T ogx = gko * xox + gka * (xix - uu * xox), ogy = gko * xoy + gka * (xiy - uu * xoy),
               ogz = gko * xoz + gka * (xiz - uu * xoz);
@@ -360,12 +376,12 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     const double qin = a.ion_coef * (r2d * rd - 1.0) - double(j) + a.q_s;
     const T er = T(a.pf * qin / (r2d * rd));  // multiplies x (gives r^ / r^2)
     Ex += er * X; Ey += er * Y; Ez += er * Z;
-    if (!a.self_image) {
-      // remove the image of the particle itself: pf sum_l f_l (l+1) r^{-(2l+3)} r^
+    if (a.self_image) {
+      // the particle's own image: pf sum_l f_l (l+1) r^{-(2l+3)} r^
       T h = T(0);
 #pragma unroll
       for (int l = L; l >= 1; --l) h = h * ir2 + a.f[l] * T(l + 1);
-      const T es = -T(a.pf) * h * ir2 * ir2 * ir2;  // r^{-(2l+3)} r^ = ir2^{l-1} ir2^3 x
+      const T es = T(a.pf) * h * ir2 * ir2 * ir2;  // r^{-(2l+3)} r^ = ir2^{l-1} ir2^3 x
       Ex += es * X; Ey += es * Y; Ez += es * Z;
     }
   }
