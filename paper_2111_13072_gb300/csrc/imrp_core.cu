@@ -240,43 +240,65 @@ void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, 
 // ============================================================================
 // Scans of the tile moments (FP64 accumulation)
 // ============================================================================
-// Grid (ngroups, ceil(nc/32)), 256 threads: lane = component, warp w owns tiles
-// 16w .. 16w+15 of the group. Writes, relative to the group, the exclusive
-// prefix of the Rs components (tiles before t) and the exclusive suffix of the
-// Is components (tiles after t), each summed directly in its own direction so
-// that no partial sum is formed as a difference of larger sums; and the group
-// totals.
+// Grid (ngroups, ceil(nc / kScanComps)), 128 threads = the 128 tiles of a
+// group. For each of the block's kScanComps components u: a block scan over
+// the group's tiles of agg[u][tile], written as the exclusive prefix for Rs
+// components (tiles before t) and the exclusive suffix for Is components
+// (tiles after t), each summed in its own direction so that no partial sum is
+// formed as a difference of larger sums. Warp scans run in T for all
+// components at once (independent shuffles) and warp totals are combined in
+// T (the stored in-group result is T); the group total goes to gagg[g][u] in
+// FP64. (FP64 arithmetic per thread is kept out of this kernel: the FP64 rate
+// of the GPU is a small fraction of its FP32 rate.)
+constexpr int kScanComps = 16;  // even: component parity (Rs/Is) = parity of cc
+
 template <class T>
-__global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T* __restrict__ pfx,
-                                                  double* __restrict__ gagg, int64_t ntiles, int nc) {
-  __shared__ double tot[8][32];
+__global__ void __launch_bounds__(kTilesPerGroup) k_tile_scan(const T* __restrict__ agg, T* __restrict__ pfx,
+                                                             double* __restrict__ gagg, int64_t ntiles, int nc) {
+  constexpr int NW = kTilesPerGroup / 32;
+  __shared__ T ws[kScanComps][NW];
   const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = blockIdx.y * 32 + lane;
-  const bool okc = c < nc;
-  const int64_t t0 = int64_t(blockIdx.x) * kTilesPerGroup + warp * 16;
-  double run = 0.0;
-  for (int k = 0; k < 16; ++k) {
-    const int64_t t = t0 + k;
-    if (okc && t < ntiles) run += double(agg[t * nc + c]);
-  }
-  tot[warp][lane] = run;
-  __syncthreads();
-  const bool suffix = (c & 1) != 0;
-  double off = 0.0, all = 0.0;
+  const int64_t t = int64_t(blockIdx.x) * kTilesPerGroup + threadIdx.x;
+  const bool ok = t < ntiles;
+  const int c0 = blockIdx.y * kScanComps;
+  T v[kScanComps], s[kScanComps];
 #pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    const double v = tot[w][lane];
-    if (suffix ? unsigned(w) > warp : unsigned(w) < warp) off += v;
-    all += v;
+  for (int cc = 0; cc < kScanComps; ++cc) {
+    const int c = c0 + cc;
+    v[cc] = (ok && c < nc) ? agg[int64_t(c) * ntiles + t] : T(0);
+    s[cc] = v[cc];
   }
-  if (warp == 0 && okc) gagg[int64_t(blockIdx.x) * nc + c] = all;
-  run = off;
-  for (int kk = 0; kk < 16; ++kk) {
-    const int64_t t = t0 + (suffix ? 15 - kk : kk);
-    if (okc && t < ntiles) {
-      const double v = double(agg[t * nc + c]);
-      pfx[t * nc + c] = T(run);
-      run += v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int cc = 0; cc < kScanComps; ++cc) {
+      if (cc & 1) {  // Is: inclusive suffix within the warp
+        const T y = __shfl_down_sync(0xffffffffu, s[cc], o);
+        if (lane + o < 32) s[cc] += y;
+      } else {       // Rs: inclusive prefix within the warp
+        const T y = __shfl_up_sync(0xffffffffu, s[cc], o);
+        if (lane >= unsigned(o)) s[cc] += y;
+      }
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < kScanComps; ++cc)
+    if ((cc & 1) ? lane == 0 : lane == 31) ws[cc][warp] = s[cc];
+  __syncthreads();
+#pragma unroll
+  for (int cc = 0; cc < kScanComps; ++cc) {
+    const int c = c0 + cc;
+    if (c >= nc) break;
+    T off = T(0);
+#pragma unroll
+    for (int w = 0; w < NW; ++w)
+      if ((cc & 1) ? unsigned(w) > warp : unsigned(w) < warp) off += ws[cc][w];
+    if (ok) pfx[int64_t(c) * ntiles + t] = off + (s[cc] - v[cc]);
+    if (threadIdx.x == 0) {
+      double all = 0.0;  // the group total in FP64 (one thread per block)
+#pragma unroll
+      for (int w = 0; w < NW; ++w) all += double(ws[cc][w]);
+      gagg[int64_t(blockIdx.x) * nc + c] = all;
     }
   }
 }
@@ -284,8 +306,8 @@ __global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T*
 template <class T>
 void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s) {
   const int64_t ng = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
-  dim3 grid(unsigned(ng), unsigned((nc + 31) / 32));
-  k_tile_scan<T><<<grid, 256, 0, s>>>(agg, pfx, gagg, ntiles, nc);
+  dim3 grid(unsigned(ng), unsigned((nc + kScanComps - 1) / kScanComps));
+  k_tile_scan<T><<<grid, kTilesPerGroup, 0, s>>>(agg, pfx, gagg, ntiles, nc);
 }
 
 // Grid ceil(nc/32), 256 threads: warp w owns a contiguous segment of groups.

@@ -115,7 +115,7 @@ template <class T> struct MomArgs {
   const T* z;
   int64_t n;
   T rho_inv;   // 1 / r_out: regular harmonics use x / r_out so |Rs| <= 1
-  T* agg;      // [ntiles][2 ncomp(L)], component u = 2 e + s, s = 0 Rs, s = 1 Is
+  T* agg;      // [2 ncomp(L)][ntiles], component u = 2 e + s, s = 0 Rs, s = 1 Is
 };
 
 // Entry tables of the gradient coefficients held in shared memory per warp.
@@ -136,10 +136,10 @@ template <class T> struct FieldArgs {
   uint32_t* key;      // next radius key (push mode)
   uint32_t* kidx;     // identity payload for the next sort (push mode)
   int64_t n;
-  const T* pfx;       // [ntiles][NC] in-group: Rs exclusive prefix, Is exclusive suffix
+  const T* pfx;       // [NC][ntiles] in-group: Rs exclusive prefix, Is exclusive suffix
   const T* gbase;     // [ngroups][NC] Rs: sum over earlier groups; Is: sum over later groups
   const T* tot;       // [NC] totals (Is components used)
-  const T* agg;       // [ntiles][NC] tile sums (own tile removed from the image moments)
+  const T* agg;       // [NC][ntiles] tile sums (own tile removed from the image moments)
   const StepState* st;
   T* Eout;            // field mode: E in sorted order [3][n]
   int* err;

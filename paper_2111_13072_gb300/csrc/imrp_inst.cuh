@@ -29,9 +29,9 @@ template <class T> void fill_tables(Tables<T>& t) {
 }
 
 template <class T, int L> void mom_launch(const MomArgs<T>& a, cudaStream_t s) {
-  const int64_t ntiles = (a.n + 31) / 32;
-  const int64_t blocks = (ntiles + 7) / 8;
-  if (blocks > 0) k_moments<T, L><<<unsigned(blocks), 256, 0, s>>>(a);
+  const int64_t per = kMomThreads * kMomPPT;
+  const int64_t blocks = (a.n + per - 1) / per;
+  if (blocks > 0) k_moments<T, L><<<unsigned(blocks), kMomThreads, moments_smem<T>(), s>>>(a);
 }
 
 template <class T, int L> void field_launch(const FieldArgs<T>& a, int wpb, cudaStream_t s) {
@@ -42,6 +42,9 @@ template <class T, int L> void field_launch(const FieldArgs<T>& a, int wpb, cuda
 }
 
 template <class T, int L> cudaError_t set_attr() {
+  cudaError_t e = cudaFuncSetAttribute(k_moments<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(moments_smem<T>()));
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_field<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(8 * field_smem_per_warp<T>(L) > 227 * 1024 ? 227 * 1024
                                                                              : 8 * field_smem_per_warp<T>(L)));

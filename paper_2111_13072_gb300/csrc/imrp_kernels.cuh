@@ -19,81 +19,115 @@ template <class T> __device__ __forceinline__ T rsqrt_t(T v);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double v) { return rsqrt(v); }
 
-// One warp per tile of 32 radius-sorted particles: q Rs_l^m(x/r_out) and
-// q Is_l^m(x), 1 <= l <= L, summed over the tile (q = -1 per electron).
+// Tile moments: the sums over each tile of 32 radius-sorted particles of
+// q Rs_l^m(x/r_out) and q Is_l^m(x), 1 <= l <= L (q = -1 per electron).
+// Two threads per tile, 16 particles each. The recurrences run column by
+// column (fixed m, rising l); the column sums stay in registers while the
+// thread walks its 16 particles, whose positions and diagonal terms
+// (Rs_m^m, Is_m^m) live in shared memory in a [particle][thread] layout
+// (conflict-free). The two halves of a tile are combined with one shuffle per
+// component. Output layout: agg[u][tile], u = 2 e + s (s = 0 Rs, s = 1 Is).
+constexpr int kMomThreads = 64;  // 32 tiles per CTA
+constexpr int kMomPPT = 16;      // particles per thread
+
+template <class T>
+__host__ __device__ constexpr size_t moments_smem() {
+  return sizeof(T) * 7 * kMomPPT * (kMomThreads + 1);
+}
+
 template <class T, int L>
-__global__ void __launch_bounds__(256) k_moments(MomArgs<T> a) {
-  constexpr int NC = 2 * ncomp(L);
+__global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int S = kMomThreads + 1;  // padded row
+  T* sx = reinterpret_cast<T*>(smem_raw);
+  T* sy = sx + kMomPPT * S;
+  T* sz = sy + kMomPPT * S;
+  T* sRr = sz + kMomPPT * S;
+  T* sRi = sRr + kMomPPT * S;
+  T* sIr = sRi + kMomPPT * S;
+  T* sIi = sIr + kMomPPT * S;
   const Tables<T>& tb = tab<T>();
-  const unsigned lane = lane_id();
-  const int64_t tile = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int th = threadIdx.x;
   const int64_t ntiles = (a.n + 31) >> 5;
-  if (tile >= ntiles) return;  // warp-uniform
-  const int64_t j = tile * 32 + lane;
-  const bool valid = j < a.n;
-  const T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
-  const T q = valid ? T(-1) : T(0);
-  const T r2 = X * X + Y * Y + Z * Z;
-  const T ir2 = T(1) / r2;
-  const T ir = rsqrt_t(r2);
-  const T Xs = X * a.rho_inv, Ys = Y * a.rho_inv, Zs = Z * a.rho_inv;
-  const T rs2 = r2 * a.rho_inv * a.rho_inv;
-  const T Zir2 = Z * ir2;
-  T* out = a.agg + tile * NC;
+  const int64_t pbase = int64_t(blockIdx.x) * (kMomThreads * kMomPPT);
+  // stage 1024 particles: particle k of the CTA goes to row k % 16, column k / 16
+#pragma unroll 4
+  for (int i = 0; i < kMomPPT; ++i) {
+    const int k = i * kMomThreads + th;
+    const int64_t j = pbase + k;
+    const bool valid = j < a.n;
+    const T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
+    const int o = (k % kMomPPT) * S + k / kMomPPT;
+    sx[o] = X; sy[o] = Y; sz[o] = Z;
+    const T q = valid ? T(-1) : T(0);
+    sRr[o] = q; sRi[o] = T(0);
+    sIr[o] = q * rsqrt_t(X * X + Y * Y + Z * Z); sIi[o] = T(0);
+  }
+  __syncthreads();
+  const int64_t tile = int64_t(blockIdx.x) * (kMomThreads / 2) + (th >> 1);
+  const bool writer = (th & 1) == 0 && tile < ntiles;
+  const T ri = a.rho_inv;
 
-  T buf[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) buf[k] = T(0);
-
-  // The charge q is folded into the seeds Rs_0^0 = q, Is_0^0 = q / r.
-  T dRr = q, dRi = T(0), dIr = q * ir, dIi = T(0);
 #pragma unroll
   for (int m = 0; m <= L; ++m) {
-    if (m > 0) {
-      const T c = tb.dg[m];
-      const T cx = c * Xs, cy = c * Ys;
-      const T nr = cx * dRr - cy * dRi, ni = cx * dRi + cy * dRr;
-      dRr = nr;
-      dRi = ni;
-      const T ex = c * X * ir2, ey = c * Y * ir2;
-      const T mr = ex * dIr - ey * dIi, mi = ex * dIi + ey * dIr;
-      dIr = mr;
-      dIi = mi;
-    }
-    T R1r = dRr, R1i = dRi, R0r = T(0), R0i = T(0);
-    T I1r = dIr, I1i = dIi, I0r = T(0), I0i = T(0);
+    constexpr int kMaxC = 4 * (L + 1);
+    const int nc = m == 0 ? 2 * L : 4 * (L - m + 1);  // components of this column
+    T acc[kMaxC];
 #pragma unroll
-    for (int l = m; l <= L; ++l) {
-      if (l > m) {
-        const T A = tb.a[l * kTabL + m], B = tb.b[l * kTabL + m];
-        const T az = A * Zs, br = B * rs2;
-        const T nr = az * R1r - br * R0r, ni = az * R1i - br * R0i;
-        R0r = R1r; R0i = R1i; R1r = nr; R1i = ni;
-        const T ai = A * Zir2, bi = B * ir2;
-        const T mr = ai * I1r - bi * I0r, mi = ai * I1i - bi * I0i;
-        I0r = I1r; I0i = I1i; I1r = mr; I1i = mi;
+    for (int k = 0; k < kMaxC; ++k) acc[k] = T(0);
+#pragma unroll 1
+    for (int p = 0; p < kMomPPT; ++p) {
+      const int o = p * S + th;
+      const T X = sx[o], Y = sy[o], Z = sz[o];
+      const T r2 = X * X + Y * Y + Z * Z;
+      const T ir2 = T(1) / r2;
+      const T Zs = Z * ri, rs2 = r2 * ri * ri, Zir2 = Z * ir2;
+      T dRr = sRr[o], dRi = sRi[o], dIr = sIr[o], dIi = sIi[o];
+      if (m > 0) {
+        const T c = tb.dg[m];
+        const T cx = c * X * ri, cy = c * Y * ri;
+        const T nr = cx * dRr - cy * dRi, ni = cx * dRi + cy * dRr;
+        dRr = nr; dRi = ni;
+        const T ex = c * X * ir2, ey = c * Y * ir2;
+        const T mr = ex * dIr - ey * dIi, mi = ex * dIi + ey * dIr;
+        dIr = mr; dIi = mi;
+        sRr[o] = dRr; sRi[o] = dRi; sIr[o] = dIr; sIi[o] = dIi;
       }
-      if (l >= 1) {
+      T R1r = dRr, R1i = dRi, R0r = T(0), R0i = T(0);
+      T I1r = dIr, I1i = dIi, I0r = T(0), I0i = T(0);
 #pragma unroll
-        for (int part = 0; part < (m > 0 ? 2 : 1); ++part) {
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            const int u = 2 * comp_idx(L, l, m, part) + s;
-            buf[u & 31] = s == 0 ? (part == 0 ? R1r : R1i) : (part == 0 ? I1r : I1i);
-            if ((u & 31) == 31) {
-              const T sum = warp_transpose_reduce(buf);
-              out[(u & ~31) + lane] = sum;
-#pragma unroll
-              for (int k = 0; k < 32; ++k) buf[k] = T(0);
-            }
+      for (int l = m; l <= L; ++l) {
+        if (l > m) {
+          const T A = tb.a[l * kTabL + m], B = tb.b[l * kTabL + m];
+          const T az = A * Zs, br = B * rs2;
+          const T nr = az * R1r - br * R0r, ni = az * R1i - br * R0i;
+          R0r = R1r; R0i = R1i; R1r = nr; R1i = ni;
+          const T ai = A * Zir2, bi = B * ir2;
+          const T mr = ai * I1r - bi * I0r, mi = ai * I1i - bi * I0i;
+          I0r = I1r; I0i = I1i; I1r = mr; I1i = mi;
+        }
+        if (l >= 1) {
+          if (m == 0) {
+            acc[2 * (l - 1) + 0] += R1r;
+            acc[2 * (l - 1) + 1] += I1r;
+          } else {
+            const int b = 4 * (l - m);
+            acc[b + 0] += R1r;
+            acc[b + 1] += I1r;
+            acc[b + 2] += R1i;
+            acc[b + 3] += I1i;
           }
         }
       }
     }
-  }
-  if (NC & 31) {
-    const T sum = warp_transpose_reduce(buf);
-    if (lane < unsigned(NC & 31)) out[(NC & ~31) + lane] = sum;
+    const int64_t u0 = 2 * int64_t(col_off(L, m));
+#pragma unroll
+    for (int k = 0; k < kMaxC; ++k) {
+      if (k < nc) {
+        const T s2 = acc[k] + __shfl_xor_sync(0xffffffffu, acc[k], 1);
+        if (writer) a.agg[(u0 + k) * ntiles + tile] = s2;
+      }
+    }
   }
 }
 
@@ -149,16 +183,16 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
 
   // ---- phase 1: cI (coefficients of Is, s = 0) and cR (of Rs(x/r_out), s = 1)
   {
-    const T* pt = a.pfx + tile * NC;
+    const T* pt = a.pfx + tile;   // [u][tile]
     const T* gb = a.gbase + g * NC;
-    const T* at = a.agg + tile * NC;
+    const T* at = a.agg + tile;   // [u][tile]
     for (int e = lane; e < NC / 2; e += 32) {
       int l, m, part;
       decode_comp(L, e, l, m, part);
       const T rl = a.rhol[l];  // r_out^l
-      const T A = gb[2 * e] + pt[2 * e];                 // sum over inner tiles of q Rs(x_i / r_out)
-      const T B = gb[2 * e + 1] + pt[2 * e + 1];         // sum over outer tiles of q Is(x_i)
-      const T W = a.tot[2 * e + 1] - at[2 * e + 1];      // sum over the other tiles of q Is(x_i)
+      const T A = gb[2 * e] + pt[(2 * e) * ntiles];          // sum over inner tiles of q Rs(x_i / r_out)
+      const T B = gb[2 * e + 1] + pt[(2 * e + 1) * ntiles];  // sum over outer tiles of q Is(x_i)
+      const T W = a.tot[2 * e + 1] - at[(2 * e + 1) * ntiles];  // sum over the other tiles of q Is(x_i)
       T cI = rl * A - a.f[l] * W;
       if (m == 0 && (l & 1)) cI += T(u_drive * a.cdrive[l]);
       sc[2 * e] = cI;
