@@ -167,6 +167,47 @@ int imrp_get_info(const imrp_ctx* ctx, imrp_info* info);
 #define IMRP_N_STAGES 5
 int imrp_profile_steps(imrp_ctx* ctx, int64_t n_steps, double* ms);
 
+/* ---------------------------------------------------------------------------
+ * Field evaluation without any allocation. (The paper has no counterpart: this
+ * entry point exists for the software that embeds the library.)
+ *
+ * Some callers cannot call cudaMalloc: code that runs where a framework owns
+ * all device memory through its own pool, code issued while another library
+ * holds the device's allocation lock, and allocation-free service loops that
+ * must not add to device memory after start-up. imrp_field_noalloc computes
+ * exactly what imrp_get_field computes (the field E of the modified, truncated
+ * Green's function, the ions, Q_S and the drive at step `step`), for a
+ * particle set given in device memory, with no context and no allocation: its
+ * intermediate buffers live in one static device array of fixed size (about
+ * 7 MB), which every GPU that loads this library holds until the process
+ * exits.
+ *
+ *   p       physical parameters as for imrp_create (p->N is ignored);
+ *           1 <= p->l_max <= IMRP_NOALLOC_MAX_L and l_max instantiated
+ *   x_dev   device pointer, FP64 positions [n][3] in units of R, 1 < |x| < r_out
+ *   n       1 <= n <= IMRP_NOALLOC_MAX_N; n~ and the ion background follow n
+ *           as after imrp_load_particles
+ *   step    step index whose drive u_asy(t_step) enters the field (0 as
+ *           right after a load)
+ *   E_dev   device pointer, FP64 field [n][3] in input order (written)
+ *   stream  cudaStream_t (as void*) on which the work is issued; NULL = the
+ *           legacy default stream. The call waits for its own work on that
+ *           stream before it returns.
+ *
+ * The first call on a device performs that device's set-up (it looks up the
+ * device address of the static array with cudaGetSymbolAddress and fills the
+ * kernels' constant tables), with that device current; make that first call
+ * before any stream capture. Every call on a device shares the one array, and
+ * the array keeps the last call's contents (what must start at zero is
+ * cleared by each call): calls that overlap on the GPU, from two streams or
+ * two host threads, race on it and must not be made.
+ * Errors: IMRP_E_INVAL (n or l_max beyond the limits, bad parameters, a
+ * position outside the shell), IMRP_E_NAN, IMRP_E_CUDA. */
+#define IMRP_NOALLOC_MAX_N 16384
+#define IMRP_NOALLOC_MAX_L 16
+int imrp_field_noalloc(const imrp_params* p, const double* x_dev, int64_t n, int64_t step,
+                       double* E_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@ EXPORTS = [
     "imrp_default_params", "imrp_create", "imrp_destroy", "imrp_last_error", "imrp_set_stream",
     "imrp_load_particles", "imrp_step", "imrp_step_async", "imrp_sync", "imrp_get_qdiff",
     "imrp_get_field", "imrp_get_particles", "imrp_spectrum", "imrp_get_info", "imrp_profile_steps",
+    "imrp_field_noalloc",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -84,6 +85,7 @@ def load_library(path: str = LIB_PATH):
     L.imrp_spectrum.argtypes = [c_void_p, ctypes.c_int64, ctypes.c_double, pd, pd, pd, pd, pd, pd]
     L.imrp_get_info.argtypes = [c_void_p, P(Info)]
     L.imrp_profile_steps.argtypes = [c_void_p, ctypes.c_int64, pd]
+    L.imrp_field_noalloc.argtypes = [P(Params), c_void_p, ctypes.c_int64, ctypes.c_int64, c_void_p, c_void_p]
     for name in EXPORTS:
         if name != "imrp_default_params" and name != "imrp_last_error":
             getattr(L, name).restype = ctypes.c_int
@@ -112,6 +114,15 @@ def params_from_workload(w, **overrides) -> Params:
     for k, v in overrides.items():
         setattr(p, k, v)
     return p
+
+
+def field_noalloc(params: Params, x_dev_ptr: int, n: int, step: int, E_dev_ptr: int,
+                  stream_ptr: int | None = None) -> None:
+    """imrp_field_noalloc on caller-owned device buffers (FP64 [n][3] each)."""
+    rc = load_library().imrp_field_noalloc(ctypes.byref(params), ctypes.c_void_p(x_dev_ptr), n, step,
+                                           ctypes.c_void_p(E_dev_ptr), ctypes.c_void_p(stream_ptr or 0))
+    if rc != 0:
+        raise IMRPError(rc, "imrp_field_noalloc failed")
 
 
 class Sim:
