@@ -63,6 +63,9 @@ enum : int { kErrNaN = 1, kErrTimeout = 2, kErrRange = 4 };
 template <class T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4; };
+template <class T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
 
 // Recurrence tables in constant memory, one copy per translation unit.
 template <class T> struct Tables {
@@ -161,9 +164,14 @@ template <class T> struct FieldArgs {
   double cdrive[kTabL];  // 4 pi n~ * c_l' b^P_l for odd l (drive in units of pf)
 };
 
+// Shared memory of one warp of the field kernel: per gradient entry six
+// values (d/dx, d/dy, d/dz of the Re and Im coefficient) split as
+// (re.x, re.y, re.z, im.x) + (im.y, im.z), then the 2 ncomp(L) expansion
+// coefficients of the tile.
 template <class T>
 __host__ __device__ constexpr size_t field_smem_per_warp(int L) {
-  return sizeof(typename Vec4<T>::type) * 2 * (nI(L) + nR(L)) + sizeof(T) * 2 * ncomp(L);
+  return (sizeof(typename Vec4<T>::type) + sizeof(typename Vec2<T>::type)) * (nI(L) + nR(L)) +
+         sizeof(T) * 2 * ncomp(L);
 }
 
 }  // namespace imrp

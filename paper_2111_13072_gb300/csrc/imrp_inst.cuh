@@ -28,6 +28,64 @@ template <class T> void fill_tables(Tables<T>& t) {
   for (int m = 0; m < kTabL; ++m) t.dg[m] = m == 0 ? T(1) : T(-sqrt((2.0 * m - 1.0) / (2.0 * m)));
 }
 
+// Host copies of the prologue tables, computed when the library is loaded
+// (fixed-size arrays: no allocation), uploaded once per device by unit_init.
+EntryRec h_ent[kEntTotal];
+uint16_t h_comp[kCompTotal];
+
+void fill_prologue_tables() {
+  for (int di = 0; di < kNumDegrees; ++di) {
+    const int L = degree_at(di);
+    const int eo = ent_off(L), co = comp_tab_off(L);
+    for (int m = 0; m <= L; ++m)
+      for (int l = (m > 1 ? m : 1); l <= L; ++l)
+        for (int part = 0; part < (m > 0 ? 2 : 1); ++part)
+          h_comp[co + comp_idx(L, l, m, part)] = uint16_t(l | ((m == 0 && (l & 1)) ? (1 << 8) : 0));
+    auto record = [&](bool isI, int Lp, int M) {
+      EntryRec r{};
+      const int s = isI ? 0 : 1;
+      const int lq = isI ? Lp - 1 : Lp + 1;
+      const int ms[3] = {M - 1, M + 1, M};
+      uint16_t flags = 0;
+      for (int q = 0; q < 3; ++q) {
+        const int mq = ms[q], am = mq < 0 ? -mq : mq;
+        if (lq < 1 || lq > L || am > lq) {
+          r.src[2 * q] = -1;
+          r.src[2 * q + 1] = -1;
+          continue;
+        }
+        r.src[2 * q] = int16_t(2 * comp_idx(L, lq, am, 0) + s);
+        r.src[2 * q + 1] = am > 0 ? int16_t(2 * comp_idx(L, lq, am, 1) + s) : int16_t(-1);
+        if (mq < 0) {  // X^{-m} = (-1)^m conj(X^m)
+          if (am & 1) flags |= uint16_t(1u << (2 * q));
+          else flags |= uint16_t(1u << (2 * q + 1));
+        }
+      }
+      if (isI) flags |= uint16_t(1u << 8);
+      if (M > 0) flags |= uint16_t(1u << 9);
+      r.flags = flags;
+      if (isI) {
+        r.s1 = float(sqrt(double((Lp + M) * (Lp + M - 1))));
+        r.s2 = float(-sqrt(double((Lp - M) * (Lp - M - 1))));
+        r.sz = float(-sqrt(double((Lp + M) * (Lp - M))));
+      } else {
+        r.s1 = float(sqrt(double((Lp - M + 2) * (Lp - M + 1))));
+        r.s2 = float(-sqrt(double((Lp + M + 2) * (Lp + M + 1))));
+        r.sz = float(sqrt(double((Lp + 1 + M) * (Lp + 1 - M))));
+      }
+      return r;
+    };
+    for (int M = 0; M <= L + 1; ++M)
+      for (int Lp = (M > 1 ? M : 1); Lp <= L + 1; ++Lp) h_ent[eo + idxI(L, Lp, M)] = record(true, Lp, M);
+    for (int M = 0; M <= L - 1; ++M)
+      for (int Lp = M; Lp <= L - 1; ++Lp) h_ent[eo + nI(L) + idxR(L, Lp, M)] = record(false, Lp, M);
+  }
+}
+struct PrologueInit {
+  PrologueInit() { fill_prologue_tables(); }
+};
+const PrologueInit g_prologue_init;
+
 template <class T, int L> void mom_launch(const MomArgs<T>& a, cudaStream_t s) {
   const int64_t per = kMomThreads * kMomPPT;
   const int64_t blocks = (a.n + per - 1) / per;
@@ -39,6 +97,14 @@ template <class T, int L> void field_launch(const FieldArgs<T>& a, int wpb, cuda
   const int64_t blocks = (ntiles + wpb - 1) / wpb;
   const size_t smem = size_t(wpb) * field_smem_per_warp<T>(L);
   if (blocks > 0) k_field<T, L><<<unsigned(blocks), wpb * 32, smem, s>>>(a);
+}
+
+template <class T, int L> int field_occ(int wpb) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_field<T, L>, wpb * 32,
+                                                    size_t(wpb) * field_smem_per_warp<T>(L)) != cudaSuccess)
+    return 0;
+  return nb;
 }
 
 template <class T, int L> cudaError_t set_attr() {
@@ -68,6 +134,10 @@ template <class T, int L> cudaError_t set_attr() {
     cudaError_t e = sizeof(T) == 4 ? cudaMemcpyToSymbol(c_tab_f, &t, sizeof(t))              \
                                    : cudaMemcpyToSymbol(c_tab_d, &t, sizeof(t));             \
     if (e != cudaSuccess) return int(e);                                                     \
+    e = cudaMemcpyToSymbol(g_ent, h_ent, sizeof(h_ent));                                     \
+    if (e != cudaSuccess) return int(e);                                                     \
+    e = cudaMemcpyToSymbol(g_comp, h_comp, sizeof(h_comp));                                  \
+    if (e != cudaSuccess) return int(e);                                                     \
     cudaError_t es[] = {set_attr<T, Ls>()...};                                               \
     for (cudaError_t x : es)                                                                 \
       if (x != cudaSuccess) return int(x);                                                   \
@@ -76,7 +146,8 @@ template <class T, int L> cudaError_t set_attr() {
   }                                                                                          \
   template <int... Ls> void unit_register(std::vector<KernelSet<T>>& v) {                   \
     KernelSet<T> ks[] = {KernelSet<T>{Ls, &mom_launch<T, Ls>, &field_launch<T, Ls>,         \
-                                      &unit_init<Ls...>, field_smem_per_warp<T>(Ls)}...};   \
+                                      &unit_init<Ls...>, field_smem_per_warp<T>(Ls),        \
+                                      &field_occ<T, Ls>}...};                               \
     for (auto& k : ks) v.push_back(k);                                                       \
   }                                                                                          \
   }                                                                                          \

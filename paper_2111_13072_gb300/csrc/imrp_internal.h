@@ -71,6 +71,7 @@ template <class T> struct KernelSet {
   void (*field)(const FieldArgs<T>&, int wpb, cudaStream_t);
   int (*init)(int device);  // tables + attributes, once per device
   size_t smem_per_warp;
+  int (*field_blocks_per_sm)(int wpb);  // occupancy of the field kernel at wpb warps per CTA
 };
 void register_all(std::vector<KernelSet<float>>& f, std::vector<KernelSet<double>>& d);
 

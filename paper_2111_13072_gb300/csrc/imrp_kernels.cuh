@@ -15,6 +15,43 @@ template <class T> __device__ __forceinline__ const Tables<T>& tab();
 template <> __device__ __forceinline__ const Tables<float>& tab<float>() { return c_tab_f; }
 template <> __device__ __forceinline__ const Tables<double>& tab<double>() { return c_tab_d; }
 
+// Per-degree prologue tables of the field kernel, in global memory of this
+// translation unit (filled by fill_prologue_tables at initialisation), for
+// every instantiated degree.
+// EntryRec: one gradient entry k of the shared-memory coefficient arrays.
+struct EntryRec {
+  int16_t src[6];   // scratch index of c1.re, c1.im, c2.re, c2.im, c0.re, c0.im (-1: zero)
+  uint16_t flags;   // bit q < 6: negate source q; bit 8: multipole (Is) part; bit 9: M > 0
+  uint16_t pad;
+  float s1, s2, sz, pad2;  // ladder factors
+};
+constexpr int kNumDegrees = 7;  // the instantiated degrees: 1, 2, 4, 8, 12, 16, 24
+__host__ __device__ constexpr int degree_at(int i) {
+  return i == 0 ? 1 : i == 1 ? 2 : i == 2 ? 4 : i == 3 ? 8 : i == 4 ? 12 : i == 5 ? 16 : 24;
+}
+__host__ __device__ constexpr int ent_off(int L) {
+  int o = 0;
+  for (int i = 0; i < kNumDegrees; ++i) {
+    const int d = degree_at(i);
+    if (d == L) return o;
+    o += nI(d) + nR(d);
+  }
+  return -1;
+}
+__host__ __device__ constexpr int comp_tab_off(int L) {
+  int o = 0;
+  for (int i = 0; i < kNumDegrees; ++i) {
+    const int d = degree_at(i);
+    if (d == L) return o;
+    o += ncomp(d);
+  }
+  return -1;
+}
+constexpr int kEntTotal = ent_off(24) + nI(24) + nR(24);
+constexpr int kCompTotal = comp_tab_off(24) + ncomp(24);
+static __device__ EntryRec g_ent[kEntTotal];
+static __device__ uint16_t g_comp[kCompTotal];  // per component: l | (drive << 8)
+
 template <class T> __device__ __forceinline__ T rsqrt_t(T v);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double v) { return rsqrt(v); }
@@ -131,14 +168,28 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
   }
 }
 
+// Column of a position in a column-major triangle: the largest m in [m_lo,
+// m_hi] with off(m) <= k, for an increasing offset function off. Starts from a
+// closed-form guess and corrects by at most a few steps.
+template <class Off>
+__device__ __forceinline__ int find_col(int k, int m_lo, int m_hi, float guess, Off off) {
+  int m = int(guess);
+  m = m < m_lo ? m_lo : (m > m_hi ? m_hi : m);
+  while (m < m_hi && off(m + 1) <= k) ++m;
+  while (m > m_lo && off(m) > k) --m;
+  return m;
+}
+
 // Decodes packed component e (0 <= e < ncomp(L)) into (l, m, part).
 __device__ __forceinline__ void decode_comp(int L, int e, int& l, int& m, int& part) {
   if (e < L) { l = e + 1; m = 0; part = 0; return; }
-  int mm = 1;
-  while (mm < L && e >= col_off(L, mm + 1)) ++mm;
-  const int r = e - col_off(L, mm);
-  m = mm;
-  l = mm + (r >> 1);
+  // col_off(m) = L + 2 (m-1)(L+1) - (m-1) m for m >= 1: solve for m
+  const float j = float(e - L);
+  const float bq = float(2 * L + 3);
+  const float g = 1.0f + 0.5f * (bq - sqrtf(fmaxf(bq * bq - 4.0f * j, 0.0f)));
+  m = find_col(e, 1, L, g, [L](int mm) { return col_off(L, mm); });
+  const int r = e - col_off(L, m);
+  l = m + (r >> 1);
   part = r & 1;
 }
 
@@ -164,8 +215,10 @@ __device__ __forceinline__ void fetch_c(const T* sc, int s, int L, int l, int m,
 template <class T, int L>
 __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   using V4 = typename Vec4<T>::type;
+  using V2 = typename Vec2<T>::type;
   constexpr int NC = 2 * ncomp(L);
   constexpr int NI = nI(L), NR = nR(L);
+  constexpr int NE = NI + NR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Tables<T>& tb = tab<T>();
   const unsigned lane = lane_id();
@@ -174,9 +227,10 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   const int64_t tile = int64_t(blockIdx.x) * wpb + warp;
   const int64_t ntiles = (a.n + 31) >> 5;
   if (tile >= ntiles) return;  // warp-uniform; no block-wide barrier below
-  V4* coef = reinterpret_cast<V4*>(smem_raw) + size_t(warp) * 2 * (NI + NR);
-  T* sc = reinterpret_cast<T*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * 2 * (NI + NR)) +
-          size_t(warp) * NC;
+  V4* coefA = reinterpret_cast<V4*>(smem_raw) + size_t(warp) * NE;
+  V2* coefB = reinterpret_cast<V2*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * NE) + size_t(warp) * NE;
+  T* sc = reinterpret_cast<T*>(reinterpret_cast<V2*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * NE) +
+                               size_t(wpb) * NE) + size_t(warp) * NC;
   const int64_t g = tile / kTilesPerGroup;
   const double u_drive = a.st->u;
   const T kick = T(a.st->kick);
@@ -186,15 +240,16 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     const T* pt = a.pfx + tile;   // [u][tile]
     const T* gb = a.gbase + g * NC;
     const T* at = a.agg + tile;   // [u][tile]
+    const uint16_t* ctab = g_comp + comp_tab_off(L);
     for (int e = lane; e < NC / 2; e += 32) {
-      int l, m, part;
-      decode_comp(L, e, l, m, part);
+      const uint16_t cr = ctab[e];
+      const int l = cr & 0xff;
       const T rl = a.rhol[l];  // r_out^l
       const T A = gb[2 * e] + pt[(2 * e) * ntiles];          // sum over inner tiles of q Rs(x_i / r_out)
       const T B = gb[2 * e + 1] + pt[(2 * e + 1) * ntiles];  // sum over outer tiles of q Is(x_i)
       const T W = a.tot[2 * e + 1] - at[(2 * e + 1) * ntiles];  // sum over the other tiles of q Is(x_i)
       T cI = rl * A - a.f[l] * W;
-      if (m == 0 && (l & 1)) cI += T(u_drive * a.cdrive[l]);
+      if (cr >> 8) cI += T(u_drive * a.cdrive[l]);
       sc[2 * e] = cI;
       sc[2 * e + 1] = rl * B;
     }
@@ -203,37 +258,20 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   // ---- phase 2: gradient coefficients, scaled by -pf, x2 for m > 0
   {
     const T mpf = T(-a.pf);
-    for (int k = lane; k < NI + NR; k += 32) {
-      const bool isI = k < NI;
-      int Lp, M;
-      {
-        int kk = isI ? k : k - NI;
-        int mm = 0;
-        if (isI) {
-          while (mm < L + 1 && kk >= offI(L, mm + 1)) ++mm;
-          Lp = kk - offI(L, mm) + (mm > 1 ? mm : 1);
-        } else {
-          while (mm < L - 1 && kk >= offR(L, mm + 1)) ++mm;
-          Lp = kk - offR(L, mm) + mm;
-        }
-        M = mm;
+    const EntryRec* etab = g_ent + ent_off(L);
+    for (int k = lane; k < NE; k += 32) {
+      const EntryRec er = etab[k];
+      T c[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const int si = er.src[q];
+        const T val = si >= 0 ? sc[si] : T(0);
+        c[q] = ((er.flags >> q) & 1) ? -val : val;
       }
-      T c1r, c1i, c2r, c2i, c0r, c0i, s1, s2, sz;
-      if (isI) {
-        fetch_c(sc, 0, L, Lp - 1, M - 1, c1r, c1i);
-        fetch_c(sc, 0, L, Lp - 1, M + 1, c2r, c2i);
-        fetch_c(sc, 0, L, Lp - 1, M, c0r, c0i);
-        s1 = sqrt(T((Lp + M) * (Lp + M - 1)));
-        s2 = -sqrt(T((Lp - M) * (Lp - M - 1)));
-        sz = -sqrt(T((Lp + M) * (Lp - M)));
-      } else {
-        fetch_c(sc, 1, L, Lp + 1, M - 1, c1r, c1i);
-        fetch_c(sc, 1, L, Lp + 1, M + 1, c2r, c2i);
-        fetch_c(sc, 1, L, Lp + 1, M, c0r, c0i);
-        s1 = sqrt(T((Lp - M + 2) * (Lp - M + 1)));
-        s2 = -sqrt(T((Lp + M + 2) * (Lp + M + 1)));
-        sz = sqrt(T((Lp + 1 + M) * (Lp + 1 - M)));
-      }
+      const T c1r = c[0], c1i = c[1], c2r = c[2], c2i = c[3], c0r = c[4], c0i = c[5];
+      const T s1 = T(er.s1), s2 = T(er.s2), sz = T(er.sz);
+      const bool isI = (er.flags >> 8) & 1;
+      const int M = (er.flags >> 9) & 1;
       // dx = (s1 c1 + s2 c2)/2 ; dy = (i/2)(s1 c1 - s2 c2) ; dz = sz c0
       const T dxr = T(0.5) * (s1 * c1r + s2 * c2r), dxi = T(0.5) * (s1 * c1i + s2 * c2i);
       const T tr = s1 * c1r - s2 * c2r, ti = s1 * c1i - s2 * c2i;
@@ -241,11 +279,12 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T dzr = sz * c0r, dzi = sz * c0i;
       T w = (M > 0 ? T(2) : T(1)) * mpf;
       if (!isI) w *= a.rho_inv;
-      V4 re, im;
-      re.x = w * dxr; re.y = w * dyr; re.z = w * dzr; re.w = T(0);
-      im.x = w * dxi; im.y = w * dyi; im.z = w * dzi; im.w = T(0);
-      coef[2 * k] = re;
-      coef[2 * k + 1] = im;
+      V4 ca;
+      V2 cb;
+      ca.x = w * dxr; ca.y = w * dyr; ca.z = w * dzr; ca.w = w * dxi;
+      cb.x = w * dyi; cb.y = w * dzi;
+      coefA[k] = ca;
+      coefB[k] = cb;
     }
   }
   __syncwarp();
@@ -258,6 +297,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   const T ir2 = T(1) / r2;
   const T ir = rsqrt_t(r2);
   T Ex = T(0), Ey = T(0), Ez = T(0);
+  T Fx = T(0), Fy = T(0), Fz = T(0);  // second accumulator chain (Im parts)
 
   // far field, multipole part: sum over Is_l^m(x), 1 <= l <= L+1
   {
@@ -281,11 +321,11 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
           c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
         }
         if (l >= 1) {
-          const V4 cr = coef[2 * idxI(L, l, m)];
-          Ex += cr.x * c1r; Ey += cr.y * c1r; Ez += cr.z * c1r;
+          const V4 ca = coefA[idxI(L, l, m)];
+          Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
           if (m > 0) {
-            const V4 ci = coef[2 * idxI(L, l, m) + 1];
-            Ex += ci.x * c1i; Ey += ci.y * c1i; Ez += ci.z * c1i;
+            const V2 cb = coefB[idxI(L, l, m)];
+            Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
           }
         }
       }
@@ -313,15 +353,17 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
           const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
           c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
         }
-        const V4 cr = coef[2 * (NI + idxR(L, l, m))];
-        Ex += cr.x * c1r; Ey += cr.y * c1r; Ez += cr.z * c1r;
+        const V4 ca = coefA[NI + idxR(L, l, m)];
+        Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
         if (m > 0) {
-          const V4 ci = coef[2 * (NI + idxR(L, l, m)) + 1];
-          Ex += ci.x * c1i; Ey += ci.y * c1i; Ez += ci.z * c1i;
+          const V2 cb = coefB[NI + idxR(L, l, m)];
+          Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
         }
       }
     }
   }
+
+  Ex += Fx; Ey += Fy; Ez += Fz;
 
   // near field: pair terms (l >= 1) of the particles of this tile, direct
   // r_<^l / r_>^{l+1} P_l and image -f_l P_l / (r r')^{l+1}.
@@ -338,18 +380,18 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T pey = __shfl_sync(0xffffffffu, ey, src);
       const T pez = __shfl_sync(0xffffffffu, ez, src);
       const T prk = __shfl_sync(0xffffffffu, rk, src);
+      const T pir = __shfl_sync(0xffffffffu, ir, src);
       const T pm = __shfl_sync(0xffffffffu, vmask, src);
       const bool me_inner = int(lane) < src;
       const T ri = me_inner ? rk : prk, ro = me_inner ? prk : rk;
+      const T iri = me_inner ? ir : pir, iro = me_inner ? pir : ir;
       const T xix = me_inner ? ex : pex, xiy = me_inner ? ey : pey, xiz = me_inner ? ez : pez;
       const T xox = me_inner ? pex : ex, xoy = me_inner ? pey : ey, xoz = me_inner ? pez : ez;
-      const T iro = T(1) / ro;
       const T sr = ri * iro;
       const T uu = xix * xox + xiy * xoy + xiz * xoz;
       // Q_l = s^l P_l(u), D_l = s^l P'_l(u); image weights f_l h^l, h = 1/r_i^2,
       // so that f_l P_l/(r_i r_o)^{l+1} = t f_l h^l Q_l with t = 1/(r_i r_o)
       const T s2r = sr * sr, su = sr * uu;
-      const T iri = T(1) / ri;
       const T hh = iri * iri;
       T Qm = T(1), Q = su, Dm = T(0), D = sr;
       T S0 = Q, S1 = Q, S2 = D;
@@ -402,13 +444,21 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   // l = 0: electrons inside (sorted index j), ions inside, surface charge;
   // then the self-image correction. The count difference is formed in FP64
   // from the exact FP64 radius of the (FP32 or FP64) position.
-  double r2d = 0.0;
   {
     const double xd = double(X), yd = double(Y), zd = double(Z);
-    r2d = xd * xd + yd * yd + zd * zd;
-    const double rd = sqrt(r2d);
-    const double qin = a.ion_coef * (r2d * rd - 1.0) - double(j) + a.q_s;
-    const T er = T(a.pf * qin / (r2d * rd));  // multiplies x (gives r^ / r^2)
+    const double r2d = xd * xd + yd * yd + zd * zd;  // exact for FP32 positions
+    double rd;
+    if constexpr (sizeof(T) == 4) {
+      // FP32 root refined by one Newton step in FP64 (no FP64 sqrt or division)
+      const float rf = r2 * ir;
+      rd = double(rf) + (r2d - double(rf) * double(rf)) * double(0.5f * ir);
+    } else {
+      rd = sqrt(r2d);
+    }
+    // inner charge in units of e: ions inside minus electrons inside (+ Q_S); the
+    // difference is small, so it is formed in FP64 and then scaled in T
+    const double qin = fma(a.ion_coef, r2d * rd - 1.0, a.q_s - double(j));
+    const T er = T(qin) * (T(a.pf) * ir2 * ir);  // multiplies x (gives r^ / r^2)
     Ex += er * X; Ey += er * Y; Ez += er * Z;
     if (a.self_image) {
       // the particle's own image: pf sum_l f_l (l+1) r^{-(2l+3)} r^
@@ -436,9 +486,17 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
 
   // ---- walls (Sec. 4): mirror the radius back, keep the speed
   {
-    const double xd = double(X), yd = double(Y), zd = double(Z);
-    double rr = xd * xd + yd * yd + zd * zd;
-    if (rr < 1.0 || rr > a.r_out2) {
+    double rr;
+    bool hit;
+    {
+      const T rt = X * X + Y * Y + Z * Z;
+      const bool near_wall = rt < T(1.0 + 1e-5) || rt > T(a.r_out2 * (1.0 - 1e-5));
+      const double xd = double(X), yd = double(Y), zd = double(Z);
+      rr = xd * xd + yd * yd + zd * zd;  // exact for FP32 positions; also the next key
+      hit = near_wall && (rr < 1.0 || rr > a.r_out2);
+    }
+    if (hit) {
+      const double xd = double(X), yd = double(Y), zd = double(Z);
       const double rd = sqrt(rr);
       const bool inner = rr < 1.0;
       double rn = inner ? 2.0 - rd : 2.0 * double(a.r_out) - rd;
@@ -474,8 +532,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       }
       rr = double(X) * double(X) + double(Y) * double(Y) + double(Z) * double(Z);
     }
-    if (!(isfinite(double(X)) && isfinite(double(Y)) && isfinite(double(Z)) &&
-          isfinite(double(VX)) && isfinite(double(VY)) && isfinite(double(VZ)))) {
+    if (!(isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(VX) && isfinite(VY) && isfinite(VZ))) {
       atomicOr(a.err, kErrNaN);
       rr = 1.0;
     }
