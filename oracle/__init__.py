@@ -333,6 +333,9 @@ def fit_damped_sine(qd, dt, t_fit, w0, b0, t_start=0.0):
     if best is None:
         return np.array([np.nan] * 4)
     a, b, c, ph = best[1]
+    # one curve, several parameter sets: report a >= 0, c >= 0, phi in [0, 2 pi)
+    if c < 0:
+        c, ph = -c, np.pi - ph
     if a < 0:
         a, ph = -a, ph + np.pi
-    return np.array([a, b, c, ph])
+    return np.array([a, b, c, np.mod(ph, 2 * np.pi)])

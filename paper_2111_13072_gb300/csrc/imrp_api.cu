@@ -764,7 +764,11 @@ extern "C" int imrp_spectrum(imrp_ctx* ctx, int64_t n_freq, double w_max, double
         const double r = fit_model(tau, y, pp);
         if (r < bres && std::isfinite(r)) { bres = r; memcpy(best, pp, sizeof(pp)); }
       }
+      // one curve, several parameter sets: report a >= 0, c >= 0, phi in [0, 2 pi)
+      if (best[2] < 0) { best[2] = -best[2]; best[3] = kPi - best[3]; }
       if (best[0] < 0) { best[0] = -best[0]; best[3] += kPi; }
+      best[3] = fmod(best[3], 2.0 * kPi);
+      if (best[3] < 0) best[3] += 2.0 * kPi;
     }
     memcpy(fit, best, sizeof(best));
   }

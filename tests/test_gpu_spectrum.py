@@ -1,0 +1,111 @@
+"""Spectrum (Sec. 4: admittance from the Fourier transform of Q_diff, damped-sine
+fit) of the GPU path against the FP64 oracle.
+
+1. The spectrum computation itself on the same recorded Q_diff and u_asy
+   series: the GPU's FP64 DFT and host fit against the oracle's.
+2. Whole runs from the same seeded state: trajectories are chaotic, so the
+   comparison is statistical -- resonance within 1 %, half-width within 5 %.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_13072_gb300.inputs import Workload, workload_state
+
+pytestmark = pytest.mark.gpu
+
+W = Workload("spectrum", N=4000, l_max=4, T_e_eV=1.0, n_e_m3=1e15, drive_kind=0, V_volts=20.0,
+             width_wpe=1.0)
+NSTEPS, NF, WMAX = 1600, 800, 1.2
+
+
+@pytest.fixture(scope="module")
+def imrp():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2111_13072_gb300 import build, imrp as m
+    build.build()
+    return m
+
+
+def _oracle_params():
+    return oracle.from_physical(W.R_E_m, W.R_D_m, W.eps_D, W.R_out_m, W.n_e_m3, W.T_e_eV, W.N,
+                                W.l_max, W.dt, drive_kind=W.drive_kind, V_volts=W.V_volts,
+                                width_wpe=W.width_wpe, seed=W.seed)
+
+
+@pytest.fixture(scope="module")
+def oracle_run():
+    x, v = workload_state(W)
+    op = _oracle_params()
+    _, _, q, u, _ = oracle.run(op, x, v, NSTEPS)
+    om, Y, wr, dw = oracle.spectrum(q, u, W.dt, NF, WMAX)
+    return {"q": q, "u": u, "omega": om, "Y": Y, "w_res": wr, "dw": dw,
+            "fit": oracle.fit_damped_sine(q, W.dt, op.t0 + 3 * op.sigma, wr, dw / 2)}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_spectrum_computation_matches_oracle(imrp, prec):
+    x, v = workload_state(W)
+    with imrp.Sim(imrp.params_from_workload(W, precision=prec)) as sim:
+        sim.load(x, v)
+        q, u = sim.step(NSTEPS)
+        sp = sim.spectrum(NF, WMAX)
+    op = _oracle_params()
+    om, Y, wr, dw = oracle.spectrum(q, u, W.dt, NF, WMAX)
+    np.testing.assert_allclose(sp["omega"], om, rtol=1e-14)
+    scale = np.max(np.abs(Y))
+    np.testing.assert_allclose(sp["reY"], Y.real, rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(sp["imY"], Y.imag, rtol=0, atol=1e-9 * scale)
+    assert sp["w_res"] == pytest.approx(wr, rel=1e-9)
+    assert sp["dw"] == pytest.approx(dw, rel=1e-9)
+    fo = oracle.fit_damped_sine(q, W.dt, op.t0 + 3 * op.sigma, wr, dw / 2)
+    np.testing.assert_allclose(sp["fit"][:3], fo[:3], rtol=1e-4)
+
+
+SEEDS = (0, 1, 2, 3, 4, 5)
+NRUN = 800
+
+
+def _avg_spectrum(runs):
+    """Ensemble average of Y over runs of (q, u); peak and width of the mean Re Y."""
+    Ys = []
+    for q, u in runs:
+        om, Y, _, _ = oracle.spectrum(q, u, W.dt, NF, WMAX)
+        Ys.append(Y)
+    Ym = np.mean(Ys, axis=0)
+    wr, dw = oracle.peak_and_fwhm(om, Ym.real)
+    return wr, dw
+
+
+@pytest.fixture(scope="module")
+def oracle_ensemble():
+    op = _oracle_params()
+    runs = []
+    for seed in SEEDS:
+        w = Workload("spectrum", N=W.N, l_max=W.l_max, T_e_eV=W.T_e_eV, n_e_m3=W.n_e_m3,
+                     drive_kind=W.drive_kind, V_volts=W.V_volts, width_wpe=W.width_wpe, seed=seed)
+        x, v = workload_state(w)
+        op.seed = seed
+        _, _, q, u, _ = oracle.run(op, x, v, NRUN)
+        runs.append((q, u))
+    return _avg_spectrum(runs)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_run_spectrum_statistics(imrp, oracle_ensemble, prec):
+    """Ensemble of 6 seeds on each side (same seeded states, same wall keys):
+    the mean admittance peaks within 1 % and its half-width within 5 %."""
+    runs = []
+    for seed in SEEDS:
+        w = Workload("spectrum", N=W.N, l_max=W.l_max, T_e_eV=W.T_e_eV, n_e_m3=W.n_e_m3,
+                     drive_kind=W.drive_kind, V_volts=W.V_volts, width_wpe=W.width_wpe, seed=seed)
+        x, v = workload_state(w)
+        with imrp.Sim(imrp.params_from_workload(w, precision=prec)) as sim:
+            sim.load(x, v)
+            q, u = sim.step(NRUN)
+        runs.append((q, u))
+    wr, dw = _avg_spectrum(runs)
+    wr_o, dw_o = oracle_ensemble
+    assert wr == pytest.approx(wr_o, rel=0.01)
+    assert dw == pytest.approx(dw_o, rel=0.05)
