@@ -168,6 +168,34 @@ int imrp_get_info(const imrp_ctx* ctx, imrp_info* info);
 int imrp_profile_steps(imrp_ctx* ctx, int64_t n_steps, double* ms);
 
 /* ---------------------------------------------------------------------------
+ * Autotuning and batched ensembles (no counterpart in the paper: they serve the
+ * ensemble and request-serving workloads built on the same hot path).
+ *
+ * imrp_autotune times, on the loaded particles and with field evaluations only
+ * (the state does not advance), the field kernel at 8, 4, 2 and 1 warps per
+ * CTA and the tile scan at 8, 16 and 32 components per block, and keeps the
+ * fastest of each for the context. wpb_out / scan_cpb_out (may be NULL)
+ * receive the choices. Errors: IMRP_E_STATE (nothing loaded), IMRP_E_CUDA. */
+int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* scan_cpb_out);
+
+/* A batch steps several loaded contexts of one device together: every step of
+ * every context is captured into one CUDA graph (each context on its own
+ * stream, forked from and joined to the batch's stream), replayed per pair of
+ * steps, so that instances of uneven N overlap on the GPU. The batch does not
+ * own the contexts; they must stay alive and must not be used through their
+ * own entry points between imrp_batch_step and imrp_batch_sync. Each context
+ * computes exactly what imrp_step would compute for it alone.
+ * imrp_batch_create: ctxs[n] distinct, loaded, same device.
+ * imrp_batch_step: queues n_steps steps of every context (asynchronous).
+ * imrp_batch_sync: waits and checks every context's device error flags. */
+typedef struct imrp_batch imrp_batch;
+int imrp_batch_create(imrp_ctx* const* ctxs, int n, imrp_batch** out);
+int imrp_batch_step(imrp_batch* b, int64_t n_steps);
+int imrp_batch_sync(imrp_batch* b);
+int imrp_batch_destroy(imrp_batch* b);
+const char* imrp_batch_last_error(const imrp_batch* b);
+
+/* ---------------------------------------------------------------------------
  * Field evaluation without any allocation. (The paper has no counterpart: this
  * entry point exists for the software that embeds the library.)
  *

@@ -79,6 +79,7 @@ struct imrp_ctx {
   int nc = 0;
   int64_t ntiles = 0, ngroups = 0;
   int wpb = 8;
+  int scan_cpb = 16;  // components per block of the tile scan
   // streams / graphs
   cudaStream_t own_stream = nullptr, stream = nullptr;
   cudaGraphExec_t graph2 = nullptr;
@@ -200,7 +201,7 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   ks->moments(ma, s);
   if (ev) cudaEventRecord(ev[3], s);
   launch_tile_scan<T>(static_cast<T*>(ctx->agg), static_cast<T*>(ctx->pfx), ctx->gagg, ctx->ntiles,
-                      ctx->nc, s);
+                      ctx->nc, s, ctx->scan_cpb);
   launch_group_scan<T>(ctx->gagg, static_cast<T*>(ctx->gbase), static_cast<T*>(ctx->tot), ctx->totd,
                        ctx->ngroups, ctx->nc, s);
   FinalizeArgs fa;
@@ -614,6 +615,230 @@ int imrp_get_info(const imrp_ctx* ctx, imrp_info* info) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner and batched stepping of many contexts.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Radius keys for the current storage order (no step is taken).
+int ensure_keys(imrp_ctx* ctx) {
+  if (ctx->keys_valid) return IMRP_OK;
+  const double ks = 4294967296.0 / (ctx->r_out * ctx->r_out - 1.0);
+  if (ctx->prec == 1) {
+    float** s = state_ptrs<float>(ctx, ctx->cur);
+    launch_keys<float>(s[0], s[1], s[2], ctx->key0, ctx->idx0, ctx->n, ks, ctx->stream);
+  } else {
+    double** s = state_ptrs<double>(ctx, ctx->cur);
+    launch_keys<double>(s[0], s[1], s[2], ctx->key0, ctx->idx0, ctx->n, ks, ctx->stream);
+  }
+  CK(cudaGetLastError());
+  ctx->keys_valid = true;
+  return IMRP_OK;
+}
+
+// Device time of stage k (events ev[k] .. ev[k+1]) of a field-only pass, summed over reps.
+int time_stage(imrp_ctx* ctx, int stage, int reps, float* ms) {
+  cudaEvent_t ev[IMRP_N_STAGES + 1];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  float tot = 0.f;
+  int rc = IMRP_OK;
+  for (int r = 0; r < reps && !rc; ++r) {
+    rc = enqueue_any(ctx, false, ev);
+    if (rc) break;
+    cudaError_t e = cudaEventSynchronize(ev[IMRP_N_STAGES]);
+    if (e != cudaSuccess) { rc = ctx->fail(IMRP_E_CUDA, "autotune: %s", cudaGetErrorString(e)); break; }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[stage], ev[stage + 1]);
+    tot += t;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  *ms = tot;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* scan_cpb_out) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "autotune before load");
+  const int reps = 3;
+  // field kernel: warps per CTA
+  {
+    int best_w = ctx->wpb;
+    float best = 1e30f;
+    for (int w : {8, 4, 2, 1}) {
+      const int nb = ctx->prec == 1 ? find_set<float>(ctx->L)->field_blocks_per_sm(w)
+                                    : find_set<double>(ctx->L)->field_blocks_per_sm(w);
+      if (nb < 1) continue;
+      ctx->wpb = w;
+      float ms = 0.f;
+      int rc = time_stage(ctx, 4, reps, &ms);
+      if (rc) return rc;
+      if (ms < best) { best = ms; best_w = w; }
+    }
+    ctx->wpb = best_w;
+  }
+  // tile scan: components per block
+  {
+    int best_c = ctx->scan_cpb;
+    float best = 1e30f;
+    for (int c : {8, 16, 32}) {
+      ctx->scan_cpb = c;
+      float ms = 0.f;
+      int rc = time_stage(ctx, 3, reps, &ms);
+      if (rc) return rc;
+      if (ms < best) { best = ms; best_c = c; }
+    }
+    ctx->scan_cpb = best_c;
+  }
+  if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+  if (wpb_out) *wpb_out = ctx->wpb;
+  if (scan_cpb_out) *scan_cpb_out = ctx->scan_cpb;
+  return check_err(ctx);
+}
+
+struct imrp_batch {
+  std::vector<imrp_ctx*> c;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t g = nullptr;
+  std::vector<int> cur_at_capture;
+  std::vector<const double*> hist_at_capture;
+  std::string err;
+};
+
+extern "C" int imrp_batch_create(imrp_ctx* const* ctxs, int n, imrp_batch** out) {
+  if (!out || !ctxs || n < 1) return IMRP_E_INVAL;
+  *out = nullptr;
+  int dev0 = -1;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || !ctxs[i]->loaded) return IMRP_E_STATE;
+    if (dev0 < 0) dev0 = ctxs[i]->device;
+    if (ctxs[i]->device != dev0) return IMRP_E_INVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return IMRP_E_INVAL;
+  }
+  imrp_batch* b = new (std::nothrow) imrp_batch();
+  if (!b) return IMRP_E_NOMEM;
+  b->c.assign(ctxs, ctxs + n);
+  bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  b->join.assign(n, nullptr);
+  for (int i = 0; i < n && ok; ++i) ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (auto e : b->join) if (e) cudaEventDestroy(e);
+    delete b;
+    return IMRP_E_CUDA;
+  }
+  *out = b;
+  return IMRP_OK;
+}
+
+extern "C" int imrp_batch_destroy(imrp_batch* b) {
+  if (!b) return IMRP_OK;
+  cudaStreamSynchronize(b->stream);
+  if (b->g) cudaGraphExecDestroy(b->g);
+  cudaStreamDestroy(b->stream);
+  cudaEventDestroy(b->fork);
+  for (auto e : b->join) cudaEventDestroy(e);
+  delete b;
+  return IMRP_OK;
+}
+
+extern "C" const char* imrp_batch_last_error(const imrp_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+namespace {
+int batch_fail(imrp_batch* b, imrp_ctx* ctx, int rc) {
+  b->err = ctx ? ctx->err : std::string("batch error");
+  return rc;
+}
+}  // namespace
+
+extern "C" int imrp_batch_step(imrp_batch* b, int64_t n_steps) {
+  if (!b) return IMRP_E_INVAL;
+  if (n_steps < 0) return IMRP_E_INVAL;
+  if (n_steps == 0) return IMRP_OK;
+  const int n = int(b->c.size());
+  // prior work of each context happens before the batch; histories large enough
+  for (imrp_ctx* ctx : b->c) {
+    int rc = grow_history(ctx, ctx->host_step + n_steps + 1);
+    if (rc) return batch_fail(b, ctx, rc);
+    rc = ensure_keys(ctx);
+    if (rc) return batch_fail(b, ctx, rc);
+    cudaEventRecord(b->join[0], ctx->stream);
+    cudaStreamWaitEvent(b->stream, b->join[0], 0);
+  }
+  int64_t pairs = n_steps / 2;
+  if (pairs > 0) {
+    bool valid = b->g != nullptr;
+    for (int i = 0; i < n && valid; ++i)
+      valid = b->cur_at_capture[i] == b->c[i]->cur && b->hist_at_capture[i] == b->c[i]->qhist;
+    if (!valid) {
+      if (b->g) { cudaGraphExecDestroy(b->g); b->g = nullptr; }
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return batch_fail(b, nullptr, IMRP_E_CUDA);
+      cudaEventRecord(b->fork, b->stream);
+      int rc = IMRP_OK;
+      for (int i = 0; i < n && !rc; ++i) {
+        imrp_ctx* ctx = b->c[i];
+        cudaStreamWaitEvent(ctx->stream, b->fork, 0);
+        rc = enqueue_any(ctx, true);
+        if (!rc) rc = enqueue_any(ctx, true);
+        cudaEventRecord(b->join[i], ctx->stream);
+        cudaStreamWaitEvent(b->stream, b->join[i], 0);
+        if (rc) { b->err = ctx->err; }
+      }
+      cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+      if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+      if (ec != cudaSuccess) { b->err = cudaGetErrorString(ec); return IMRP_E_CUDA; }
+      ec = cudaGraphInstantiate(&b->g, g, 0);
+      cudaGraphDestroy(g);
+      if (ec != cudaSuccess) { b->err = cudaGetErrorString(ec); return IMRP_E_CUDA; }
+      b->cur_at_capture.resize(n);
+      b->hist_at_capture.resize(n);
+      for (int i = 0; i < n; ++i) {
+        b->cur_at_capture[i] = b->c[i]->cur;
+        b->hist_at_capture[i] = b->c[i]->qhist;
+      }
+    }
+    for (int64_t k = 0; k < pairs; ++k)
+      if (cudaGraphLaunch(b->g, b->stream) != cudaSuccess) { b->err = "graph launch"; return IMRP_E_CUDA; }
+  }
+  if (n_steps & 1) {
+    cudaEventRecord(b->fork, b->stream);
+    for (int i = 0; i < n; ++i) {
+      imrp_ctx* ctx = b->c[i];
+      cudaStreamWaitEvent(ctx->stream, b->fork, 0);
+      int rc = enqueue_any(ctx, true);
+      if (rc) return batch_fail(b, ctx, rc);
+      cudaEventRecord(b->join[i], ctx->stream);
+      cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+  }
+  for (imrp_ctx* ctx : b->c) {
+    ctx->host_step += n_steps;
+    // later work on the context's own stream waits for the batch
+    cudaEventRecord(b->fork, b->stream);
+    cudaStreamWaitEvent(ctx->stream, b->fork, 0);
+  }
+  if (cudaGetLastError() != cudaSuccess) { b->err = "launch"; return IMRP_E_CUDA; }
+  return IMRP_OK;
+}
+
+extern "C" int imrp_batch_sync(imrp_batch* b) {
+  if (!b) return IMRP_E_INVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) { b->err = "sync"; return IMRP_E_CUDA; }
+  for (imrp_ctx* ctx : b->c) {
+    int rc = check_err(ctx);
+    if (rc) return batch_fail(b, ctx, rc);
+  }
+  return IMRP_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Spectrum post-processing on the host (peak, width, damped-sine fit).

@@ -250,9 +250,10 @@ void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, 
 // T (the stored in-group result is T); the group total goes to gagg[g][u] in
 // FP64. (FP64 arithmetic per thread is kept out of this kernel: the FP64 rate
 // of the GPU is a small fraction of its FP32 rate.)
-constexpr int kScanComps = 16;  // even: component parity (Rs/Is) = parity of cc
 
-template <class T>
+// kScanComps (components per block) is a template parameter, even, so that the
+// component parity (Rs / Is) is the parity of cc; the autotuner picks it.
+template <class T, int kScanComps>
 __global__ void __launch_bounds__(kTilesPerGroup) k_tile_scan(const T* __restrict__ agg, T* __restrict__ pfx,
                                                              double* __restrict__ gagg, int64_t ntiles, int nc) {
   constexpr int NW = kTilesPerGroup / 32;
@@ -304,10 +305,13 @@ __global__ void __launch_bounds__(kTilesPerGroup) k_tile_scan(const T* __restric
 }
 
 template <class T>
-void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s) {
+void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s, int cpb) {
   const int64_t ng = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
-  dim3 grid(unsigned(ng), unsigned((nc + kScanComps - 1) / kScanComps));
-  k_tile_scan<T><<<grid, kTilesPerGroup, 0, s>>>(agg, pfx, gagg, ntiles, nc);
+  const int c = cpb == 8 ? 8 : (cpb == 32 ? 32 : 16);
+  dim3 grid(unsigned(ng), unsigned((nc + c - 1) / c));
+  if (c == 8) k_tile_scan<T, 8><<<grid, kTilesPerGroup, 0, s>>>(agg, pfx, gagg, ntiles, nc);
+  else if (c == 32) k_tile_scan<T, 32><<<grid, kTilesPerGroup, 0, s>>>(agg, pfx, gagg, ntiles, nc);
+  else k_tile_scan<T, 16><<<grid, kTilesPerGroup, 0, s>>>(agg, pfx, gagg, ntiles, nc);
 }
 
 // Grid ceil(nc/32), 256 threads: warp w owns a contiguous segment of groups.
@@ -441,7 +445,7 @@ void launch_dft(const double* q, const double* u, int64_t ns, double dt, double 
                                cudaStream_t);                                                      \
   template void launch_scatter_by_id<T>(const T* const*, int, const uint32_t*, double*, int64_t,   \
                                         cudaStream_t);                                             \
-  template void launch_tile_scan<T>(const T*, T*, double*, int64_t, int, cudaStream_t);            \
+  template void launch_tile_scan<T>(const T*, T*, double*, int64_t, int, cudaStream_t, int);       \
   template void launch_group_scan<T>(const double*, T*, T*, double*, int64_t, int, cudaStream_t);
 IMRP_INST_CORE(float)
 IMRP_INST_CORE(double)

@@ -38,8 +38,10 @@ void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, 
                           int64_t n, cudaStream_t s);
 
 // ---- scans (imrp_core.cu) ---------------------------------------------------
+// cpb: components per block, one of 8, 16, 32 (chosen by the autotuner)
 template <class T>
-void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s);
+void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s,
+                      int cpb = 16);
 template <class T>
 void launch_group_scan(const double* gagg, T* gbase, T* tot, double* totd, int64_t ngroups,
                        int nc, cudaStream_t s);

@@ -20,7 +20,8 @@ EXPORTS = [
     "imrp_default_params", "imrp_create", "imrp_destroy", "imrp_last_error", "imrp_set_stream",
     "imrp_load_particles", "imrp_step", "imrp_step_async", "imrp_sync", "imrp_get_qdiff",
     "imrp_get_field", "imrp_get_particles", "imrp_spectrum", "imrp_get_info", "imrp_profile_steps",
-    "imrp_field_noalloc",
+    "imrp_field_noalloc", "imrp_autotune", "imrp_batch_create", "imrp_batch_step", "imrp_batch_sync",
+    "imrp_batch_destroy", "imrp_batch_last_error",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -85,9 +86,16 @@ def load_library(path: str = LIB_PATH):
     L.imrp_spectrum.argtypes = [c_void_p, ctypes.c_int64, ctypes.c_double, pd, pd, pd, pd, pd, pd]
     L.imrp_get_info.argtypes = [c_void_p, P(Info)]
     L.imrp_profile_steps.argtypes = [c_void_p, ctypes.c_int64, pd]
+    L.imrp_autotune.argtypes = [c_void_p, P(ctypes.c_int), P(ctypes.c_int)]
+    L.imrp_batch_create.argtypes = [P(c_void_p), ctypes.c_int, P(c_void_p)]
+    L.imrp_batch_step.argtypes = [c_void_p, ctypes.c_int64]
+    L.imrp_batch_sync.argtypes = [c_void_p]
+    L.imrp_batch_destroy.argtypes = [c_void_p]
+    L.imrp_batch_last_error.argtypes = [c_void_p]
+    L.imrp_batch_last_error.restype = ctypes.c_char_p
     L.imrp_field_noalloc.argtypes = [P(Params), c_void_p, ctypes.c_int64, ctypes.c_int64, c_void_p, c_void_p]
     for name in EXPORTS:
-        if name != "imrp_default_params" and name != "imrp_last_error":
+        if name not in ("imrp_default_params", "imrp_last_error", "imrp_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -123,6 +131,47 @@ def field_noalloc(params: Params, x_dev_ptr: int, n: int, step: int, E_dev_ptr: 
                                            ctypes.c_void_p(E_dev_ptr), ctypes.c_void_p(stream_ptr or 0))
     if rc != 0:
         raise IMRPError(rc, "imrp_field_noalloc failed")
+
+
+class Batch:
+    """Steps several loaded Sim instances together (one captured graph per step pair)."""
+
+    def __init__(self, sims):
+        self._lib = load_library()
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s._h for s in self.sims])
+        h = ctypes.c_void_p()
+        rc = self._lib.imrp_batch_create(arr, len(self.sims), ctypes.byref(h))
+        if rc != 0:
+            raise IMRPError(rc, "imrp_batch_create failed")
+        self._h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise IMRPError(rc, self._lib.imrp_batch_last_error(self._h).decode())
+
+    def step(self, n: int):
+        self._check(self._lib.imrp_batch_step(self._h, n))
+
+    def sync(self):
+        self._check(self._lib.imrp_batch_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.imrp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Sim:
@@ -222,6 +271,12 @@ class Sim:
         ms = np.zeros(len(STAGES))
         self._check(self._lib.imrp_profile_steps(self._h, n, _ptr(ms)))
         return dict(zip(STAGES, ms.tolist()))
+
+    def autotune(self):
+        """Picks the field CTA size and tile-scan width by timing; returns (wpb, scan_cpb)."""
+        w, c = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.imrp_autotune(self._h, ctypes.byref(w), ctypes.byref(c)))
+        return w.value, c.value
 
     def info(self) -> Info:
         i = Info()
