@@ -26,6 +26,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -144,6 +146,64 @@ def cpu_baseline(w, budget_s=15.0, L=None):
                       f"scan evaluator, {dt:.1f} s"}
 
 
+def ensemble_measure(steps, warmup, autotune=True, n_instances=64, stream=None):
+    """The 64-instance ensemble (N log-uniform in [1e4, 1e6], T_e in [0.5, 5] eV,
+    n_e log-uniform in [1e14, 1e17] m^-3, l_max in {8, 12, 16}, mixed precision),
+    stepped as one batch; device time with CUDA events on the batch stream."""
+    import torch
+    from paper_2111_13072_gb300 import imrp
+    from paper_2111_13072_gb300.inputs import workload_state
+    from paper_2111_13072_gb300.serve import ensemble_workloads
+    ws = ensemble_workloads(n_instances)
+    sims = []
+    for w in ws:
+        s = imrp.Sim(imrp.params_from_workload(w))
+        x, v = workload_state(w)
+        s.load(x, v)
+        if autotune:
+            s.autotune()
+        sims.append(s)
+    stream = stream or torch.cuda.Stream()
+    with imrp.Batch(sims) as b:
+        b.set_stream(stream.cuda_stream)
+        b.step(warmup)
+        b.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        b.sync()
+        ms = e0.elapsed_time(e1)
+    ntot = sum(w.N for w in ws)
+    for s in sims:
+        s.close()
+    return {"value": ntot * steps / (ms / 1e3), "unit": UNIT, "instances": n_instances,
+            "particles": ntot, "steps": steps, "ms_per_step": ms / steps, "autotuned": autotune,
+            "workload": "64 instances, N log-uniform [1e4,1e6], T_e U[0.5,5] eV, n_e log-U[1e14,1e17], "
+                        "l_max in {8,12,16}, mixed precision, one captured graph per step pair"}
+
+
+def serving_measure(n_requests, steps, rate=20.0):
+    """Continuous-batching service: Poisson arrivals at `rate` of spectrum
+    requests (N log-uniform in [1e5, 4e6], T_e in [0.5, 5] eV, n_e log-uniform
+    in [1e14, 1e17] m^-3, l_max in {8, 16}); latency = completion - arrival."""
+    from paper_2111_13072_gb300.serve import SpectrumServer, serving_requests
+    reqs = serving_requests(n_requests, rate=rate, steps=steps)
+    srv = SpectrumServer(chunk=max(10, steps // 10))
+    t0 = time.perf_counter()
+    res = srv.serve(reqs, realtime=True)
+    span = time.perf_counter() - t0
+    lat = np.array([r.latency for r in res])
+    ps = sum(r.workload.N * r.steps for r in reqs)
+    return {"requests": n_requests, "steps_per_request": steps, "rate_req_per_s": rate,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "spectra_per_s": n_requests / span, "particle_steps_per_s": ps / span,
+            "max_active": srv.stats["max_active"], "peak_bytes": srv.stats["peak_bytes"],
+            "workload": "Poisson arrivals, N log-uniform [1e5,4e6], T_e U[0.5,5] eV, n_e log-U[1e14,1e17], "
+                        "l_max in {8,16}, mixed precision"}
+
+
 def run_reference(args, w):
     """--impl reference: the FP64 CPU oracle as the reference arm."""
     import oracle
@@ -186,6 +246,8 @@ def main():
     ap.add_argument("--workload", default="mixed_n2e6_l16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -194,6 +256,28 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     from paper_2111_13072_gb300.inputs import WORKLOADS, workload_state
+    if args.workload in ("ensemble64", "serving"):
+        import torch
+        torch.cuda.set_device(local)
+        from paper_2111_13072_gb300 import build
+        build.build()
+        if args.workload == "ensemble64":
+            with ClockSampler(local) as clk:
+                r = ensemble_measure(args.steps, args.warmup)
+            line = {"metric": "particle-steps/s, 64-instance batched ensemble", "value": r["value"],
+                    "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                    "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                    "config": {"workload": r["workload"], "particles": r["particles"]},
+                    "clocks": clk.summary(), "gpu_launches": LAUNCHES_PER_STEP * 64 * args.steps}
+        else:
+            r = serving_measure(max(4, args.steps // 50), args.steps)
+            line = {"metric": "served spectra p50/p99 latency", "value": r["p50_s"], "unit": "s",
+                    "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": 0,
+                    "p99_s": r["p99_s"], "spectra_per_s": r["spectra_per_s"], "data": "synthetic",
+                    "dtype": "f32", "config": r, "vs_baseline": None, "scaling": "weak"}
+        print(json.dumps(line), flush=True)
+        return
     w = WORKLOADS[args.workload]
 
     if args.impl == "reference":
@@ -310,6 +394,9 @@ def main():
                     "note": "plain FP64 GPU path, same workload"}
     sim.close()
 
+    serving = None if args.no_serving else serving_measure(12, 500)
+    ensemble = None if args.no_ensemble else ensemble_measure(200, 4, autotune=False)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -323,7 +410,8 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (per-step working set > 300 MB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks, "fp64_gpu": fp64}
+                "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks, "fp64_gpu": fp64,
+                "serving": serving, "ensemble": ensemble}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

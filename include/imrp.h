@@ -92,6 +92,11 @@ void imrp_default_params(imrp_params* p);
  * IMRP_E_NOMEM, IMRP_E_CUDA. */
 int imrp_create(const imrp_params* p, imrp_ctx** out);
 
+/* Device memory in bytes that imrp_create(p) allocates, plus the Q_diff history
+ * of n_steps steps: what an admission controller needs before creating a
+ * context. Errors: IMRP_E_INVAL. */
+int imrp_footprint(const imrp_params* p, int64_t n_steps, size_t* bytes);
+
 /* Frees all device memory and the stream. NULL is accepted. */
 int imrp_destroy(imrp_ctx* ctx);
 
@@ -193,6 +198,8 @@ int imrp_batch_create(imrp_ctx* const* ctxs, int n, imrp_batch** out);
 int imrp_batch_step(imrp_batch* b, int64_t n_steps);
 int imrp_batch_sync(imrp_batch* b);
 int imrp_batch_destroy(imrp_batch* b);
+/* Issues the batch's work on a caller-owned cudaStream_t (NULL: its own). */
+int imrp_batch_set_stream(imrp_batch* b, void* cuda_stream);
 const char* imrp_batch_last_error(const imrp_batch* b);
 
 /* ---------------------------------------------------------------------------

@@ -309,6 +309,24 @@ int launch_steps(imrp_ctx* ctx, int64_t nsteps) {
   return IMRP_OK;
 }
 
+// Device bytes that alloc_ctx requests for N particles at degree L (before
+// the Q_diff history, which grows with the steps taken).
+size_t footprint_bytes(int64_t N, int L, int prec) {
+  const size_t es = prec == 1 ? sizeof(float) : sizeof(double);
+  const int64_t ntiles = (N + 31) / 32;
+  const int64_t ngroups = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
+  const int64_t nc = 2 * int64_t(ncomp(L));
+  size_t b = 0;
+  b += 2 * (6 * N * es + N * 4);                    // state ping-pong + ids
+  b += 4 * size_t(N) * 4;                           // keys and slots
+  b += size_t(256 * sort_blocks(N) + 256) * 4;      // histogram
+  b += 2 * size_t(ntiles * nc) * es;                // tile sums and in-group scans
+  b += size_t(ngroups * nc) * (es + 8) + size_t(nc) * (es + 8);
+  b += 3 * size_t(N) * es + 6 * size_t(N) * 8;      // field output, staging
+  b += sizeof(StepState) + sizeof(int);
+  return b;
+}
+
 int alloc_ctx(imrp_ctx* ctx) {
   const int64_t N = ctx->p.N;
   const size_t es = ctx->prec == 1 ? sizeof(float) : sizeof(double);
@@ -341,6 +359,14 @@ int alloc_ctx(imrp_ctx* ctx) {
 }  // namespace
 
 extern "C" {
+
+int imrp_footprint(const imrp_params* p, int64_t n_steps, size_t* bytes) {
+  if (!p || !bytes || p->N < 1 || n_steps < 0) return IMRP_E_INVAL;
+  if (p->precision != 0 && p->precision != 1) return IMRP_E_INVAL;
+  if (p->l_max < 1 || p->l_max >= kTabL - 2) return IMRP_E_INVAL;
+  *bytes = footprint_bytes(p->N, p->l_max, p->precision) + size_t(2 * std::max<int64_t>(n_steps + 1, 4096)) * 8;
+  return IMRP_OK;
+}
 
 void imrp_default_params(imrp_params* p) {
   if (!p) return;
@@ -701,6 +727,7 @@ extern "C" int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* scan_cpb_out) {
 struct imrp_batch {
   std::vector<imrp_ctx*> c;
   cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
   cudaGraphExec_t g = nullptr;
@@ -742,7 +769,7 @@ extern "C" int imrp_batch_destroy(imrp_batch* b) {
   if (!b) return IMRP_OK;
   cudaStreamSynchronize(b->stream);
   if (b->g) cudaGraphExecDestroy(b->g);
-  cudaStreamDestroy(b->stream);
+  cudaStreamDestroy(b->own_stream ? b->own_stream : b->stream);
   cudaEventDestroy(b->fork);
   for (auto e : b->join) cudaEventDestroy(e);
   delete b;
@@ -757,6 +784,14 @@ int batch_fail(imrp_batch* b, imrp_ctx* ctx, int rc) {
   return rc;
 }
 }  // namespace
+
+extern "C" int imrp_batch_set_stream(imrp_batch* b, void* stream) {
+  if (!b) return IMRP_E_INVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return IMRP_E_CUDA;
+  if (b->own_stream == nullptr) b->own_stream = b->stream;
+  b->stream = stream ? static_cast<cudaStream_t>(stream) : b->own_stream;
+  return IMRP_OK;
+}
 
 extern "C" int imrp_batch_step(imrp_batch* b, int64_t n_steps) {
   if (!b) return IMRP_E_INVAL;

@@ -21,7 +21,7 @@ EXPORTS = [
     "imrp_load_particles", "imrp_step", "imrp_step_async", "imrp_sync", "imrp_get_qdiff",
     "imrp_get_field", "imrp_get_particles", "imrp_spectrum", "imrp_get_info", "imrp_profile_steps",
     "imrp_field_noalloc", "imrp_autotune", "imrp_batch_create", "imrp_batch_step", "imrp_batch_sync",
-    "imrp_batch_destroy", "imrp_batch_last_error",
+    "imrp_batch_destroy", "imrp_batch_last_error", "imrp_batch_set_stream", "imrp_footprint",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -91,6 +91,8 @@ def load_library(path: str = LIB_PATH):
     L.imrp_batch_step.argtypes = [c_void_p, ctypes.c_int64]
     L.imrp_batch_sync.argtypes = [c_void_p]
     L.imrp_batch_destroy.argtypes = [c_void_p]
+    L.imrp_batch_set_stream.argtypes = [c_void_p, c_void_p]
+    L.imrp_footprint.argtypes = [P(Params), ctypes.c_int64, P(ctypes.c_size_t)]
     L.imrp_batch_last_error.argtypes = [c_void_p]
     L.imrp_batch_last_error.restype = ctypes.c_char_p
     L.imrp_field_noalloc.argtypes = [P(Params), c_void_p, ctypes.c_int64, ctypes.c_int64, c_void_p, c_void_p]
@@ -133,6 +135,15 @@ def field_noalloc(params: Params, x_dev_ptr: int, n: int, step: int, E_dev_ptr: 
         raise IMRPError(rc, "imrp_field_noalloc failed")
 
 
+def footprint(params: Params, n_steps: int) -> int:
+    """Device bytes of a context for these parameters and n_steps recorded steps."""
+    out = ctypes.c_size_t()
+    rc = load_library().imrp_footprint(ctypes.byref(params), n_steps, ctypes.byref(out))
+    if rc != 0:
+        raise IMRPError(rc, "imrp_footprint failed")
+    return out.value
+
+
 class Batch:
     """Steps several loaded Sim instances together (one captured graph per step pair)."""
 
@@ -149,6 +160,9 @@ class Batch:
     def _check(self, rc):
         if rc != 0:
             raise IMRPError(rc, self._lib.imrp_batch_last_error(self._h).decode())
+
+    def set_stream(self, stream_ptr: int | None):
+        self._check(self._lib.imrp_batch_set_stream(self._h, ctypes.c_void_p(stream_ptr or 0)))
 
     def step(self, n: int):
         self._check(self._lib.imrp_batch_step(self._h, n))
