@@ -52,7 +52,8 @@ typedef struct imrp_params {
   double T_e_eV;     /* electron temperature [eV]; informational (the field does not use it) */
   int64_t N;         /* capacity: maximum number of super-particles               */
   int32_t l_max;     /* truncation degree of the projection P^ (Sec. 2/3); one of 1,2,4,8,12,16,24 */
-  int32_t m0_only;   /* must be 0 (full (l,m) expansion)                          */
+  int32_t m0_only;   /* 0: all (l, m); 1: only the m = 0 terms of each degree -- with
+                        l_max = 1 the truncated kernel of Sec. 3 (cos t cos t' dipole) */
   double dt;         /* time step [1/omega_pe]                                    */
   int32_t drive_kind; /* 0 Gaussian pulse, 1 impulse at the first step (Sec. 4), 2 off */
   int32_t wall_rule;  /* 0 diffuse reflection (Sec. 4), 1 specular reflection      */
@@ -217,7 +218,7 @@ const char* imrp_batch_last_error(const imrp_batch* b);
  * 7 MB), which every GPU that loads this library holds until the process
  * exits.
  *
- *   p       physical parameters as for imrp_create (p->N is ignored);
+ *   p       physical parameters as for imrp_create (p->N is ignored, m0_only = 0);
  *           1 <= p->l_max <= IMRP_NOALLOC_MAX_L and l_max instantiated
  *   x_dev   device pointer, FP64 positions [n][3] in units of R, 1 < |x| < r_out
  *   n       1 <= n <= IMRP_NOALLOC_MAX_N; n~ and the ion background follow n

@@ -247,6 +247,7 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   a.r_out = T(ctx->r_out);
   a.wall_rule = ctx->p.wall_rule;
   a.self_image = ctx->p.self_image;
+  a.m0_only = ctx->p.m0_only;
   a.seed = ctx->p.seed;
   double rl = 1.0;
   for (int l = 0; l < kTabL; ++l) {
@@ -410,7 +411,7 @@ int imrp_create(const imrp_params* p, imrp_ctx** out) {
   if (!(p->R_out_m > p->R_D_m)) return bad("outer wall");
   if (!(p->eps_D >= 1.0) || !(p->n_e_m3 > 0) || !(p->dt > 0) || !(p->T_e_eV > 0)) return bad("plasma");
   if (p->N < 1 || p->N > (int64_t(1) << 31)) return bad("N");
-  if (p->m0_only != 0) return bad("m0_only");
+  if (p->m0_only != 0 && p->m0_only != 1) return bad("m0_only");
   if (p->precision != 0 && p->precision != 1) return bad("precision");
   if (p->drive_kind < 0 || p->drive_kind > 2 || p->wall_rule < 0 || p->wall_rule > 1) return bad("rules");
   if (p->drive_kind == 0 && !(p->width_wpe > 0)) return bad("width");
@@ -489,16 +490,16 @@ int imrp_set_stream(imrp_ctx* ctx, void* stream) {
 int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t n) {
   if (!ctx) return IMRP_E_INVAL;
   if (!x || !v || n < 1 || n > ctx->cap) return ctx->fail(IMRP_E_INVAL, "load: n = %lld out of range [1, %lld]", (long long)n, (long long)ctx->cap);
-  // interleave on the device: copy x and v into the [n][6] staging layout
-  CK(cudaMemcpy2DAsync(ctx->stage, 6 * sizeof(double), x, 3 * sizeof(double), 3 * sizeof(double), n,
-                       cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpy2DAsync(ctx->stage + 3, 6 * sizeof(double), v, 3 * sizeof(double), 3 * sizeof(double), n,
-                       cudaMemcpyHostToDevice, ctx->stream));
+  // two contiguous copies into the staging buffer: x [n][3], then v [n][3]
+  CK(cudaMemcpyAsync(ctx->stage, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->stage + 3 * n, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   ctx->cur = 0;
   if (ctx->prec == 1)
-    launch_load<float>(ctx->stage, state_ptrs<float>(ctx, 0), ctx->id_buf[0], n, ctx->r_out, ctx->derr, ctx->stream);
+    launch_load<float>(ctx->stage, ctx->stage + 3 * n, state_ptrs<float>(ctx, 0), ctx->id_buf[0], n, ctx->r_out,
+                       ctx->derr, ctx->stream);
   else
-    launch_load<double>(ctx->stage, state_ptrs<double>(ctx, 0), ctx->id_buf[0], n, ctx->r_out, ctx->derr, ctx->stream);
+    launch_load<double>(ctx->stage, ctx->stage + 3 * n, state_ptrs<double>(ctx, 0), ctx->id_buf[0], n, ctx->r_out,
+                        ctx->derr, ctx->stream);
   StepState s0{};
   s0.step = 0;
   s0.next = 0;
@@ -577,19 +578,22 @@ int imrp_get_particles(imrp_ctx* ctx, double* x, double* v) {
   if (!ctx) return IMRP_E_INVAL;
   if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "get_particles before load");
   const int64_t n = ctx->n;
+  // positions to stage[0, 3n) and velocities to stage[3n, 6n), each [n][3] in id order
   if (ctx->prec == 1) {
     float** s = state_ptrs<float>(ctx, ctx->cur);
-    const float* cs[6] = {s[0], s[1], s[2], s[3], s[4], s[5]};
-    launch_scatter_by_id<float>(cs, 6, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
+    const float* cx[3] = {s[0], s[1], s[2]};
+    const float* cv[3] = {s[3], s[4], s[5]};
+    launch_scatter_by_id<float>(cx, 3, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
+    launch_scatter_by_id<float>(cv, 3, ctx->id_buf[ctx->cur], ctx->stage + 3 * n, n, ctx->stream);
   } else {
     double** s = state_ptrs<double>(ctx, ctx->cur);
-    const double* cs[6] = {s[0], s[1], s[2], s[3], s[4], s[5]};
-    launch_scatter_by_id<double>(cs, 6, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
+    const double* cx[3] = {s[0], s[1], s[2]};
+    const double* cv[3] = {s[3], s[4], s[5]};
+    launch_scatter_by_id<double>(cx, 3, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
+    launch_scatter_by_id<double>(cv, 3, ctx->id_buf[ctx->cur], ctx->stage + 3 * n, n, ctx->stream);
   }
-  if (x) CK(cudaMemcpy2DAsync(x, 3 * sizeof(double), ctx->stage, 6 * sizeof(double), 3 * sizeof(double), n,
-                              cudaMemcpyDeviceToHost, ctx->stream));
-  if (v) CK(cudaMemcpy2DAsync(v, 3 * sizeof(double), ctx->stage + 3, 6 * sizeof(double), 3 * sizeof(double), n,
-                              cudaMemcpyDeviceToHost, ctx->stream));
+  if (x) CK(cudaMemcpyAsync(x, ctx->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (v) CK(cudaMemcpyAsync(v, ctx->stage + 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return check_err(ctx);
 }
 

@@ -187,20 +187,22 @@ void launch_keys(const T* x, const T* y, const T* z, uint32_t* key, uint32_t* ki
 
 template <class T> struct Ptr6 { T* d[6]; };
 
-// AoS FP64 [n][6] -> SoA T, ids = 0..n-1; flags positions outside 1 < r < r_out
-// or non-finite values.
+// FP64 positions x[n][3] and velocities v[n][3] -> SoA T, ids = 0..n-1; flags
+// positions outside 1 < r < r_out or non-finite values.
 template <class T>
-__global__ void k_load(const double* __restrict__ xv, Ptr6<T> p, uint32_t* __restrict__ id, int64_t n,
-                       double r_out, int* err) {
+__global__ void k_load(const double* __restrict__ xs, const double* __restrict__ vs, Ptr6<T> p,
+                       uint32_t* __restrict__ id, int64_t n, double r_out, int* err) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double v[6];
   bool fin = true;
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    v[c] = xv[6 * j + c];
-    fin = fin && isfinite(v[c]);
+  for (int c = 0; c < 3; ++c) {
+    v[c] = xs[3 * j + c];
+    v[3 + c] = vs[3 * j + c];
   }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) fin = fin && isfinite(v[c]);
   T t[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) t[c] = T(v[c]);
@@ -213,11 +215,11 @@ __global__ void k_load(const double* __restrict__ xv, Ptr6<T> p, uint32_t* __res
 }
 
 template <class T>
-void launch_load(const double* xv, T* const* dst, uint32_t* id, int64_t n, double r_out, int* err,
-                 cudaStream_t s) {
+void launch_load(const double* xs, const double* vs, T* const* dst, uint32_t* id, int64_t n, double r_out,
+                 int* err, cudaStream_t s) {
   Ptr6<T> p;
   for (int c = 0; c < 6; ++c) p.d[c] = dst[c];
-  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(xv, p, id, n, r_out, err);
+  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(xs, vs, p, id, n, r_out, err);
 }
 
 template <class T>
@@ -441,8 +443,8 @@ void launch_dft(const double* q, const double* u, int64_t ns, double dt, double 
                                   const uint32_t*, int64_t, cudaStream_t);                         \
   template void launch_keys<T>(const T*, const T*, const T*, uint32_t*, uint32_t*, int64_t, double, \
                                cudaStream_t);                                                      \
-  template void launch_load<T>(const double*, T* const*, uint32_t*, int64_t, double, int*,         \
-                               cudaStream_t);                                                      \
+  template void launch_load<T>(const double*, const double*, T* const*, uint32_t*, int64_t, double, \
+                               int*, cudaStream_t);                                                \
   template void launch_scatter_by_id<T>(const T* const*, int, const uint32_t*, double*, int64_t,   \
                                         cudaStream_t);                                             \
   template void launch_tile_scan<T>(const T*, T*, double*, int64_t, int, cudaStream_t, int);       \

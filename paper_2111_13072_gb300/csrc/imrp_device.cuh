@@ -158,6 +158,7 @@ template <class T> struct FieldArgs {
   T r_out;
   int wall_rule;
   int self_image;
+  int m0_only;        // 1: keep only the m = 0 terms of every degree (the paper's truncation)
   uint64_t seed;
   T f[kTabL];         // f_l of App. A
   T rhol[kTabL];      // r_out^l

@@ -40,7 +40,8 @@ void fill_prologue_tables() {
     for (int m = 0; m <= L; ++m)
       for (int l = (m > 1 ? m : 1); l <= L; ++l)
         for (int part = 0; part < (m > 0 ? 2 : 1); ++part)
-          h_comp[co + comp_idx(L, l, m, part)] = uint16_t(l | ((m == 0 && (l & 1)) ? (1 << 8) : 0));
+          h_comp[co + comp_idx(L, l, m, part)] =
+              uint16_t(l | ((m == 0 && (l & 1)) ? (1 << 8) : 0) | (m > 0 ? (1 << 9) : 0));
     auto record = [&](bool isI, int Lp, int M) {
       EntryRec r{};
       const int s = isI ? 0 : 1;

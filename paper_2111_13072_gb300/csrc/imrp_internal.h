@@ -30,8 +30,8 @@ template <class T>
 void launch_keys(const T* x, const T* y, const T* z, uint32_t* key, uint32_t* kidx, int64_t n,
                  double kscale, cudaStream_t s);
 template <class T>
-void launch_load(const double* xv /* [n][6]: x y z vx vy vz */, T* const* dst, uint32_t* id,
-                 int64_t n, double r_out, int* err, cudaStream_t s);
+void launch_load(const double* x /* [n][3] */, const double* v /* [n][3] */, T* const* dst,
+                 uint32_t* id, int64_t n, double r_out, int* err, cudaStream_t s);
 // out[id[j]][c] = comp_c[j] for c < 3 (and c < 6 with the velocity arrays)
 template <class T>
 void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, double* out,

@@ -50,7 +50,7 @@ __host__ __device__ constexpr int comp_tab_off(int L) {
 constexpr int kEntTotal = ent_off(24) + nI(24) + nR(24);
 constexpr int kCompTotal = comp_tab_off(24) + ncomp(24);
 static __device__ EntryRec g_ent[kEntTotal];
-static __device__ uint16_t g_comp[kCompTotal];  // per component: l | (drive << 8)
+static __device__ uint16_t g_comp[kCompTotal];  // per component: l | (drive << 8) | (m > 0) << 9
 
 template <class T> __device__ __forceinline__ T rsqrt_t(T v);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
@@ -249,9 +249,11 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T B = gb[2 * e + 1] + pt[(2 * e + 1) * ntiles];  // sum over outer tiles of q Is(x_i)
       const T W = a.tot[2 * e + 1] - at[(2 * e + 1) * ntiles];  // sum over the other tiles of q Is(x_i)
       T cI = rl * A - a.f[l] * W;
-      if (cr >> 8) cI += T(u_drive * a.cdrive[l]);
+      if ((cr >> 8) & 1) cI += T(u_drive * a.cdrive[l]);
+      T cR = rl * B;
+      if (a.m0_only && ((cr >> 9) & 1)) { cI = T(0); cR = T(0); }
       sc[2 * e] = cI;
-      sc[2 * e + 1] = rl * B;
+      sc[2 * e + 1] = cR;
     }
   }
   __syncwarp();
@@ -374,7 +376,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     T Nx = T(0), Ny = T(0), Nz = T(0);  // sum of grad phi (phi = sum_l r_<^l/r_>^{l+1} P_l)
     const T vmask = valid ? T(1) : T(0);
 #pragma unroll 1
-    for (int s = 1; s <= 16; ++s) {
+    for (int s = 1; s <= 16 && !a.m0_only; ++s) {
       const int src = (lane + s) & 31;
       const T pex = __shfl_sync(0xffffffffu, ex, src);
       const T pey = __shfl_sync(0xffffffffu, ey, src);
@@ -436,6 +438,65 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
         Nz += __shfl_sync(0xffffffffu, tz, dst);
       }
     }
+#pragma unroll 1
+    for (int s = 1; s <= 16 && a.m0_only; ++s) {
+      // m = 0 truncation: sum_l [r_i^l / r_o^{l+1} - f_l / (r_i r_o)^{l+1}] P_l(cos t_i) P_l(cos t_o)
+      const int src = (lane + s) & 31;
+      const T pex = __shfl_sync(0xffffffffu, ex, src);
+      const T pey = __shfl_sync(0xffffffffu, ey, src);
+      const T pez = __shfl_sync(0xffffffffu, ez, src);
+      const T prk = __shfl_sync(0xffffffffu, rk, src);
+      const T pir = __shfl_sync(0xffffffffu, ir, src);
+      const T pm = __shfl_sync(0xffffffffu, vmask, src);
+      const bool me_inner = int(lane) < src;
+      const T ri = me_inner ? rk : prk;
+      const T iri = me_inner ? ir : pir, iro = me_inner ? pir : ir;
+      const T xix = me_inner ? ex : pex, xiy = me_inner ? ey : pey, xiz = me_inner ? ez : pez;
+      const T xox = me_inner ? pex : ex, xoy = me_inner ? pey : ey, xoz = me_inner ? pez : ez;
+      const T sr = ri * iro;
+      const T tt = iri * iro;
+      const T ui = xiz, uo = xoz;  // cos of the polar angles
+      T Pim = T(1), Pi = ui, Dim = T(0), Di = T(1);
+      T Pom = T(1), Po = uo, Dom = T(0), Do = T(1);
+      T sp = sr, tp = tt * tt;     // s^l and t^{l+1} at l = 1
+      T A1 = T(0), A2 = T(0), A3 = T(0), C1 = T(0), C2 = T(0);
+#pragma unroll
+      for (int l = 1; l <= L; ++l) {
+        if (l > 1) {
+          const T cl = T(2 * l - 1) / T(l), dl = T(l - 1) / T(l);
+          const T Pin = cl * ui * Pi - dl * Pim, Pon = cl * uo * Po - dl * Pom;
+          const T Din = Dim + T(2 * l - 1) * Pi, Don = Dom + T(2 * l - 1) * Po;
+          Pim = Pi; Pi = Pin; Dim = Di; Di = Din;
+          Pom = Po; Po = Pon; Dom = Do; Do = Don;
+          sp *= sr;
+          tp *= tt;
+        }
+        const T bl = a.f[l] * tp;
+        const T pp = Pi * Po;
+        A1 += T(l + 1) * sp * pp;
+        A2 += T(l + 1) * bl * pp;
+        A3 += T(l) * sp * pp;
+        const T wgt = sp * iro - bl;
+        C1 += wgt * Pi * Do;
+        C2 += wgt * Di * Po;
+      }
+      // grad at the outer point and at the inner point
+      const T go = -A1 * iro * iro + A2 * iro, gi = (A3 * iro + A2) * iri;
+      const T ogx = go * xox - C1 * iro * uo * xox, ogy = go * xoy - C1 * iro * uo * xoy,
+              ogz = go * xoz + C1 * iro * (T(1) - uo * xoz);
+      const T igx = gi * xix - C2 * iri * ui * xix, igy = gi * xiy - C2 * iri * ui * xiy,
+              igz = gi * xiz + C2 * iri * (T(1) - ui * xiz);
+      const T w = pm * vmask;
+      Nx += w * (me_inner ? igx : ogx); Ny += w * (me_inner ? igy : ogy); Nz += w * (me_inner ? igz : ogz);
+      if (s < 16) {
+        const T tx = w * (me_inner ? ogx : igx), ty = w * (me_inner ? ogy : igy),
+                tz = w * (me_inner ? ogz : igz);
+        const int dst = (lane - s) & 31;
+        Nx += __shfl_sync(0xffffffffu, tx, dst);
+        Ny += __shfl_sync(0xffffffffu, ty, dst);
+        Nz += __shfl_sync(0xffffffffu, tz, dst);
+      }
+    }
     // E = -pf sum_i q_i grad phi = +pf grad phi (q_i = -1)
     const T pfT = T(a.pf);
     Ex += pfT * Nx; Ey += pfT * Ny; Ez += pfT * Nz;
@@ -460,7 +521,28 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     const double qin = fma(a.ion_coef, r2d * rd - 1.0, a.q_s - double(j));
     const T er = T(qin) * (T(a.pf) * ir2 * ir);  // multiplies x (gives r^ / r^2)
     Ex += er * X; Ey += er * Y; Ez += er * Z;
-    if (a.self_image) {
+    if (a.self_image && a.m0_only) {
+      // own image with the m = 0 kernel: pf sum_l f_l r^{-(2l+3)} [(l+1) P_l^2 r^ - P_l P_l' (z^ - u r^)]
+      const T u = Z * ir;
+      T Pm = T(1), P = u, Dm = T(0), D = T(1), rp = ir2 * ir2 * ir;  // r^{-5} at l = 1
+      T hr = T(0), ha = T(0);
+#pragma unroll
+      for (int l = 1; l <= L; ++l) {
+        if (l > 1) {
+          const T Pn = (T(2 * l - 1) * u * P - T(l - 1) * Pm) / T(l);
+          const T Dn = Dm + T(2 * l - 1) * P;
+          Pm = P; P = Pn; Dm = D; D = Dn;
+          rp *= ir2;
+        }
+        hr += a.f[l] * T(l + 1) * P * P * rp;
+        ha += a.f[l] * P * D * rp;
+      }
+      const T pfT = T(a.pf);
+      // r^ = x / r, z^ - u r^ = (0, 0, 1) - u x / r
+      Ex += pfT * (hr * X * ir + ha * u * X * ir);
+      Ey += pfT * (hr * Y * ir + ha * u * Y * ir);
+      Ez += pfT * (hr * Z * ir - ha * (T(1) - u * Z * ir));
+    } else if (a.self_image) {
       // the particle's own image: pf sum_l f_l (l+1) r^{-(2l+3)} r^
       T h = T(0);
 #pragma unroll

@@ -156,3 +156,25 @@ def test_large_sampled_parity(imrp):
     r = np.linalg.norm(xg, axis=1)
     assert np.all(r >= 1.0) and np.all(r <= op.r_out)
     assert np.all(np.isfinite(vg)) and np.all(np.isfinite(q))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("L,si,drive", [(1, 0, 1), (1, 1, 1), (4, 0, 2), (8, 1, 1), (16, 0, 1)])
+def test_m0_only_truncation_matches_oracle(imrp, prec, L, si, drive):
+    """The paper's truncation (Sec. 3: m = 0 terms only; with l_max = 1 the printed
+    cos t cos t' kernel), self image on and off, with a strong impulse drive."""
+    n = 3001
+    x, v = workload_state(BASE, N=n)
+    p, op = _pair(imrp, BASE, n, precision=prec, l_max=L, m0_only=1, self_image=si,
+                  drive_kind=drive, V_volts=200.0)
+    op.m0_only = 1
+    with imrp.Sim(p) as sim:
+        sim.load(x, v)
+        E = sim.field()
+        q, _ = sim.step(3)
+        xg, vg = sim.particles()
+    Eo = oracle.field_scan(op, x, u=oracle.drive(op, 0))
+    assert _rel(E, Eo) < TOL[prec]
+    xo, vo, qo, _, _ = oracle.run(op, x, v, 3)
+    assert _rel(vg - v, vo - v) < 10 * TOL[prec]
+    np.testing.assert_allclose(q, qo, rtol=10 * TOL[prec], atol=10 * TOL[prec] * np.max(np.abs(qo)))
