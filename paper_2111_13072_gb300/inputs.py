@@ -72,6 +72,9 @@ WORKLOADS = {
                              steps=2000, precision=0, seed=0),
     "mixed_n2e6_l16": Workload("mixed_n2e6_l16", N=2000000, l_max=16, T_e_eV=3.0, n_e_m3=1e16,
                                steps=20000, precision=1, seed=0),
+    # profiling size of the l_max = 24 case (a few GB on the device)
+    "mixed_n4e6_l24": Workload("mixed_n4e6_l24", N=4000000, l_max=24, T_e_eV=2.0, n_e_m3=1e16,
+                               outer_debye=40.0, steps=5000, precision=1, seed=0),
     "mixed_n1.6e7_l24": Workload("mixed_n1.6e7_l24", N=16000000, l_max=24, T_e_eV=2.0,
                                  n_e_m3=1e16, outer_debye=40.0, steps=5000, precision=1, seed=0),
 }
