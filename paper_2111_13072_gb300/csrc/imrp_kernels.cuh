@@ -227,10 +227,11 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   const int64_t tile = int64_t(blockIdx.x) * wpb + warp;
   const int64_t ntiles = (a.n + 31) >> 5;
   if (tile >= ntiles) return;  // warp-uniform; no block-wide barrier below
-  V4* coefA = reinterpret_cast<V4*>(smem_raw) + size_t(warp) * NE;
-  V2* coefB = reinterpret_cast<V2*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * NE) + size_t(warp) * NE;
-  T* sc = reinterpret_cast<T*>(reinterpret_cast<V2*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * NE) +
-                               size_t(wpb) * NE) + size_t(warp) * NC;
+  constexpr int CH = chunk_cap(L);
+  V4* coefA = reinterpret_cast<V4*>(smem_raw) + size_t(warp) * CH;
+  V2* coefB = reinterpret_cast<V2*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * CH) + size_t(warp) * CH;
+  T* sc = reinterpret_cast<T*>(reinterpret_cast<V2*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * CH) +
+                               size_t(wpb) * CH) + size_t(warp) * NC;
   const int64_t g = tile / kTilesPerGroup;
   const double u_drive = a.st->u;
   const T kick = T(a.st->kick);
@@ -257,11 +258,25 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     }
   }
   __syncwarp();
-  // ---- phase 2: gradient coefficients, scaled by -pf, x2 for m > 0
-  {
-    const T mpf = T(-a.pf);
-    const EntryRec* etab = g_ent + ent_off(L);
-    for (int k = lane; k < NE; k += 32) {
+  // ---- phase 3: the particle of this lane
+  const int64_t j = tile * 32 + lane;
+  const bool valid = j < a.n;
+  T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
+  const T r2 = X * X + Y * Y + Z * Z;
+  const T ir2 = T(1) / r2;
+  const T ir = rsqrt_t(r2);
+  T Ex = T(0), Ey = T(0), Ez = T(0);
+  T Fx = T(0), Fy = T(0), Fz = T(0);  // second accumulator chain (Im parts)
+
+  // ---- far field, in column chunks of at most kChunk gradient entries: the
+  // entries of a chunk are formed in shared memory (phase 2, scaled by -pf,
+  // x2 for m > 0) and evaluated at once; the recurrence's diagonal term is
+  // carried from chunk to chunk in registers.
+  const T mpf = T(-a.pf);
+  const EntryRec* etab = g_ent + ent_off(L);
+  auto build = [&](int k0, int k1) {
+    __syncwarp();
+    for (int k = k0 + int(lane); k < k1; k += 32) {
       const EntryRec er = etab[k];
       T c[6];
 #pragma unroll
@@ -285,81 +300,86 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       V2 cb;
       ca.x = w * dxr; ca.y = w * dyr; ca.z = w * dzr; ca.w = w * dxi;
       cb.x = w * dyi; cb.y = w * dzi;
-      coefA[k] = ca;
-      coefB[k] = cb;
+      coefA[k - k0] = ca;
+      coefB[k - k0] = cb;
     }
-  }
-  __syncwarp();
+    __syncwarp();
+  };
 
-  // ---- phase 3: the particle of this lane
-  const int64_t j = tile * 32 + lane;
-  const bool valid = j < a.n;
-  T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
-  const T r2 = X * X + Y * Y + Z * Z;
-  const T ir2 = T(1) / r2;
-  const T ir = rsqrt_t(r2);
-  T Ex = T(0), Ey = T(0), Ez = T(0);
-  T Fx = T(0), Fy = T(0), Fz = T(0);  // second accumulator chain (Im parts)
-
-  // far field, multipole part: sum over Is_l^m(x), 1 <= l <= L+1
+  if constexpr (!chunked(L)) build(0, NI + NR);  // all entries of both parts at once
+  // multipole part: sum over Is_l^m(x), 1 <= l <= L+1
   {
     const T Zir2 = Z * ir2;
     T dr = ir, di = T(0);
+    constexpr int QI = chunked(L) ? nchunkI(L) : 1;
 #pragma unroll
-    for (int m = 0; m <= L + 1; ++m) {
-      if (m > 0) {
-        const T c = tb.dg[m];
-        const T ex = c * X * ir2, ey = c * Y * ir2;
-        const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
-        dr = nr;
-        di = ni;
-      }
-      T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+    for (int q = 0; q < QI; ++q) {
+      const int m0 = chunked(L) ? chunkI(L, q) : 0, m1 = chunked(L) ? chunkI(L, q + 1) : L + 2;
+      const int k0 = chunked(L) ? offI(L, m0) : 0;
+      if constexpr (chunked(L)) build(k0, offI(L, m1));
 #pragma unroll
-      for (int l = m; l <= L + 1; ++l) {
-        if (l > m) {
-          const T A = tb.a[l * kTabL + m] * Zir2, B = tb.b[l * kTabL + m] * ir2;
-          const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
-          c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+      for (int m = m0; m < m1; ++m) {
+        if (m > 0) {
+          const T c = tb.dg[m];
+          const T ex = c * X * ir2, ey = c * Y * ir2;
+          const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
+          dr = nr;
+          di = ni;
         }
-        if (l >= 1) {
-          const V4 ca = coefA[idxI(L, l, m)];
-          Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
-          if (m > 0) {
-            const V2 cb = coefB[idxI(L, l, m)];
-            Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+        T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+#pragma unroll
+        for (int l = m; l <= L + 1; ++l) {
+          if (l > m) {
+            const T A = tb.a[l * kTabL + m] * Zir2, B = tb.b[l * kTabL + m] * ir2;
+            const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
+            c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+          }
+          if (l >= 1) {
+            const V4 ca = coefA[idxI(L, l, m) - k0];
+            Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
+            if (m > 0) {
+              const V2 cb = coefB[idxI(L, l, m) - k0];
+              Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+            }
           }
         }
       }
     }
   }
-  // far field, local part: sum over Rs_l^m(x / r_out), 0 <= l <= L-1
+  // local part: sum over Rs_l^m(x / r_out), 0 <= l <= L-1
   {
     const T Xs = X * a.rho_inv, Ys = Y * a.rho_inv, Zs = Z * a.rho_inv;
     const T rs2 = r2 * a.rho_inv * a.rho_inv;
     T dr = T(1), di = T(0);
+    constexpr int QR = chunked(L) ? nchunkR(L) : 1;
 #pragma unroll
-    for (int m = 0; m <= L - 1; ++m) {
-      if (m > 0) {
-        const T c = tb.dg[m];
-        const T ex = c * Xs, ey = c * Ys;
-        const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
-        dr = nr;
-        di = ni;
-      }
-      T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+    for (int q = 0; q < QR; ++q) {
+      const int m0 = chunked(L) ? chunkR(L, q) : 0, m1 = chunked(L) ? chunkR(L, q + 1) : L;
+      const int k0 = chunked(L) ? NI + offR(L, m0) : 0;
+      if constexpr (chunked(L)) build(k0, NI + offR(L, m1));
 #pragma unroll
-      for (int l = m; l <= L - 1; ++l) {
-        if (l > m) {
-          const T A = tb.a[l * kTabL + m] * Zs, B = tb.b[l * kTabL + m] * rs2;
-          const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
-          c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
-        }
-        const V4 ca = coefA[NI + idxR(L, l, m)];
-        Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
+      for (int m = m0; m < m1; ++m) {
         if (m > 0) {
-          const V2 cb = coefB[NI + idxR(L, l, m)];
-          Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+          const T c = tb.dg[m];
+          const T ex = c * Xs, ey = c * Ys;
+          const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
+          dr = nr;
+          di = ni;
+        }
+        T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+#pragma unroll
+        for (int l = m; l <= L - 1; ++l) {
+          if (l > m) {
+            const T A = tb.a[l * kTabL + m] * Zs, B = tb.b[l * kTabL + m] * rs2;
+            const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
+            c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+          }
+          const V4 ca = coefA[NI + idxR(L, l, m) - k0];
+          Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
+          if (m > 0) {
+            const V2 cb = coefB[NI + idxR(L, l, m) - k0];
+            Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+          }
         }
       }
     }
