@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s at N=2e6,l_max=16 (mixed vs FP64); served spectra p50/p99"
 UNIT = "particle-steps/s"
-LAUNCHES_PER_STEP = 18  # 12 sort + reorder + moments + tile scan + group scan + finalize + field
+LAUNCHES_PER_STEP = 19  # 12 sort + reorder + moments + tile scan + 2 group scan + finalize + field
 
 
 def workload_desc(w):

@@ -167,7 +167,8 @@ int imrp_get_info(const imrp_ctx* ctx, imrp_info* info);
 /* Stage timing. Runs n_steps steps launched one by one (no CUDA graph) with a
  * CUDA event pair around each stage on the context's stream, and writes the
  * summed device time of each stage in milliseconds to ms[IMRP_N_STAGES]:
- * 0 radix sort, 1 reorder, 2 tile moments, 3 scans + finalize,
+ * 0 radix sort, 1 reorder, 2 tile moments with the in-group scans,
+ * 3 group scan + finalize,
  * 4 field gather + push. The steps are real steps (they advance the state and
  * are recorded like imrp_step). */
 #define IMRP_N_STAGES 5
@@ -179,10 +180,11 @@ int imrp_profile_steps(imrp_ctx* ctx, int64_t n_steps, double* ms);
  *
  * imrp_autotune times, on the loaded particles and with field evaluations only
  * (the state does not advance), the field kernel at 8, 4, 2 and 1 warps per
- * CTA and the tile scan at 8, 16 and 32 components per block, and keeps the
- * fastest of each for the context. wpb_out / scan_cpb_out (may be NULL)
- * receive the choices. Errors: IMRP_E_STATE (nothing loaded), IMRP_E_CUDA. */
-int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* scan_cpb_out);
+ * CTA and the group scan (the FP64 scan over the 1024-particle scan groups)
+ * at 16, 32 and 64 groups per segment at least, and keeps the fastest of each
+ * for the context. wpb_out / gseg_out (may be NULL) receive the choices.
+ * Errors: IMRP_E_STATE (nothing loaded), IMRP_E_CUDA. */
+int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* gseg_out);
 
 /* A batch steps several loaded contexts of one device together: every step of
  * every context is captured into one CUDA graph (each context on its own

@@ -79,7 +79,7 @@ struct imrp_ctx {
   int nc = 0;
   int64_t ntiles = 0, ngroups = 0;
   int wpb = 8;
-  int scan_cpb = 16;  // components per block of the tile scan
+  int gseg = 32;  // least groups per segment of the group scan
   // streams / graphs
   cudaStream_t own_stream = nullptr, stream = nullptr;
   cudaGraphExec_t graph2 = nullptr;
@@ -90,7 +90,8 @@ struct imrp_ctx {
   int cur = 0;
   uint32_t *key0 = nullptr, *idx0 = nullptr, *key1 = nullptr, *idx1 = nullptr, *hist = nullptr;
   void *agg = nullptr, *pfx = nullptr, *gbase = nullptr, *tot = nullptr, *eout = nullptr;
-  double *gagg = nullptr, *totd = nullptr;
+  double *gagg = nullptr, *totd = nullptr, *gswork = nullptr;
+  unsigned* gsticket = nullptr;
   double *qhist = nullptr, *uhist = nullptr;
   int64_t hcap = 0;
   double* stage = nullptr;  // [cap][6] FP64 staging for load / readback
@@ -130,11 +131,13 @@ void free_all(imrp_ctx* c) {
     cudaFree(c->id_buf[b]); c->id_buf[b] = nullptr;
   }
   void* ps[] = {c->key0, c->idx0, c->key1, c->idx1, c->hist, c->agg, c->pfx, c->gbase, c->tot,
-                c->eout, c->gagg, c->totd, c->qhist, c->uhist, c->stage, c->st, c->derr, c->dft};
+                c->eout, c->gagg, c->totd, c->gswork, c->gsticket, c->qhist, c->uhist, c->stage, c->st,
+                c->derr, c->dft};
   for (void* p : ps) cudaFree(p);
   c->key0 = c->idx0 = c->key1 = c->idx1 = c->hist = nullptr;
   c->agg = c->pfx = c->gbase = c->tot = c->eout = nullptr;
-  c->gagg = c->totd = c->qhist = c->uhist = c->stage = c->dft = nullptr;
+  c->gagg = c->totd = c->gswork = c->qhist = c->uhist = c->stage = c->dft = nullptr;
+  c->gsticket = nullptr;
   c->st = nullptr;
   c->derr = nullptr;
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -195,15 +198,15 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   MomArgs<T> ma;
   ma.x = S[0]; ma.y = S[1]; ma.z = S[2];
   ma.n = n;
+  ma.rho = T(ctx->r_out);
   ma.rho_inv = T(1.0 / ctx->r_out);
   ma.agg = static_cast<T*>(ctx->agg);
   if (ev) cudaEventRecord(ev[2], s);
   ks->moments(ma, s);
   if (ev) cudaEventRecord(ev[3], s);
-  launch_tile_scan<T>(static_cast<T*>(ctx->agg), static_cast<T*>(ctx->pfx), ctx->gagg, ctx->ntiles,
-                      ctx->nc, s, ctx->scan_cpb);
-  launch_group_scan<T>(ctx->gagg, static_cast<T*>(ctx->gbase), static_cast<T*>(ctx->tot), ctx->totd,
-                       ctx->ngroups, ctx->nc, s);
+  launch_tile_scan<T>(static_cast<T*>(ctx->agg), static_cast<T*>(ctx->pfx), ctx->gagg, ctx->ntiles, ctx->nc, s);
+  launch_group_scan<T>(ctx->gagg, ctx->gswork, ctx->gsticket, static_cast<T*>(ctx->gbase),
+                       static_cast<T*>(ctx->tot), ctx->totd, ctx->ngroups, ctx->nc, ctx->gseg, s);
   FinalizeArgs fa;
   fa.st = ctx->st;
   fa.totd = ctx->totd;
@@ -321,8 +324,9 @@ size_t footprint_bytes(int64_t N, int L, int prec) {
   b += 2 * (6 * N * es + N * 4);                    // state ping-pong + ids
   b += 4 * size_t(N) * 4;                           // keys and slots
   b += size_t(256 * sort_blocks(N) + 256) * 4;      // histogram
-  b += 2 * size_t(ntiles * nc) * es;                // tile sums and in-group scans
+  b += 2 * size_t(tile_stride(ntiles) * nc) * es;   // tile sums and in-group scans
   b += size_t(ngroups * nc) * (es + 8) + size_t(nc) * (es + 8);
+  b += size_t(gs_work_doubles(int(nc))) * 8 + size_t(gs_col_blocks(int(nc))) * 4;
   b += 3 * size_t(N) * es + 6 * size_t(N) * 8;      // field output, staging
   b += sizeof(StepState) + sizeof(int);
   return b;
@@ -343,12 +347,15 @@ int alloc_ctx(imrp_ctx* ctx) {
   CK(cudaMalloc(&ctx->key1, N * sizeof(uint32_t)));
   CK(cudaMalloc(&ctx->idx1, N * sizeof(uint32_t)));
   CK(cudaMalloc(&ctx->hist, (256 * sort_blocks(N) + 256) * sizeof(uint32_t)));
-  CK(cudaMalloc(&ctx->agg, ntiles * nc * es));
-  CK(cudaMalloc(&ctx->pfx, ntiles * nc * es));
+  CK(cudaMalloc(&ctx->agg, tile_stride(ntiles) * nc * es));
+  CK(cudaMalloc(&ctx->pfx, tile_stride(ntiles) * nc * es));
   CK(cudaMalloc(&ctx->gbase, ngroups * nc * es));
   CK(cudaMalloc(&ctx->tot, nc * es));
   CK(cudaMalloc(&ctx->gagg, ngroups * nc * sizeof(double)));
   CK(cudaMalloc(&ctx->totd, nc * sizeof(double)));
+  CK(cudaMalloc(&ctx->gswork, gs_work_doubles(nc) * sizeof(double)));
+  CK(cudaMalloc(&ctx->gsticket, gs_col_blocks(nc) * sizeof(unsigned)));
+  CK(cudaMemset(ctx->gsticket, 0, gs_col_blocks(nc) * sizeof(unsigned)));
   CK(cudaMalloc(&ctx->eout, 3 * N * es));
   CK(cudaMalloc(&ctx->stage, 6 * N * sizeof(double)));
   CK(cudaMalloc(&ctx->st, sizeof(StepState)));
@@ -689,7 +696,7 @@ int time_stage(imrp_ctx* ctx, int stage, int reps, float* ms) {
 
 }  // namespace
 
-extern "C" int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* scan_cpb_out) {
+extern "C" int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* gseg_out) {
   if (!ctx) return IMRP_E_INVAL;
   if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "autotune before load");
   const int reps = 3;
@@ -709,22 +716,22 @@ extern "C" int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* scan_cpb_out) {
     }
     ctx->wpb = best_w;
   }
-  // tile scan: components per block
+  // group scan: least groups per segment
   {
-    int best_c = ctx->scan_cpb;
+    int best_c = ctx->gseg;
     float best = 1e30f;
-    for (int c : {8, 16, 32}) {
-      ctx->scan_cpb = c;
+    for (int c : {16, 32, 64}) {
+      ctx->gseg = c;
       float ms = 0.f;
       int rc = time_stage(ctx, 3, reps, &ms);
       if (rc) return rc;
       if (ms < best) { best = ms; best_c = c; }
     }
-    ctx->scan_cpb = best_c;
+    ctx->gseg = best_c;
   }
   if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
   if (wpb_out) *wpb_out = ctx->wpb;
-  if (scan_cpb_out) *scan_cpb_out = ctx->scan_cpb;
+  if (gseg_out) *gseg_out = ctx->gseg;
   return check_err(ctx);
 }
 

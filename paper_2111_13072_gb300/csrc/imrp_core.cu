@@ -242,125 +242,188 @@ void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, 
 // ============================================================================
 // Scans of the tile moments (FP64 accumulation)
 // ============================================================================
-// Grid (ngroups, ceil(nc / kScanComps)), 128 threads = the 128 tiles of a
-// group. For each of the block's kScanComps components u: a block scan over
-// the group's tiles of agg[u][tile], written as the exclusive prefix for Rs
-// components (tiles before t) and the exclusive suffix for Is components
-// (tiles after t), each summed in its own direction so that no partial sum is
-// formed as a difference of larger sums. Warp scans run in T for all
-// components at once (independent shuffles) and warp totals are combined in
-// T (the stored in-group result is T); the group total goes to gagg[g][u] in
-// FP64. (FP64 arithmetic per thread is kept out of this kernel: the FP64 rate
-// of the GPU is a small fraction of its FP32 rate.)
+// Tile scan: the in-group scans of the tile sums agg[u][tile] over the tw
+// tiles of whole groups (row stride ts). One warp task = 128 consecutive tiles of
+// one row = 4 groups; lane l holds tiles 4l..4l+3 (one vector load), so a
+// group is 8 lanes. Each lane sums its 4 tiles in order, an 8-lane shuffle
+// scan gives the lane's offset, and the lane writes its 4 results with one
+// vector store. Rs rows (u even): exclusive prefix towards higher tiles; Is
+// rows (u odd): exclusive suffix towards lower tiles; each summed in its own
+// direction (no total minus a partial sum, which would cancel). The group
+// total (the inclusive sum at the far end) goes to gagg[g][u] in FP64. Each
+// warp takes kTsTasks consecutive tasks and issues their loads first.
+// ============================================================================
+constexpr int kTsTasks = 4;
 
-// kScanComps (components per block) is a template parameter, even, so that the
-// component parity (Rs / Is) is the parity of cc; the autotuner picks it.
-template <class T, int kScanComps>
-__global__ void __launch_bounds__(kTilesPerGroup) k_tile_scan(const T* __restrict__ agg, T* __restrict__ pfx,
-                                                             double* __restrict__ gagg, int64_t ntiles, int nc) {
-  constexpr int NW = kTilesPerGroup / 32;
-  __shared__ T ws[kScanComps][NW];
-  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t t = int64_t(blockIdx.x) * kTilesPerGroup + threadIdx.x;
-  const bool ok = t < ntiles;
-  const int c0 = blockIdx.y * kScanComps;
-  T v[kScanComps], s[kScanComps];
+template <class T>
+__global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T* __restrict__ pfx,
+                                                   double* __restrict__ gagg, int64_t tw, int64_t ts, int nc) {
+  using V4 = typename Vec4<T>::type;
+  const int lane = threadIdx.x & 31, r = lane & 7;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nseg = (tw + 127) / 128;  // 128-tile segments per row
+  const int64_t ntask = nseg * nc;
+  const int64_t t0 = warp * kTsTasks;
+  if (t0 >= ntask) return;  // warp-uniform
+  const int64_t u0 = t0 / nseg, s0 = t0 - u0 * nseg;
+  V4 v[kTsTasks];
+  {
+    int64_t u = u0, sg = s0;
 #pragma unroll
-  for (int cc = 0; cc < kScanComps; ++cc) {
-    const int c = c0 + cc;
-    v[cc] = (ok && c < nc) ? agg[int64_t(c) * ntiles + t] : T(0);
-    s[cc] = v[cc];
-  }
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-    for (int cc = 0; cc < kScanComps; ++cc) {
-      if (cc & 1) {  // Is: inclusive suffix within the warp
-        const T y = __shfl_down_sync(0xffffffffu, s[cc], o);
-        if (lane + o < 32) s[cc] += y;
-      } else {       // Rs: inclusive prefix within the warp
-        const T y = __shfl_up_sync(0xffffffffu, s[cc], o);
-        if (lane >= unsigned(o)) s[cc] += y;
+    for (int k = 0; k < kTsTasks; ++k) {
+      const int64_t tile = sg * 128 + 4 * lane;
+      if (t0 + k < ntask && tile < tw) {
+        v[k] = *reinterpret_cast<const V4*>(agg + u * ts + tile);
+      } else {
+        v[k].x = v[k].y = v[k].z = v[k].w = T(0);
       }
+      if (++sg == nseg) { sg = 0; ++u; }
     }
   }
+  int64_t u = u0, sg = s0;
 #pragma unroll
-  for (int cc = 0; cc < kScanComps; ++cc)
-    if ((cc & 1) ? lane == 0 : lane == 31) ws[cc][warp] = s[cc];
-  __syncthreads();
+  for (int k = 0; k < kTsTasks; ++k) {
+    if (t0 + k >= ntask) break;  // warp-uniform
+    const int64_t tile = sg * 128 + 4 * lane;
+    const int64_t g = tile / 32;
+    V4 o;
+    if (u & 1) {  // Is: exclusive suffix
+      const T f2 = v[k].w, f1 = f2 + v[k].z, f0 = f1 + v[k].y, sum = f0 + v[k].x;
+      T x = __shfl_down_sync(0xffffffffu, sum, 1, 8);
+      if (r == 7) x = T(0);
 #pragma unroll
-  for (int cc = 0; cc < kScanComps; ++cc) {
-    const int c = c0 + cc;
-    if (c >= nc) break;
-    T off = T(0);
+      for (int d = 1; d < 8; d <<= 1) {
+        const T y = __shfl_down_sync(0xffffffffu, x, d, 8);
+        if (r + d < 8) x += y;
+      }
+      o.x = x + f0; o.y = x + f1; o.z = x + f2; o.w = x;
+      if (r == 0 && tile < tw) gagg[g * nc + u] = double(x + sum);
+    } else {      // Rs: exclusive prefix
+      const T e1 = v[k].x, e2 = e1 + v[k].y, e3 = e2 + v[k].z, sum = e3 + v[k].w;
+      T x = __shfl_up_sync(0xffffffffu, sum, 1, 8);
+      if (r == 0) x = T(0);
 #pragma unroll
-    for (int w = 0; w < NW; ++w)
-      if ((cc & 1) ? unsigned(w) > warp : unsigned(w) < warp) off += ws[cc][w];
-    if (ok) pfx[int64_t(c) * ntiles + t] = off + (s[cc] - v[cc]);
-    if (threadIdx.x == 0) {
-      double all = 0.0;  // the group total in FP64 (one thread per block)
-#pragma unroll
-      for (int w = 0; w < NW; ++w) all += double(ws[cc][w]);
-      gagg[int64_t(blockIdx.x) * nc + c] = all;
+      for (int d = 1; d < 8; d <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, x, d, 8);
+        if (r >= d) x += y;
+      }
+      o.x = x; o.y = x + e1; o.z = x + e2; o.w = x + e3;
+      if (r == 7 && tile < tw) gagg[g * nc + u] = double(x + sum);
     }
+    if (tile < tw) *reinterpret_cast<V4*>(pfx + u * ts + tile) = o;
+    if (++sg == nseg) { sg = 0; ++u; }
   }
 }
 
 template <class T>
-void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s, int cpb) {
-  const int64_t ng = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
-  const int c = cpb == 8 ? 8 : (cpb == 32 ? 32 : 16);
-  dim3 grid(unsigned(ng), unsigned((nc + c - 1) / c));
-  if (c == 8) k_tile_scan<T, 8><<<grid, kTilesPerGroup, 0, s>>>(agg, pfx, gagg, ntiles, nc);
-  else if (c == 32) k_tile_scan<T, 32><<<grid, kTilesPerGroup, 0, s>>>(agg, pfx, gagg, ntiles, nc);
-  else k_tile_scan<T, 16><<<grid, kTilesPerGroup, 0, s>>>(agg, pfx, gagg, ntiles, nc);
+void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s) {
+  const int64_t tw = tiles_whole(ntiles), ts = tile_stride(ntiles);
+  const int64_t warps = ((tw + 127) / 128 * nc + kTsTasks - 1) / kTsTasks;
+  const int64_t blocks = (warps * 32 + 255) / 256;
+  if (blocks > 0) k_tile_scan<T><<<unsigned(blocks), 256, 0, s>>>(agg, pfx, gagg, tw, ts, nc);
 }
 
-// Grid ceil(nc/32), 256 threads: warp w owns a contiguous segment of groups.
-// gbase: Rs components -> exclusive prefix over earlier groups; Is components
-// -> exclusive suffix over later groups (summed from the end). tot/totd: totals.
+// ============================================================================
+// Group scan. Input: the FP64 totals gagg[g][u] of the scan groups (written
+// by the moments kernel). Output: gbase[g][u] = the sum over the earlier
+// groups (Rs components, u even) or over the later groups (Is components, u
+// odd), each summed in its own direction, and the totals tot / totd.
+// The groups are cut into nseg segments of G groups (G a multiple of 8);
+// CTA (column block b, segment s) handles components 32 b + lane with its 8
+// warps splitting the segment. k_group_sums forms the warp and segment sums;
+// the last CTA of a column block to finish (an atomic ticket, no waiting)
+// scans the segment sums of that block in a fixed order, so the result is
+// the same whichever CTA finishes last. k_group_bases then walks each warp's
+// groups once more and writes the bases.
+// Work space w (FP64): [nseg][8][nc] warp sums, then [nseg][nc] segment sums,
+// then [nseg][nc] segment bases.
+// ============================================================================
 template <class T>
-__global__ void __launch_bounds__(256) k_group_scan(const double* __restrict__ gagg, T* __restrict__ gbase,
-                                                   T* __restrict__ tot, double* __restrict__ totd,
-                                                   int64_t ngroups, int nc) {
-  __shared__ double ws[8][32];
+__global__ void __launch_bounds__(kGsWarps * 32) k_group_sums(const double* __restrict__ gagg,
+                                                              double* __restrict__ w, unsigned* __restrict__ ticket,
+                                                              T* __restrict__ tot, double* __restrict__ totd,
+                                                              int64_t ngroups, int nc, int64_t G, int nseg) {
+  __shared__ double ws[kGsWarps][32];
+  __shared__ bool last;
   const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
   const bool okc = c < nc;
-  const int64_t seg = (ngroups + 7) / 8;
-  const int64_t g0 = int64_t(warp) * seg < ngroups ? int64_t(warp) * seg : ngroups;
-  const int64_t g1 = g0 + seg < ngroups ? g0 + seg : ngroups;
+  const int seg = blockIdx.y;
+  double* wsum = w;
+  double* ssum = w + int64_t(kGsMaxSeg) * kGsWarps * nc;
+  double* sbase = ssum + int64_t(kGsMaxSeg) * nc;
+  const int64_t per = G / kGsWarps;
+  const int64_t g0 = int64_t(seg) * G + warp * per;
+  const int64_t g1 = g0 + per < ngroups ? g0 + per : ngroups;
   double run = 0.0;
-  for (int64_t g = g0; g < g1; ++g)
-    if (okc) run += gagg[g * nc + c];
+  if (okc) {
+#pragma unroll 4
+    for (int64_t g = g0; g < g1; ++g) run += gagg[g * nc + c];
+    wsum[(int64_t(seg) * kGsWarps + warp) * nc + c] = run;
+  }
   ws[warp][lane] = run;
   __syncthreads();
-  const bool suffix = (c & 1) != 0;
-  double off = 0.0, all = 0.0;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    const double v = ws[w][lane];
-    if (suffix ? unsigned(w) > warp : unsigned(w) < warp) off += v;
-    all += v;
-  }
-  run = off;
-  if (okc) {
-    for (int64_t k = 0; k < g1 - g0; ++k) {
-      const int64_t g = suffix ? g1 - 1 - k : g0 + k;
-      gbase[g * nc + c] = T(run);
-      run += gagg[g * nc + c];
-    }
-  }
   if (warp == 0 && okc) {
+    double sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < kGsWarps; ++k) sum += ws[k][lane];
+    ssum[int64_t(seg) * nc + c] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&ticket[blockIdx.x], 1u) == unsigned(nseg - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (warp == 0 && okc) {
+    double all = 0.0;
+    const bool suffix = (c & 1) != 0;
+    for (int k = 0; k < nseg; ++k) {
+      const int s2 = suffix ? nseg - 1 - k : k;
+      sbase[int64_t(s2) * nc + c] = all;
+      all += __ldcg(ssum + int64_t(s2) * nc + c);
+    }
     tot[c] = T(all);
     totd[c] = all;
+  }
+  if (threadIdx.x == 0) ticket[blockIdx.x] = 0u;  // ready for the next step
+}
+
+template <class T>
+__global__ void __launch_bounds__(kGsWarps * 32) k_group_bases(const double* __restrict__ gagg,
+                                                               const double* __restrict__ w, T* __restrict__ gbase,
+                                                               int64_t ngroups, int nc, int64_t G) {
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  if (c >= nc) return;  // no barrier below
+  const int seg = blockIdx.y;
+  const bool suffix = (c & 1) != 0;
+  const double* wsum = w;
+  const double* sbase = w + int64_t(kGsMaxSeg) * (kGsWarps + 1) * nc;
+  double run = sbase[int64_t(seg) * nc + c];
+#pragma unroll
+  for (int k = 0; k < kGsWarps; ++k)
+    if (suffix ? unsigned(k) > warp : unsigned(k) < warp) run += wsum[(int64_t(seg) * kGsWarps + k) * nc + c];
+  const int64_t per = G / kGsWarps;
+  const int64_t g0 = int64_t(seg) * G + warp * per;
+  const int64_t g1 = g0 + per < ngroups ? g0 + per : ngroups;
+#pragma unroll 4
+  for (int64_t k = 0; k < g1 - g0; ++k) {
+    const int64_t g = suffix ? g1 - 1 - k : g0 + k;
+    gbase[g * nc + c] = T(run);
+    run += gagg[g * nc + c];
   }
 }
 
 template <class T>
-void launch_group_scan(const double* gagg, T* gbase, T* tot, double* totd, int64_t ngroups, int nc,
-                       cudaStream_t s) {
-  k_group_scan<T><<<unsigned((nc + 31) / 32), 256, 0, s>>>(gagg, gbase, tot, totd, ngroups, nc);
+void launch_group_scan(const double* gagg, double* work, unsigned* ticket, T* gbase, T* tot, double* totd,
+                       int64_t ngroups, int nc, int gseg, cudaStream_t s) {
+  if (ngroups <= 0) return;
+  const int64_t G = gs_seg_len(ngroups, gseg);
+  const int nseg = int(gs_nseg(ngroups, gseg));
+  dim3 grid(unsigned(gs_col_blocks(nc)), unsigned(nseg));
+  k_group_sums<T><<<grid, kGsWarps * 32, 0, s>>>(gagg, work, ticket, tot, totd, ngroups, nc, G, nseg);
+  k_group_bases<T><<<grid, kGsWarps * 32, 0, s>>>(gagg, work, gbase, ngroups, nc, G);
 }
 
 // ============================================================================
@@ -447,8 +510,9 @@ void launch_dft(const double* q, const double* u, int64_t ns, double dt, double 
                                int*, cudaStream_t);                                                \
   template void launch_scatter_by_id<T>(const T* const*, int, const uint32_t*, double*, int64_t,   \
                                         cudaStream_t);                                             \
-  template void launch_tile_scan<T>(const T*, T*, double*, int64_t, int, cudaStream_t, int);       \
-  template void launch_group_scan<T>(const double*, T*, T*, double*, int64_t, int, cudaStream_t);
+  template void launch_tile_scan<T>(const T*, T*, double*, int64_t, int, cudaStream_t);                \
+  template void launch_group_scan<T>(const double*, double*, unsigned*, T*, T*, double*, int64_t, int, \
+                                     int, cudaStream_t);
 IMRP_INST_CORE(float)
 IMRP_INST_CORE(double)
 

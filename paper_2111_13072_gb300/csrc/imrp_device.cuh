@@ -110,15 +110,46 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-constexpr int kTilesPerGroup = 128;  // tiles (of 32 particles) per scan group
+// Scan groups: one group = 32 tiles (1024 particles), scanned by one warp
+// with lane = tile. Sums inside a group are formed in the working precision
+// T; sums across groups in FP64 (the group scan below).
+constexpr int kTilesPerGroup = 32;
+// Tiles in whole groups, and the row stride (in tiles) of the [component]
+// [tile] arrays: whole groups plus kTilePad tiles, so that rows start at
+// staggered offsets (a stride that is a multiple of 256 bytes sends the rows
+// read for one tile to the same memory channels) while every row stays
+// aligned for 4-wide vector access.
+constexpr int kTilePad = 4;
+__host__ __device__ constexpr int64_t tiles_whole(int64_t ntiles) { return (ntiles + 31) / 32 * 32; }
+__host__ __device__ constexpr int64_t tile_stride(int64_t ntiles) { return tiles_whole(ntiles) + kTilePad; }
+
+// Group scan over the FP64 group totals: the groups are cut into at most
+// kGsMaxSeg segments of gs_seg_len groups, each segment summed by one CTA of
+// kGsWarps warps (32 components per CTA, one per lane).
+constexpr int kGsWarps = 8;
+constexpr int kGsMaxSeg = 64;
+__host__ __device__ inline int64_t gs_seg_len(int64_t ngroups, int gseg) {
+  int64_t G = (ngroups + kGsMaxSeg - 1) / kGsMaxSeg;
+  if (G < gseg) G = gseg;
+  return (G + kGsWarps - 1) / kGsWarps * kGsWarps;
+}
+__host__ __device__ inline int64_t gs_nseg(int64_t ngroups, int gseg) {
+  const int64_t G = gs_seg_len(ngroups, gseg);
+  return ngroups > 0 ? (ngroups + G - 1) / G : 0;
+}
+// FP64 work space of the group scan for nc components: per segment the
+// kGsWarps warp sums, the segment sum and the segment's base.
+__host__ __device__ constexpr int64_t gs_work_doubles(int nc) { return int64_t(kGsMaxSeg) * (kGsWarps + 2) * nc; }
+__host__ __device__ constexpr int gs_col_blocks(int nc) { return (nc + 31) / 32; }
 
 template <class T> struct MomArgs {
   const T* x;
   const T* y;
   const T* z;
   int64_t n;
+  T rho;       // r_out
   T rho_inv;   // 1 / r_out: regular harmonics use x / r_out so |Rs| <= 1
-  T* agg;      // [2 ncomp(L)][ntiles], component u = 2 e + s, s = 0 Rs, s = 1 Is
+  T* agg;      // [2 ncomp(L)][ntiles] tile sums, u = 2 e + s (s = 0 Rs, s = 1 Is)
 };
 
 // Entry tables of the gradient coefficients held in shared memory per warp.

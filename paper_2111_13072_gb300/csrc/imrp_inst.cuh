@@ -90,7 +90,7 @@ const PrologueInit g_prologue_init;
 template <class T, int L> void mom_launch(const MomArgs<T>& a, cudaStream_t s) {
   const int64_t per = kMomThreads * kMomPPT;
   const int64_t blocks = (a.n + per - 1) / per;
-  if (blocks > 0) k_moments<T, L><<<unsigned(blocks), kMomThreads, moments_smem<T>(), s>>>(a);
+  if (blocks > 0) k_moments<T, L><<<unsigned(blocks), kMomThreads, moments_smem<T, L>(), s>>>(a);
 }
 
 template <class T, int L> void field_launch(const FieldArgs<T>& a, int wpb, cudaStream_t s) {
@@ -110,7 +110,7 @@ template <class T, int L> int field_occ(int wpb) {
 
 template <class T, int L> cudaError_t set_attr() {
   cudaError_t e = cudaFuncSetAttribute(k_moments<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(moments_smem<T>()));
+                                       int(moments_smem<T, L>()));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_field<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(8 * field_smem_per_warp<T>(L) > 227 * 1024 ? 227 * 1024

@@ -38,13 +38,17 @@ void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, 
                           int64_t n, cudaStream_t s);
 
 // ---- scans (imrp_core.cu) ---------------------------------------------------
-// cpb: components per block, one of 8, 16, 32 (chosen by the autotuner)
+// in-group scans of agg[u][tile] into pfx (row stride tile_stride(ntiles)),
+// group totals into gagg[g][u] (FP64)
 template <class T>
-void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s,
-                      int cpb = 16);
+void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s);
+// group scan over gagg:
+// gseg: least number of groups per segment (16, 32 or 64; chosen by the
+// autotuner). work: gs_work_doubles(nc) doubles; ticket: gs_col_blocks(nc)
+// counters, zero before the first call (each call leaves them zero).
 template <class T>
-void launch_group_scan(const double* gagg, T* gbase, T* tot, double* totd, int64_t ngroups,
-                       int nc, cudaStream_t s);
+void launch_group_scan(const double* gagg, double* work, unsigned* ticket, T* gbase, T* tot, double* totd,
+                       int64_t ngroups, int nc, int gseg, cudaStream_t s);
 
 struct FinalizeArgs {
   StepState* st;

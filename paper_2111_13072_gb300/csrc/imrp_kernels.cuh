@@ -55,19 +55,29 @@ static __device__ uint16_t g_comp[kCompTotal];  // per component: l | (drive << 
 template <class T> __device__ __forceinline__ T rsqrt_t(T v);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double v) { return rsqrt(v); }
+template <class T> __device__ __forceinline__ T fma_t(T x, T y, T z);
+template <> __device__ __forceinline__ float fma_t<float>(float x, float y, float z) { return fmaf(x, y, z); }
+template <> __device__ __forceinline__ double fma_t<double>(double x, double y, double z) { return fma(x, y, z); }
 
 // Tile moments: the sums over each tile of 32 radius-sorted particles of
 // q Rs_l^m(x/r_out) and q Is_l^m(x), 1 <= l <= L (q = -1 per electron).
 // Two threads per tile, 16 particles each. The recurrences run column by
-// column (fixed m, rising l); the column sums stay in registers while the
-// thread walks its 16 particles, whose positions and diagonal terms
-// (Rs_m^m, Is_m^m) live in shared memory in a [particle][thread] layout
-// (conflict-free). The two halves of a tile are combined with one shuffle per
-// component. Output layout: agg[u][tile], u = 2 e + s (s = 0 Rs, s = 1 Is).
+// column (fixed m, rising l = m + j) in a rolled loop over m, so the code
+// stays small at any degree; the column sums stay in registers while the
+// thread walks its particles (two at a time: two independent recurrence
+// chains), whose scaled positions, r_out / r^2 and diagonal terms live in
+// shared memory in a [particle][thread] layout (conflict-free). The multipole
+// harmonics follow from the regular ones by the Kelvin relation
+//   Is_l^m(x) = Rs_l^m(x / r_out) * r_out^l / r^(2l+1),
+// the scale advancing by one factor r_out / r^2 per degree. At the end of a
+// column the two halves of each tile are combined with one shuffle per Rs/Is
+// pair (the even lane keeps the Rs sum, the odd lane the Is sum) and written:
+// agg[u][tile], u = 2 e + s (s = 0 Rs, s = 1 Is).
 constexpr int kMomThreads = 64;  // 32 tiles per CTA
 constexpr int kMomPPT = 16;      // particles per thread
+constexpr int kMomBreak = 2;     // steps between the column-end tests
 
-template <class T>
+template <class T, int L>
 __host__ __device__ constexpr size_t moments_smem() {
   return sizeof(T) * 7 * kMomPPT * (kMomThreads + 1);
 }
@@ -76,17 +86,18 @@ template <class T, int L>
 __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int S = kMomThreads + 1;  // padded row
-  T* sx = reinterpret_cast<T*>(smem_raw);
-  T* sy = sx + kMomPPT * S;
-  T* sz = sy + kMomPPT * S;
-  T* sRr = sz + kMomPPT * S;
+  T* sx = reinterpret_cast<T*>(smem_raw);  // x / r_out
+  T* sy = sx + kMomPPT * S;                // y / r_out
+  T* sz = sy + kMomPPT * S;                // z / r_out
+  T* sq = sz + kMomPPT * S;                // r_out / r^2
+  T* sRr = sq + kMomPPT * S;               // q Rs_m^m(x / r_out), real and imaginary
   T* sRi = sRr + kMomPPT * S;
-  T* sIr = sRi + kMomPPT * S;
-  T* sIi = sIr + kMomPPT * S;
+  T* ssc = sRi + kMomPPT * S;              // r_out^m / r^(2m+1)
   const Tables<T>& tb = tab<T>();
   const int th = threadIdx.x;
   const int64_t ntiles = (a.n + 31) >> 5;
   const int64_t pbase = int64_t(blockIdx.x) * (kMomThreads * kMomPPT);
+  const T ri = a.rho_inv;
   // stage 1024 particles: particle k of the CTA goes to row k % 16, column k / 16
 #pragma unroll 4
   for (int i = 0; i < kMomPPT; ++i) {
@@ -95,74 +106,96 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
     const bool valid = j < a.n;
     const T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
     const int o = (k % kMomPPT) * S + k / kMomPPT;
-    sx[o] = X; sy[o] = Y; sz[o] = Z;
-    const T q = valid ? T(-1) : T(0);
-    sRr[o] = q; sRi[o] = T(0);
-    sIr[o] = q * rsqrt_t(X * X + Y * Y + Z * Z); sIi[o] = T(0);
+    const T r2 = X * X + Y * Y + Z * Z;
+    sx[o] = X * ri; sy[o] = Y * ri; sz[o] = Z * ri;
+    sq[o] = a.rho / r2;
+    sRr[o] = valid ? T(-1) : T(0);
+    sRi[o] = T(0);
+    ssc[o] = rsqrt_t(r2);
   }
   __syncthreads();
+  const bool odd = (th & 1) != 0;
   const int64_t tile = int64_t(blockIdx.x) * (kMomThreads / 2) + (th >> 1);
-  const bool writer = (th & 1) == 0 && tile < ntiles;
-  const T ri = a.rho_inv;
+  // every tile of the whole groups is written (tiles past the particles hold
+  // zeros: their particles carry no charge)
+  const int64_t ts = tile_stride(ntiles);
+  T* const agg_t = a.agg + tile + (odd ? ts : 0);  // row u = 2 e + odd
 
-#pragma unroll
-  for (int m = 0; m <= L; ++m) {
-    constexpr int kMaxC = 4 * (L + 1);
-    const int nc = m == 0 ? 2 * L : 4 * (L - m + 1);  // components of this column
-    T acc[kMaxC];
-#pragma unroll
-    for (int k = 0; k < kMaxC; ++k) acc[k] = T(0);
 #pragma unroll 1
-    for (int p = 0; p < kMomPPT; ++p) {
-      const int o = p * S + th;
-      const T X = sx[o], Y = sy[o], Z = sz[o];
-      const T r2 = X * X + Y * Y + Z * Z;
-      const T ir2 = T(1) / r2;
-      const T Zs = Z * ri, rs2 = r2 * ri * ri, Zir2 = Z * ir2;
-      T dRr = sRr[o], dRi = sRi[o], dIr = sIr[o], dIi = sIi[o];
-      if (m > 0) {
-        const T c = tb.dg[m];
-        const T cx = c * X * ri, cy = c * Y * ri;
-        const T nr = cx * dRr - cy * dRi, ni = cx * dRi + cy * dRr;
-        dRr = nr; dRi = ni;
-        const T ex = c * X * ir2, ey = c * Y * ir2;
-        const T mr = ex * dIr - ey * dIi, mi = ex * dIi + ey * dIr;
-        dIr = mr; dIi = mi;
-        sRr[o] = dRr; sRi[o] = dRi; sIr[o] = dIr; sIi[o] = dIi;
-      }
-      T R1r = dRr, R1i = dRi, R0r = T(0), R0i = T(0);
-      T I1r = dIr, I1i = dIi, I0r = T(0), I0i = T(0);
+  for (int m = 0; m <= L; ++m) {
+    T acc[4 * (L + 1)];  // [j][R re, I re, R im, I im], l = m + j
 #pragma unroll
-      for (int l = m; l <= L; ++l) {
-        if (l > m) {
-          const T A = tb.a[l * kTabL + m], B = tb.b[l * kTabL + m];
-          const T az = A * Zs, br = B * rs2;
-          const T nr = az * R1r - br * R0r, ni = az * R1i - br * R0i;
-          R0r = R1r; R0i = R1i; R1r = nr; R1i = ni;
-          const T ai = A * Zir2, bi = B * ir2;
-          const T mr = ai * I1r - bi * I0r, mi = ai * I1i - bi * I0i;
-          I0r = I1r; I0i = I1i; I1r = mr; I1i = mi;
+    for (int k = 0; k < 4 * (L + 1); ++k) acc[k] = T(0);
+    T cA[L + 1], cB[L + 1];  // recurrence coefficients of this column
+#pragma unroll
+    for (int j = 1; j <= L; ++j) {
+      const bool in = m + j <= L;
+      cA[j] = in ? tb.a[(m + j) * kTabL + m] : T(0);
+      cB[j] = in ? tb.b[(m + j) * kTabL + m] : T(0);
+    }
+    const T dg = tb.dg[m];
+#pragma unroll 1
+    for (int p = 0; p < kMomPPT; p += 2) {
+      T Zs[2], rs2[2], q[2], R1r[2], R1i[2], R0r[2], R0i[2], sc[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int o = (p + u) * S + th;
+        const T Xs = sx[o], Ys = sy[o];
+        Zs[u] = sz[o]; q[u] = sq[o];
+        R1r[u] = sRr[o]; R1i[u] = sRi[o]; sc[u] = ssc[o];
+        if (m > 0) {  // diagonal step: Rs_m^m = dg_m (x + i y) / r_out * Rs_{m-1}^{m-1}
+          const T cx = dg * Xs, cy = dg * Ys;
+          const T nr = cx * R1r[u] - cy * R1i[u], ni = cx * R1i[u] + cy * R1r[u];
+          R1r[u] = nr; R1i[u] = ni; sc[u] *= q[u];
+          sRr[o] = nr; sRi[o] = ni; ssc[o] = sc[u];
         }
-        if (l >= 1) {
-          if (m == 0) {
-            acc[2 * (l - 1) + 0] += R1r;
-            acc[2 * (l - 1) + 1] += I1r;
-          } else {
-            const int b = 4 * (l - m);
-            acc[b + 0] += R1r;
-            acc[b + 1] += I1r;
-            acc[b + 2] += R1i;
-            acc[b + 3] += I1i;
-          }
+        rs2[u] = Xs * Xs + Ys * Ys + Zs[u] * Zs[u];
+        R0r[u] = T(0); R0i[u] = T(0);
+      }
+      if (m > 0) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          acc[0] += R1r[u]; acc[1] = fma_t(R1r[u], sc[u], acc[1]);
+          acc[2] += R1i[u]; acc[3] = fma_t(R1i[u], sc[u], acc[3]);
+        }
+      }
+#pragma unroll
+      for (int j = 1; j <= L; ++j) {
+        // the column ends at j = L - m; the test runs every kMomBreak steps (the
+        // coefficients past the end are zero, so the extra steps add zeros to
+        // sums that are not written)
+        if ((j - 1) % kMomBreak == 0 && m + j > L) break;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const T az = cA[j] * Zs[u], br = cB[j] * rs2[u];
+          const T nr = az * R1r[u] - br * R0r[u], ni = az * R1i[u] - br * R0i[u];
+          R0r[u] = R1r[u]; R0i[u] = R1i[u]; R1r[u] = nr; R1i[u] = ni;
+          sc[u] *= q[u];
+          acc[4 * j + 0] += nr; acc[4 * j + 1] = fma_t(nr, sc[u], acc[4 * j + 1]);
+          acc[4 * j + 2] += ni; acc[4 * j + 3] = fma_t(ni, sc[u], acc[4 * j + 3]);
         }
       }
     }
-    const int64_t u0 = 2 * int64_t(col_off(L, m));
+    // ---- tile sums of the column, pair p = packed component e0 + p
+    // (m = 0: p = l - 1, acc[4 l + s]; m > 0: p = 2 j + part, acc[2 p + s])
+    const int64_t e0 = col_off(L, m);
+    if (m == 0) {
 #pragma unroll
-    for (int k = 0; k < kMaxC; ++k) {
-      if (k < nc) {
-        const T s2 = acc[k] + __shfl_xor_sync(0xffffffffu, acc[k], 1);
-        if (writer) a.agg[(u0 + k) * ntiles + tile] = s2;
+      for (int p = 0; p < L; ++p) {
+        const T send = odd ? acc[4 * (p + 1)] : acc[4 * (p + 1) + 1];
+        const T recv = __shfl_xor_sync(0xffffffffu, send, 1);
+        const T v = (odd ? acc[4 * (p + 1) + 1] : acc[4 * (p + 1)]) + recv;
+        agg_t[(2 * (e0 + p)) * ts] = v;
+      }
+    } else {
+      const int np = 2 * (L - m + 1);
+#pragma unroll
+      for (int p = 0; p < 2 * L; ++p) {
+        if (p >= np) break;
+        const T send = odd ? acc[2 * p] : acc[2 * p + 1];
+        const T recv = __shfl_xor_sync(0xffffffffu, send, 1);
+        const T v = (odd ? acc[2 * p + 1] : acc[2 * p]) + recv;
+        agg_t[(2 * (e0 + p)) * ts] = v;
       }
     }
   }
@@ -227,6 +260,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   const int64_t tile = int64_t(blockIdx.x) * wpb + warp;
   const int64_t ntiles = (a.n + 31) >> 5;
   if (tile >= ntiles) return;  // warp-uniform; no block-wide barrier below
+  const int64_t ts = tile_stride(ntiles);
   constexpr int CH = chunk_cap(L);
   V4* coefA = reinterpret_cast<V4*>(smem_raw) + size_t(warp) * CH;
   V2* coefB = reinterpret_cast<V2*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * CH) + size_t(warp) * CH;
@@ -246,9 +280,9 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const uint16_t cr = ctab[e];
       const int l = cr & 0xff;
       const T rl = a.rhol[l];  // r_out^l
-      const T A = gb[2 * e] + pt[(2 * e) * ntiles];          // sum over inner tiles of q Rs(x_i / r_out)
-      const T B = gb[2 * e + 1] + pt[(2 * e + 1) * ntiles];  // sum over outer tiles of q Is(x_i)
-      const T W = a.tot[2 * e + 1] - at[(2 * e + 1) * ntiles];  // sum over the other tiles of q Is(x_i)
+      const T A = gb[2 * e] + pt[(2 * e) * ts];          // sum over inner tiles of q Rs(x_i / r_out)
+      const T B = gb[2 * e + 1] + pt[(2 * e + 1) * ts];  // sum over outer tiles of q Is(x_i)
+      const T W = a.tot[2 * e + 1] - at[(2 * e + 1) * ts];  // sum over the other tiles of q Is(x_i)
       T cI = rl * A - a.f[l] * W;
       if ((cr >> 8) & 1) cI += T(u_drive * a.cdrive[l]);
       T cR = rl * B;
@@ -306,7 +340,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     __syncwarp();
   };
 
-  if constexpr (!chunked(L)) build(0, NI + NR);  // all entries of both parts at once
+  if constexpr (!chunked(L)) build(0, NE);  // all entries of both parts at once
   // multipole part: sum over Is_l^m(x), 1 <= l <= L+1
   {
     const T Zir2 = Z * ir2;

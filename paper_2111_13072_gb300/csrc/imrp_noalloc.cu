@@ -23,8 +23,8 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Byte layout of the scratch for n particles, degree L, element size es.
 struct Layout {
-  size_t st[2][6], id[2], key0, idx0, key1, idx1, hist, agg, pfx, gagg, gbase, tot, totd, eout, step, err,
-      total;
+  size_t st[2][6], id[2], key0, idx0, key1, idx1, hist, agg, pfx, gagg, gbase, tot, totd, gswork, gsticket, eout,
+      step, err, total;
 };
 constexpr Layout layout(int64_t n, int L, size_t es) {
   Layout o{};
@@ -41,12 +41,14 @@ constexpr Layout layout(int64_t n, int L, size_t es) {
   o.key1 = at; at += align256(size_t(n) * 4);
   o.idx1 = at; at += align256(size_t(n) * 4);
   o.hist = at; at += align256(size_t(256 * nblk + 256) * 4);
-  o.agg = at; at += align256(size_t(nc * ntiles) * es);
-  o.pfx = at; at += align256(size_t(nc * ntiles) * es);
+  o.agg = at; at += align256(size_t(nc * tile_stride(ntiles)) * es);
+  o.pfx = at; at += align256(size_t(nc * tile_stride(ntiles)) * es);
   o.gagg = at; at += align256(size_t(nc * ngroups) * 8);
   o.gbase = at; at += align256(size_t(nc * ngroups) * es);
   o.tot = at; at += align256(size_t(nc) * es);
   o.totd = at; at += align256(size_t(nc) * 8);
+  o.gswork = at; at += align256(size_t(gs_work_doubles(int(nc))) * 8);
+  o.gsticket = at; at += align256(size_t(gs_col_blocks(int(nc))) * 4);
   o.eout = at; at += align256(size_t(3 * n) * es);
   o.step = at; at += align256(sizeof(StepState));
   o.err = at; at += align256(sizeof(int));
@@ -161,13 +163,15 @@ int run(const imrp_params* p, const double* x, int64_t n, int64_t step, double* 
   MomArgs<T> ma;
   ma.x = st1[0]; ma.y = st1[1]; ma.z = st1[2];
   ma.n = n;
+  ma.rho = T(r_out);
   ma.rho_inv = T(1.0 / r_out);
   ma.agg = static_cast<T*>(P(o.agg));
   ks->moments(ma, s);
   launch_tile_scan<T>(static_cast<T*>(P(o.agg)), static_cast<T*>(P(o.pfx)), static_cast<double*>(P(o.gagg)),
                       ntiles, nc, s);
-  launch_group_scan<T>(static_cast<double*>(P(o.gagg)), static_cast<T*>(P(o.gbase)), static_cast<T*>(P(o.tot)),
-                       static_cast<double*>(P(o.totd)), ngroups, nc, s);
+  launch_group_scan<T>(static_cast<double*>(P(o.gagg)), static_cast<double*>(P(o.gswork)),
+                       static_cast<unsigned*>(P(o.gsticket)), static_cast<T*>(P(o.gbase)),
+                       static_cast<T*>(P(o.tot)), static_cast<double*>(P(o.totd)), ngroups, nc, 32, s);
   double canti[kTabL] = {0}, f[kTabL] = {0};
   for (int l = 1; l <= L; ++l) {
     f[l] = f_coef(l, d, p->eps_D);

@@ -287,7 +287,7 @@ class Sim:
         return dict(zip(STAGES, ms.tolist()))
 
     def autotune(self):
-        """Picks the field CTA size and tile-scan width by timing; returns (wpb, scan_cpb)."""
+        """Picks the field CTA size and the group-scan segment length by timing; returns (wpb, gseg)."""
         w, c = ctypes.c_int(), ctypes.c_int()
         self._check(self._lib.imrp_autotune(self._h, ctypes.byref(w), ctypes.byref(c)))
         return w.value, c.value
