@@ -64,13 +64,21 @@ __global__ void __launch_bounds__(256) k_sort_rowscan(uint32_t* __restrict__ his
   if (threadIdx.x == 0) rowtot[blockIdx.x] = carry;
 }
 
+// Scatter of one pass. Each key gets its block-local position in digit order
+// (digit start within the block + earlier slots of the same digit + rank in
+// its warp: stable); the block's keys and slots are then staged in shared
+// memory in that order, so that consecutive threads write consecutive
+// positions of each digit's run in the output (coalesced even when the
+// digits are uniformly spread).
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, int64_t nblk,
     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ rowtot) {
   constexpr int kSlots = kSortItems * (kSortThreads / 32);
-  __shared__ uint16_t cnt[kSlots][256];
-  __shared__ uint32_t dbase[256];
+  static_assert(kSlots * 256 * sizeof(uint16_t) >= 2 * kSortTile * sizeof(uint32_t), "staging fits the counts");
+  __shared__ __align__(16) uint16_t cnt[kSlots][256];  // later: staged keys and slots
+  __shared__ uint32_t dbase[256];   // global start of digit d for this block
+  __shared__ uint32_t lstart[256];  // block-local start of digit d
   __shared__ uint32_t wsum[8];
   const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int s = 0; s < kSlots; ++s) cnt[s][t] = 0;
@@ -92,18 +100,20 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
   __syncthreads();
   const int64_t base = int64_t(blockIdx.x) * kSortTile;
   const unsigned lt = (1u << lane) - 1u;
-  uint32_t key[kSortItems], rank[kSortItems];
+  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const int64_t idx = base + int64_t(i) * kSortThreads + t;
     const bool ok = idx < n;
     key[i] = ok ? kin[idx] : 0u;
+    val[i] = ok ? vin[idx] : 0u;
     const unsigned d = ok ? ((key[i] >> shift) & 255u) : 256u;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     rank[i] = __popc(peers & lt);
     if (ok && lane == unsigned(__ffs(peers) - 1)) cnt[i * 8 + warp][d] = uint16_t(__popc(peers));
   }
   __syncthreads();
+  uint32_t total;  // block count of digit t
   {
     uint32_t run = 0;
     for (int s = 0; s < kSlots; ++s) {
@@ -111,16 +121,52 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
       cnt[s][t] = uint16_t(run);
       run += c;
     }
+    total = run;
+  }
+  // block-local digit starts: exclusive scan of the block counts over d
+  {
+    uint32_t s = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= unsigned(o)) s += x;
+    }
+    __syncthreads();  // wsum reuse
+    if (lane == 31) wsum[warp] = s;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (unsigned w = 0; w < warp; ++w) woff += wsum[w];
+    lstart[t] = woff + s - total;
   }
   __syncthreads();
+  uint32_t lpos[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const int64_t idx = base + int64_t(i) * kSortThreads + t;
-    if (idx < n) {
-      const unsigned d = (key[i] >> shift) & 255u;
-      const uint32_t pos = dbase[d] + cnt[i * 8 + warp][d] + rank[i];
-      kout[pos] = key[i];
-      vout[pos] = vin[idx];
+    const unsigned d = (key[i] >> shift) & 255u;
+    lpos[i] = idx < n ? lstart[d] + cnt[i * 8 + warp][d] + rank[i] : 0xffffffffu;
+  }
+  __syncthreads();  // the counts are consumed: their storage now stages the block
+  uint32_t* sk = reinterpret_cast<uint32_t*>(&cnt[0][0]);
+  uint32_t* sv = sk + kSortTile;
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    if (lpos[i] != 0xffffffffu) {
+      sk[lpos[i]] = key[i];
+      sv[lpos[i]] = val[i];
+    }
+  }
+  __syncthreads();
+  const int64_t nvalid = n - base < kSortTile ? n - base : kSortTile;
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const int p = i * kSortThreads + int(t);
+    if (p < nvalid) {
+      const uint32_t k = sk[p];
+      const unsigned d = (k >> shift) & 255u;
+      const uint32_t g = dbase[d] + (uint32_t(p) - lstart[d]);
+      kout[g] = k;
+      vout[g] = sv[p];
     }
   }
 }
