@@ -235,6 +235,10 @@ __host__ __device__ constexpr int nchunkR(int L) {
 // N = 4e6, chunks of 192 give 3.93 against 6.02 ms).
 constexpr int kChunkFrom = 20;
 __host__ __device__ constexpr bool chunked(int L) { return L >= kChunkFrom; }
+// Far-field loop form per degree (field kernel at N = 2e6, ms per launch,
+// unrolled / rolled): l_max = 8: 0.32 / 0.35; 12: 0.64 / 0.53; 16: 0.80 /
+// 0.96; 24 (N = 4e6): 3.87 / 3.79.
+__host__ __device__ constexpr bool rolled_far(int L) { return L == 12 || L >= 20; }
 __host__ __device__ constexpr int chunk_cap(int L) {
   return chunked(L) ? (kChunk < nI(L) ? kChunk : (nI(L) > nR(L) ? nI(L) : nR(L))) : nI(L) + nR(L);
 }

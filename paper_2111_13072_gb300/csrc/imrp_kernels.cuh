@@ -341,84 +341,202 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   };
 
   if constexpr (!chunked(L)) build(0, NE);  // all entries of both parts at once
-  // multipole part: sum over Is_l^m(x), 1 <= l <= L+1
-  {
-    const T Zir2 = Z * ir2;
-    T dr = ir, di = T(0);
-    constexpr int QI = chunked(L) ? nchunkI(L) : 1;
-#pragma unroll
-    for (int q = 0; q < QI; ++q) {
-      const int m0 = chunked(L) ? chunkI(L, q) : 0, m1 = chunked(L) ? chunkI(L, q + 1) : L + 2;
-      const int k0 = chunked(L) ? offI(L, m0) : 0;
-      if constexpr (chunked(L)) build(k0, offI(L, m1));
-#pragma unroll
-      for (int m = m0; m < m1; ++m) {
-        if (m > 0) {
-          const T c = tb.dg[m];
-          const T ex = c * X * ir2, ey = c * Y * ir2;
-          const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
-          dr = nr;
-          di = ni;
-        }
-        T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
-#pragma unroll
-        for (int l = m; l <= L + 1; ++l) {
-          if (l > m) {
-            const T A = tb.a[l * kTabL + m] * Zir2, B = tb.b[l * kTabL + m] * ir2;
-            const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
-            c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+  // Two forms of the far-field loops, chosen per degree by measurement
+  // (rolled_far): fully unrolled (compile-time coefficients and entry
+  // addresses), or with the columns m >= 1 in a rolled loop (the recurrence
+  // over l = m + j unrolled, with a uniform exit at the column end; the real
+  // column m = 0 peeled), which keeps the code and the register count small.
+  if constexpr (!rolled_far(L)) {
+    // multipole part: sum over Is_l^m(x), 1 <= l <= L+1
+    {
+      const T Zir2 = Z * ir2;
+      T dr = ir, di = T(0);
+      constexpr int QI = chunked(L) ? nchunkI(L) : 1;
+  #pragma unroll
+      for (int q = 0; q < QI; ++q) {
+        const int m0 = chunked(L) ? chunkI(L, q) : 0, m1 = chunked(L) ? chunkI(L, q + 1) : L + 2;
+        const int k0 = chunked(L) ? offI(L, m0) : 0;
+        if constexpr (chunked(L)) build(k0, offI(L, m1));
+  #pragma unroll
+        for (int m = m0; m < m1; ++m) {
+          if (m > 0) {
+            const T c = tb.dg[m];
+            const T ex = c * X * ir2, ey = c * Y * ir2;
+            const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
+            dr = nr;
+            di = ni;
           }
-          if (l >= 1) {
-            const V4 ca = coefA[idxI(L, l, m) - k0];
+          T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+  #pragma unroll
+          for (int l = m; l <= L + 1; ++l) {
+            if (l > m) {
+              const T A = tb.a[l * kTabL + m] * Zir2, B = tb.b[l * kTabL + m] * ir2;
+              const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
+              c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+            }
+            if (l >= 1) {
+              const V4 ca = coefA[idxI(L, l, m) - k0];
+              Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
+              if (m > 0) {
+                const V2 cb = coefB[idxI(L, l, m) - k0];
+                Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+              }
+            }
+          }
+        }
+      }
+    }
+    // local part: sum over Rs_l^m(x / r_out), 0 <= l <= L-1
+    {
+      const T Xs = X * a.rho_inv, Ys = Y * a.rho_inv, Zs = Z * a.rho_inv;
+      const T rs2 = r2 * a.rho_inv * a.rho_inv;
+      T dr = T(1), di = T(0);
+      constexpr int QR = chunked(L) ? nchunkR(L) : 1;
+  #pragma unroll
+      for (int q = 0; q < QR; ++q) {
+        const int m0 = chunked(L) ? chunkR(L, q) : 0, m1 = chunked(L) ? chunkR(L, q + 1) : L;
+        const int k0 = chunked(L) ? NI + offR(L, m0) : 0;
+        if constexpr (chunked(L)) build(k0, NI + offR(L, m1));
+  #pragma unroll
+        for (int m = m0; m < m1; ++m) {
+          if (m > 0) {
+            const T c = tb.dg[m];
+            const T ex = c * Xs, ey = c * Ys;
+            const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
+            dr = nr;
+            di = ni;
+          }
+          T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+  #pragma unroll
+          for (int l = m; l <= L - 1; ++l) {
+            if (l > m) {
+              const T A = tb.a[l * kTabL + m] * Zs, B = tb.b[l * kTabL + m] * rs2;
+              const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
+              c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+            }
+            const V4 ca = coefA[NI + idxR(L, l, m) - k0];
             Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
             if (m > 0) {
-              const V2 cb = coefB[idxI(L, l, m) - k0];
+              const V2 cb = coefB[NI + idxR(L, l, m) - k0];
               Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
             }
           }
         }
       }
     }
-  }
-  // local part: sum over Rs_l^m(x / r_out), 0 <= l <= L-1
-  {
-    const T Xs = X * a.rho_inv, Ys = Y * a.rho_inv, Zs = Z * a.rho_inv;
-    const T rs2 = r2 * a.rho_inv * a.rho_inv;
-    T dr = T(1), di = T(0);
-    constexpr int QR = chunked(L) ? nchunkR(L) : 1;
-#pragma unroll
-    for (int q = 0; q < QR; ++q) {
-      const int m0 = chunked(L) ? chunkR(L, q) : 0, m1 = chunked(L) ? chunkR(L, q + 1) : L;
-      const int k0 = chunked(L) ? NI + offR(L, m0) : 0;
-      if constexpr (chunked(L)) build(k0, NI + offR(L, m1));
-#pragma unroll
-      for (int m = m0; m < m1; ++m) {
-        if (m > 0) {
-          const T c = tb.dg[m];
-          const T ex = c * Xs, ey = c * Ys;
-          const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
-          dr = nr;
-          di = ni;
+
+  } else {
+    // multipole part: sum over Is_l^m(x), 1 <= l <= L+1
+    {
+      const T Zir2 = Z * ir2;
+      T dr = ir, di = T(0);
+      constexpr int QI = chunked(L) ? nchunkI(L) : 1;
+  #pragma unroll
+      for (int q = 0; q < QI; ++q) {
+        const int m0 = chunked(L) ? chunkI(L, q) : 0, m1 = chunked(L) ? chunkI(L, q + 1) : L + 2;
+        const int k0 = chunked(L) ? offI(L, m0) : 0;
+        if constexpr (chunked(L)) build(k0, offI(L, m1));
+        if (m0 == 0) {
+          T c1 = dr, c0 = T(0);
+  #pragma unroll
+          for (int l = 1; l <= L + 1; ++l) {
+            const T A = tb.a[l * kTabL] * Zir2, B = tb.b[l * kTabL] * ir2;
+            const T n1 = A * c1 - B * c0;
+            c0 = c1; c1 = n1;
+            const V4 ca = coefA[idxI(L, l, 0) - k0];
+            Ex += ca.x * c1; Ey += ca.y * c1; Ez += ca.z * c1;
+          }
         }
-        T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
-#pragma unroll
-        for (int l = m; l <= L - 1; ++l) {
-          if (l > m) {
-            const T A = tb.a[l * kTabL + m] * Zs, B = tb.b[l * kTabL + m] * rs2;
+  #pragma unroll 1
+        for (int m = m0 > 1 ? m0 : 1; m < m1; ++m) {
+          const T c = tb.dg[m];
+          {
+            const T ex = c * X * ir2, ey = c * Y * ir2;
+            const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
+            dr = nr;
+            di = ni;
+          }
+          const int eb = offI(L, m) - k0 - (m > 1 ? m : 1);  // entry of degree l: eb + l
+          T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+          {
+            const V4 ca = coefA[eb + m];
+            const V2 cb = coefB[eb + m];
+            Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
+            Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+          }
+  #pragma unroll
+          for (int j = 1; j <= L; ++j) {
+            const int l = m + j;
+            if (l > L + 1) break;
+            const T A = tb.a[l * kTabL + m] * Zir2, B = tb.b[l * kTabL + m] * ir2;
             const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
             c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
-          }
-          const V4 ca = coefA[NI + idxR(L, l, m) - k0];
-          Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
-          if (m > 0) {
-            const V2 cb = coefB[NI + idxR(L, l, m) - k0];
+            const V4 ca = coefA[eb + l];
+            const V2 cb = coefB[eb + l];
+            Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
             Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
           }
         }
       }
     }
-  }
+    // local part: sum over Rs_l^m(x / r_out), 0 <= l <= L-1
+    {
+      const T Xs = X * a.rho_inv, Ys = Y * a.rho_inv, Zs = Z * a.rho_inv;
+      const T rs2 = r2 * a.rho_inv * a.rho_inv;
+      T dr = T(1), di = T(0);
+      constexpr int QR = chunked(L) ? nchunkR(L) : 1;
+  #pragma unroll
+      for (int q = 0; q < QR; ++q) {
+        const int m0 = chunked(L) ? chunkR(L, q) : 0, m1 = chunked(L) ? chunkR(L, q + 1) : L;
+        const int k0 = chunked(L) ? NI + offR(L, m0) : 0;
+        if constexpr (chunked(L)) build(k0, NI + offR(L, m1));
+        if (m0 == 0) {
+          T c1 = dr, c0 = T(0);
+  #pragma unroll
+          for (int l = 0; l <= L - 1; ++l) {
+            if (l > 0) {
+              const T A = tb.a[l * kTabL] * Zs, B = tb.b[l * kTabL] * rs2;
+              const T n1 = A * c1 - B * c0;
+              c0 = c1; c1 = n1;
+            }
+            const V4 ca = coefA[NI + idxR(L, l, 0) - k0];
+            Ex += ca.x * c1; Ey += ca.y * c1; Ez += ca.z * c1;
+          }
+        }
+  #pragma unroll 1
+        for (int m = m0 > 1 ? m0 : 1; m < m1; ++m) {
+          const T c = tb.dg[m];
+          {
+            const T ex = c * Xs, ey = c * Ys;
+            const T nr = ex * dr - ey * di, ni = ex * di + ey * dr;
+            dr = nr;
+            di = ni;
+          }
+          const int eb = NI + offR(L, m) - k0 - m;  // entry of degree l: eb + l
+          T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+          {
+            const V4 ca = coefA[eb + m];
+            const V2 cb = coefB[eb + m];
+            Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
+            Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+          }
+  #pragma unroll
+          for (int j = 1; j <= L - 1; ++j) {
+            const int l = m + j;
+            if (l > L - 1) break;
+            const T A = tb.a[l * kTabL + m] * Zs, B = tb.b[l * kTabL + m] * rs2;
+            const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
+            c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+            const V4 ca = coefA[eb + l];
+            const V2 cb = coefB[eb + l];
+            Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
+            Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+          }
+        }
+      }
+    }
 
+  }
   Ex += Fx; Ey += Fy; Ez += Fz;
 
   // near field: pair terms (l >= 1) of the particles of this tile, direct
