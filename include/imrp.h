@@ -116,6 +116,19 @@ int imrp_set_stream(imrp_ctx* ctx, void* cuda_stream);
  * non-finite value). */
 int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t n);
 
+/* Streamed form of imrp_load_particles, for callers that feed a new particle
+ * set every few steps and want the host-to-device copy to overlap the steps
+ * still running. The copy of x and v runs on the context's own copy stream
+ * into one of two staging buffers (allocated on the first call, 2 x 48 bytes
+ * per particle of capacity); the conversion into the particle state is
+ * queued on the context's stream after the work already queued there. The
+ * call returns without waiting. x and v must stay valid and unchanged until
+ * the next synchronising call (imrp_sync, imrp_step, imrp_get_*); pinned host
+ * memory is needed for the copy to run asynchronously. A position outside
+ * the shell or a non-finite value is reported by the next synchronising call
+ * (IMRP_E_INVAL). Errors: IMRP_E_INVAL (n out of range), IMRP_E_CUDA. */
+int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, int64_t n);
+
 /* Advances n_steps leapfrog steps (Sec. 2 canonical equations; kick-drift
  * with merged kicks, the first kick after a load is dt/2). Each step sorts the
  * particles by radius, evaluates the field of the modified, truncated Green's
@@ -138,6 +151,13 @@ int imrp_sync(imrp_ctx* ctx);
 /* Copies Q_diff(t_n) and u_asy(t_n) for steps first .. first+count-1 since the
  * last load to host arrays (either may be NULL). */
 int imrp_get_qdiff(imrp_ctx* ctx, int64_t first, int64_t count, double* qdiff, double* uasy);
+
+/* Queues the copy of the recorded samples [first, first + count) of Q_diff and
+ * u_asy (as imrp_get_qdiff) to caller memory (host, preferably pinned, or
+ * device) on the context's stream and returns without waiting; the values are
+ * there once the stream has reached the copy. Either pointer may be NULL.
+ * Errors: IMRP_E_INVAL (range outside the recorded steps), IMRP_E_CUDA. */
+int imrp_copy_qdiff_async(imrp_ctx* ctx, int64_t first, int64_t count, double* qdiff, double* uasy);
 
 /* Field E at the current positions (what the next step would use, with the
  * drive u_asy(t_n) of the next step), written to E[n][3] in particle-id

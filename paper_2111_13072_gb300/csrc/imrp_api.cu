@@ -95,6 +95,11 @@ struct imrp_ctx {
   double *qhist = nullptr, *uhist = nullptr;
   int64_t hcap = 0;
   double* stage = nullptr;  // [cap][6] FP64 staging for load / readback
+  // streamed loads: two staging buffers filled on the copy stream (allocated on first use)
+  double* astage[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  int next_stage = 0;
   StepState* st = nullptr;
   int* derr = nullptr;
   double* dft = nullptr;
@@ -140,6 +145,15 @@ void free_all(imrp_ctx* c) {
   c->gsticket = nullptr;
   c->st = nullptr;
   c->derr = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(c->astage[k]);
+    c->astage[k] = nullptr;
+    if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+    if (c->ev_free[k]) cudaEventDestroy(c->ev_free[k]);
+    c->ev_copied[k] = c->ev_free[k] = nullptr;
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  c->copy_stream = nullptr;
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   c->own_stream = nullptr;
 }
@@ -551,6 +565,61 @@ int imrp_get_qdiff(imrp_ctx* ctx, int64_t first, int64_t count, double* qd, doub
   if (qd) CK(cudaMemcpyAsync(qd, ctx->qhist + first, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   if (ua) CK(cudaMemcpyAsync(ua, ctx->uhist + first, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return check_err(ctx);
+}
+
+int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, int64_t n) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (!x || !v || n < 1 || n > ctx->cap)
+    return ctx->fail(IMRP_E_INVAL, "load_async: n = %lld out of range [1, %lld]", (long long)n, (long long)ctx->cap);
+  if (!ctx->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaMalloc(&ctx->astage[k], 6 * ctx->cap * sizeof(double)));
+      CK(cudaEventCreateWithFlags(&ctx->ev_copied[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_free[k], cudaEventDisableTiming));
+    }
+  }
+  const int s = ctx->next_stage;
+  ctx->next_stage ^= 1;
+  double* S = ctx->astage[s];
+  // the buffer is free once the conversion of the load before the last is done
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[s], 0));
+  CK(cudaMemcpyAsync(S, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->copy_stream));
+  CK(cudaMemcpyAsync(S + 3 * n, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->copy_stream));
+  CK(cudaEventRecord(ctx->ev_copied[s], ctx->copy_stream));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[s], 0));
+  if (ctx->prec == 1)
+    launch_load<float>(S, S + 3 * n, state_ptrs<float>(ctx, 0), ctx->id_buf[0], n, ctx->r_out, ctx->derr, ctx->stream);
+  else
+    launch_load<double>(S, S + 3 * n, state_ptrs<double>(ctx, 0), ctx->id_buf[0], n, ctx->r_out, ctx->derr,
+                        ctx->stream);
+  CK(cudaEventRecord(ctx->ev_free[s], ctx->stream));
+  launch_init_step(ctx->st, ctx->stream);
+  CK(cudaGetLastError());
+  const bool same_n = ctx->loaded && ctx->n == n;
+  ctx->cur = 0;
+  ctx->n = n;
+  ctx->n_tilde = double(n) / (4.0 * kPi / 3.0 * (ctx->r_out * ctx->r_out * ctx->r_out - 1.0));
+  ctx->n_ion = double(n);
+  ctx->ntiles = (n + 31) / 32;
+  ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
+  ctx->host_step = 0;
+  ctx->loaded = true;
+  ctx->keys_valid = false;
+  // a captured step pair depends on n only through its launch shapes and scalars
+  if (!same_n && ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+  return IMRP_OK;
+}
+
+int imrp_copy_qdiff_async(imrp_ctx* ctx, int64_t first, int64_t count, double* qd, double* ua) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (first < 0 || count < 0 || first + count > ctx->host_step)
+    return ctx->fail(IMRP_E_INVAL, "copy_qdiff_async: range [%lld, %lld) outside the %lld recorded steps",
+                     (long long)first, (long long)(first + count), (long long)ctx->host_step);
+  if (count == 0) return IMRP_OK;
+  if (qd) CK(cudaMemcpyAsync(qd, ctx->qhist + first, count * sizeof(double), cudaMemcpyDefault, ctx->stream));
+  if (ua) CK(cudaMemcpyAsync(ua, ctx->uhist + first, count * sizeof(double), cudaMemcpyDefault, ctx->stream));
+  return IMRP_OK;
 }
 
 int imrp_step(imrp_ctx* ctx, int64_t n_steps, double* qdiff_out, double* uasy_out) {

@@ -506,6 +506,18 @@ __global__ void k_finalize(FinalizeArgs a) {
 
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s) { k_finalize<<<1, 32, 0, s>>>(a); }
 
+// Step state after a load: step 0, nothing recorded, the first kick is a half kick.
+__global__ void k_init_step(StepState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->step = 0;
+  st->next = 0;
+  st->u = 0.0;
+  st->kick = 0.0;
+  st->sync = 1;
+}
+
+void launch_init_step(StepState* st, cudaStream_t s) { k_init_step<<<1, 32, 0, s>>>(st); }
+
 // ============================================================================
 // Spectrum sums (FP64). One thread per frequency; the phase factor advances
 // by a rotation and is recomputed exactly every 256 steps.

@@ -64,6 +64,7 @@ struct FinalizeArgs {
   double canti[kTabL];
 };
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+void launch_init_step(StepState* st, cudaStream_t s);
 
 // Spectrum sums: Qh[j] = dt sum_n (q_n - q_0) e^{-i w_j t_n},
 // Uh[j] = sum_n kw_n u_n e^{-i w_j t_n}, w_j = (j+1) w_max / nf; out [nf][4].

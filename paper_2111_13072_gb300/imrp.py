@@ -22,6 +22,7 @@ EXPORTS = [
     "imrp_get_field", "imrp_get_particles", "imrp_spectrum", "imrp_get_info", "imrp_profile_steps",
     "imrp_field_noalloc", "imrp_autotune", "imrp_batch_create", "imrp_batch_step", "imrp_batch_sync",
     "imrp_batch_destroy", "imrp_batch_last_error", "imrp_batch_set_stream", "imrp_footprint",
+    "imrp_load_particles_async", "imrp_copy_qdiff_async",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -81,6 +82,8 @@ def load_library(path: str = LIB_PATH):
     L.imrp_step_async.argtypes = [c_void_p, ctypes.c_int64]
     L.imrp_sync.argtypes = [c_void_p]
     L.imrp_get_qdiff.argtypes = [c_void_p, ctypes.c_int64, ctypes.c_int64, pd, pd]
+    L.imrp_load_particles_async.argtypes = [c_void_p, pd, pd, ctypes.c_int64]
+    L.imrp_copy_qdiff_async.argtypes = [c_void_p, ctypes.c_int64, ctypes.c_int64, pd, pd]
     L.imrp_get_field.argtypes = [c_void_p, pd]
     L.imrp_get_particles.argtypes = [c_void_p, pd, pd]
     L.imrp_spectrum.argtypes = [c_void_p, ctypes.c_int64, ctypes.c_double, pd, pd, pd, pd, pd, pd]
@@ -234,6 +237,17 @@ class Sim:
         """Loads from host pointers (e.g. pinned torch tensors)."""
         P = ctypes.POINTER(ctypes.c_double)
         self._check(self._lib.imrp_load_particles(self._h, ctypes.cast(x_ptr, P), ctypes.cast(v_ptr, P), n))
+
+    def load_async_ptr(self, x_ptr: int, v_ptr: int, n: int):
+        """Streamed load from host pointers (pinned): returns without waiting."""
+        P = ctypes.POINTER(ctypes.c_double)
+        self._check(self._lib.imrp_load_particles_async(self._h, ctypes.cast(x_ptr, P), ctypes.cast(v_ptr, P), n))
+
+    def copy_qdiff_async(self, first: int, count: int, q_ptr: int, u_ptr: int = 0):
+        """Queues the copy of recorded Q_diff (and u_asy) samples to the given pointers."""
+        P = ctypes.POINTER(ctypes.c_double)
+        self._check(self._lib.imrp_copy_qdiff_async(self._h, first, count, ctypes.cast(q_ptr, P),
+                                                      ctypes.cast(u_ptr, P)))
 
     def step(self, n: int, record: bool = True):
         q = np.zeros(n) if record else None
