@@ -204,9 +204,10 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
                    4294967296.0 / (ctx->r_out * ctx->r_out - 1.0), s);
   }
   if (ev) cudaEventRecord(ev[0], s);
-  launch_radix_sort(ctx->key0, ctx->idx0, ctx->key1, ctx->idx1, ctx->hist, n, s);
+  const uint32_t* perm = launch_radix_sort(ctx->key0, ctx->idx0, ctx->key1, ctx->idx1, ctx->hist, n,
+                                           sort_first_byte(ctx->prec), s);
   if (ev) cudaEventRecord(ev[1], s);
-  launch_reorder<T>(src, dst, ctx->id_buf[ctx->cur], ctx->id_buf[1 - ctx->cur], ctx->idx0, n, s);
+  launch_reorder<T>(src, dst, ctx->id_buf[ctx->cur], ctx->id_buf[1 - ctx->cur], perm, n, s);
   ctx->cur = 1 - ctx->cur;
   T** S = dst;
   MomArgs<T> ma;

@@ -171,13 +171,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
   }
 }
 
-void launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
-                       int64_t n, cudaStream_t s) {
-  if (n <= 1) return;
+const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
+                                  int64_t n, int first_byte, cudaStream_t s) {
+  if (n <= 1) return v0;
   const int64_t nblk = sort_blocks(n);
   uint32_t* rowtot = hist + 256 * nblk;
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
-  for (int pass = 0; pass < 4; ++pass) {
+  for (int pass = first_byte; pass < 4; ++pass) {
     const int shift = 8 * pass;
     k_sort_hist<<<unsigned(nblk), kSortThreads, 0, s>>>(ki, n, shift, nblk, hist);
     k_sort_rowscan<<<256, 256, 0, s>>>(hist, nblk, rowtot);
@@ -186,6 +186,7 @@ void launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, u
     uint32_t* tk = ki; ki = ko; ko = tk;
     uint32_t* tv = vi; vi = vo; vo = tv;
   }
+  return vi;
 }
 
 // ============================================================================

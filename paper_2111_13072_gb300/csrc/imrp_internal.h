@@ -16,11 +16,19 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per CTA
 inline int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
-// Sorts (key, val) pairs by key (stable LSD radix sort, 4 passes of 8 bits).
-// k0/v0 hold the input and receive the output; k1/v1 are scratch of n;
-// hist: 256 * sort_blocks(n) + 256 words.
-void launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
-                       int64_t n, cudaStream_t s);
+// Sorts (key, val) pairs by the key bytes first_byte..3 (stable LSD radix
+// sort, one pass of 8 bits per byte; keys equal in those bytes keep their
+// order). k0/v0 hold the input; k1/v1 are scratch of n; hist: 256 *
+// sort_blocks(n) + 256 words. Returns the buffer that holds the sorted values
+// (v0 after an even number of passes, v1 after an odd one).
+// Key bytes sorted: all four, in both precisions. The radius key is
+// floor((r^2 - 1) / (r_out^2 - 1) * 2^32) of the exact FP64 r^2 of the stored
+// position, and the sorted index j of a particle is its count of electrons
+// inside (the l = 0 term), which jumps by one electron per misordered pair;
+// so even radii that FP32 arithmetic cannot tell apart are ordered exactly.
+inline int sort_first_byte(int) { return 0; }
+const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
+                                  int64_t n, int first_byte, cudaStream_t s);
 
 // ---- state movement and keys (imrp_core.cu) ---------------------------------
 template <class T>

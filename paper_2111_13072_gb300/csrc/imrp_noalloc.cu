@@ -157,9 +157,9 @@ int run(const imrp_params* p, const double* x, int64_t n, int64_t step, double* 
   k_na_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, st0[0], st0[1], st0[2], st0[3], st0[4], st0[5],
                                                           id0, n, r_out, err);
   launch_keys<T>(st0[0], st0[1], st0[2], key0, idx0, n, 4294967296.0 / (r_out * r_out - 1.0), s);
-  launch_radix_sort(key0, idx0, static_cast<uint32_t*>(P(o.key1)), static_cast<uint32_t*>(P(o.idx1)),
-                    static_cast<uint32_t*>(P(o.hist)), n, s);
-  launch_reorder<T>(st0, st1, id0, id1, idx0, n, s);
+  const uint32_t* perm = launch_radix_sort(key0, idx0, static_cast<uint32_t*>(P(o.key1)), static_cast<uint32_t*>(P(o.idx1)),
+                    static_cast<uint32_t*>(P(o.hist)), n, sort_first_byte(sizeof(T) == 4 ? 1 : 0), s);
+  launch_reorder<T>(st0, st1, id0, id1, perm, n, s);
   MomArgs<T> ma;
   ma.x = st1[0]; ma.y = st1[1]; ma.z = st1[2];
   ma.n = n;
