@@ -341,9 +341,10 @@ def main():
     tf = os.path.join(ROOT, "profiles", "field_traffic.json")
     if os.path.exists(tf):
         try:
-            rec = json.load(open(tf))
-            if rec.get("kernel_hash") == kernel_hash() and rec.get("workload") == w.name:
-                traffic = rec.get("dram_bytes_per_launch")
+            recs = json.load(open(tf))
+            for rec in recs if isinstance(recs, list) else [recs]:
+                if rec.get("kernel_hash") == kernel_hash() and rec.get("workload") == w.name:
+                    traffic = rec.get("dram_bytes_per_launch")
         except Exception:
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
