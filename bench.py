@@ -48,13 +48,15 @@ def field_flops_per_particle(L):
     final recurrence and fixed: gradient expansions of degree 1..L+1 (Is) and
     0..L-1 (Rs), 20 flops per complex entry (two scalings, complex recurrence,
     six FMAs of the contraction), 11 per real (m = 0) entry, 8 per diagonal step;
-    16 pair evaluations of the in-tile near field at 22 flops per degree plus 120;
-    50 for the l = 0 term, the push and the walls."""
+    16 pair evaluations of the in-tile direct near field, each 13 flops per
+    degree step of the scaled Legendre recurrences (10 for the first) plus 60
+    for the pair geometry and the gradient at both ends; 50 for the l = 0 term,
+    the push and the walls, and 2 L for the removal of the particle's own image."""
     nI = (L + 1) * (L + 4) // 2
     nR = L * (L + 1) // 2
     far = 20 * (nI - (L + 1)) + 11 * (L + 1) + 8 * (L + 1) + 20 * (nR - L) + 11 * L + 8 * (L - 1)
-    near = 16 * (22 * (L - 1) + 120)
-    return far + near + 50
+    near = 16 * (13 * (L - 1) - (3 if L >= 2 else 0) + 60)
+    return far + near + 50 + 2 * L
 
 
 def kernel_hash():

@@ -249,6 +249,7 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   a.gbase = static_cast<const T*>(ctx->gbase);
   a.tot = static_cast<const T*>(ctx->tot);
   a.agg = static_cast<const T*>(ctx->agg);
+  a.img_in_tile = img_in_tile_for<T>(n);
   a.st = ctx->st;
   a.Eout = static_cast<T*>(ctx->eout);
   a.err = ctx->derr;

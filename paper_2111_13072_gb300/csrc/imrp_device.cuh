@@ -173,7 +173,8 @@ template <class T> struct FieldArgs {
   const T* pfx;       // [NC][ntiles] in-group: Rs exclusive prefix, Is exclusive suffix
   const T* gbase;     // [ngroups][NC] Rs: sum over earlier groups; Is: sum over later groups
   const T* tot;       // [NC] totals (Is components used)
-  const T* agg;       // [NC][ntiles] tile sums (own tile removed from the image moments)
+  const T* agg;       // [NC][ntiles] tile sums (read only with img_in_tile)
+  int img_in_tile;    // 1: image pairs inside a tile summed directly (img_in_tile_for)
   const StepState* st;
   T* Eout;            // field mode: E in sorted order [3][n]
   int* err;
@@ -195,6 +196,19 @@ template <class T> struct FieldArgs {
   T rhol[kTabL];      // r_out^l
   double cdrive[kTabL];  // 4 pi n~ * c_l' b^P_l for odd l (drive in units of pf)
 };
+
+// The image moments of the far field include every particle, its own tile and
+// itself too; the particle's own image is then taken off analytically. When
+// the self image far outweighs the field (a lone electron next to the probe:
+// 1500 times in one case), that difference cancels in FP32 beyond 1e-4. So in
+// FP32 contexts of at most kImgInTileMaxN particles the own tile is left out of
+// the image moments and its image pairs are summed directly (a slower loop that
+// only such small contexts run). From a few tiles up the ratio is of order one.
+constexpr int64_t kImgInTileMaxN = 1024;
+template <class T>
+__host__ __device__ constexpr int img_in_tile_for(int64_t n) {
+  return sizeof(T) == 4 && n <= kImgInTileMaxN ? 1 : 0;
+}
 
 // Column chunks of the far field: chunk q of the multipole (Is) part covers
 // columns [chunkI(L, q), chunkI(L, q + 1)), greedily filled to at most kChunk

@@ -241,6 +241,21 @@ __device__ __forceinline__ void fetch_c(const T* sc, int s, int L, int l, int m,
   }
 }
 
+// Constants of the scaled Legendre recurrences of the near field. With
+// c_l = (2l-1)!!/l! (the leading coefficient of P_l), q_l = s^l P_l(u) / c_l
+// follows q_{l+1} = (s u) q_l - g_l s^2 q_{l-1}, g_l = l^2 / (4 l^2 - 1)
+// (Bonnet's recurrence divided by c_{l+1}); and with eps_{l+1} = (2l+1) c_l,
+// e_l = s^{l-1} P'_l(u) / eps_l follows e_{l+1} = r_l s^2 e_{l-1} + q_l,
+// r_l = eps_{l-1} / eps_{l+1} (from P'_{l+1} = P'_{l-1} + (2l+1) P_l).
+__host__ __device__ constexpr double leg_c(int l) {
+  double c = 1.0;
+  for (int k = 1; k <= l; ++k) c *= double(2 * k - 1) / double(k);
+  return c;
+}
+__host__ __device__ constexpr double leg_g(int l) { return double(l) * l / (4.0 * l * l - 1.0); }
+__host__ __device__ constexpr double leg_eps(int l) { return l == 0 ? 1.0 : double(2 * l - 1) * leg_c(l - 1); }
+__host__ __device__ constexpr double leg_r(int l) { return leg_eps(l - 1) / leg_eps(l + 1); }
+
 // One warp per tile. Phase 1 forms the tile's expansion coefficients, phase 2
 // their gradients (ladder identities) in shared memory, phase 3 evaluates the
 // far field of all other tiles, the near field of the pairs inside the tile,
@@ -269,6 +284,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   const int64_t g = tile / kTilesPerGroup;
   const double u_drive = a.st->u;
   const T kick = T(a.st->kick);
+  const bool img_in_tile = img_in_tile_for<T>(0) && a.img_in_tile;  // FP32 contexts only
 
   // ---- phase 1: cI (coefficients of Is, s = 0) and cR (of Rs(x/r_out), s = 1)
   {
@@ -282,7 +298,9 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T rl = a.rhol[l];  // r_out^l
       const T A = gb[2 * e] + pt[(2 * e) * ts];          // sum over inner tiles of q Rs(x_i / r_out)
       const T B = gb[2 * e + 1] + pt[(2 * e + 1) * ts];  // sum over outer tiles of q Is(x_i)
-      const T W = a.tot[2 * e + 1] - at[(2 * e + 1) * ts];  // sum over the other tiles of q Is(x_i)
+      // sum of q Is(x_i) of the image term: over all particles, or over the
+      // other tiles when the own tile's image pairs are summed directly
+      const T W = img_in_tile ? a.tot[2 * e + 1] - at[(2 * e + 1) * ts] : a.tot[2 * e + 1];
       T cI = rl * A - a.f[l] * W;
       if ((cr >> 8) & 1) cI += T(u_drive * a.cdrive[l]);
       T cR = rl * B;
@@ -539,9 +557,9 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   }
   Ex += Fx; Ey += Fy; Ez += Fz;
 
-  // near field: pair terms (l >= 1) of the particles of this tile, direct
-  // r_<^l / r_>^{l+1} P_l and image -f_l P_l / (r r')^{l+1}.
-  // Lower lane = smaller sorted radius = inner.
+  // near field: the direct pair terms r_<^l / r_>^{l+1} P_l (l >= 1) of the
+  // particles of this tile (their image terms are separable and are part of
+  // the far field). Lower lane = smaller sorted radius = inner.
   {
     const T rk = r2 * ir;
     const T ex = X * ir, ey = Y * ir, ez = Z * ir;
@@ -557,41 +575,32 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T pir = __shfl_sync(0xffffffffu, ir, src);
       const T pm = __shfl_sync(0xffffffffu, vmask, src);
       const bool me_inner = int(lane) < src;
-      const T ri = me_inner ? rk : prk, ro = me_inner ? prk : rk;
+      const T ri = me_inner ? rk : prk;
       const T iri = me_inner ? ir : pir, iro = me_inner ? pir : ir;
       const T xix = me_inner ? ex : pex, xiy = me_inner ? ey : pey, xiz = me_inner ? ez : pez;
       const T xox = me_inner ? pex : ex, xoy = me_inner ? pey : ey, xoz = me_inner ? pez : ez;
       const T sr = ri * iro;
       const T uu = xix * xox + xiy * xoy + xiz * xoz;
-      // Q_l = s^l P_l(u), D_l = s^l P'_l(u); image weights f_l h^l, h = 1/r_i^2,
-      // so that f_l P_l/(r_i r_o)^{l+1} = t f_l h^l Q_l with t = 1/(r_i r_o)
-      const T s2r = sr * sr, su = sr * uu;
-      const T hh = iri * iri;
-      T Qm = T(1), Q = su, Dm = T(0), D = sr;
-      T S0 = Q, S1 = Q, S2 = D;
-      T hp = hh;
-      T wq = a.f[1] * hp;
-      T T1 = T(2) * wq * Q, T2 = wq * D;
+      // Q_l = s^l P_l(u) and E_l = s^(l-1) P'_l(u), scaled (leg_c, leg_eps) so
+      // that each step is one product with a per-degree constant less:
+      // S0 = sum Q_l, S1 = sum l Q_l, S2 = sum s E_l = sum s^l P'_l(u).
+      const T x1 = sr * uu, y2 = sr * sr;
+      T qm = T(1), q = x1, em = T(0), e = T(1);
+      T S0 = x1, S1 = x1, S2 = T(1);
 #pragma unroll
       for (int l = 1; l < L; ++l) {
-        const T Qn = (T(2 * l + 1) * su * Q - T(l) * s2r * Qm) * T(1.0 / (l + 1));
-        const T Dn = s2r * Dm + T(2 * l + 1) * sr * Q;
-        Qm = Q; Q = Qn; Dm = D; D = Dn;
-        S0 += Q;
-        S1 += T(l + 1) * Q;
-        S2 += D;
-        hp *= hh;
-        wq = a.f[l + 1] * hp;
-        T1 += T(l + 2) * (wq * Q);
-        T2 += wq * D;
+        const T qn = fma_t(x1, q, -(T(leg_g(l)) * y2) * qm);
+        const T en = l == 1 ? q : fma_t(T(leg_r(l)) * y2, em, q);
+        qm = q; q = qn; em = e; e = en;
+        S0 = fma_t(T(leg_c(l + 1)), q, S0);
+        S1 = fma_t(T((l + 1) * leg_c(l + 1)), q, S1);
+        S2 = fma_t(T(leg_eps(l + 1)), e, S2);
       }
-      const T tt = iri * iro;
-      T1 *= tt;
-      T2 *= tt;
+      S2 *= sr;
       const T iro2 = iro * iro;
-      // grad of phi = sum_l [r_i^l/r_o^{l+1} - f_l/(r_i r_o)^{l+1}] P_l(u)
-      const T gko = -(S0 + S1) * iro2 + T1 * iro, gka = S2 * iro2 - T2 * iro;   // outer point
-      const T gio = (S1 * iro + T1) * iri, gia = (S2 * iro - T2) * iri;        // inner point
+      // grad of phi = sum_l r_i^l/r_o^{l+1} P_l(u)
+      const T gko = -(S0 + S1) * iro2, gka = S2 * iro2;  // outer point
+      const T gio = S1 * iro * iri, gia = S2 * iro * iri;  // inner point
       // outer: gko x^_o + gka (x^_i - u x^_o); inner: gio x^_i + gia (x^_o - u x^_i)
       const T ogx = gko * xox + gka * (xix - uu * xox), ogy = gko * xoy + gka * (xiy - uu * xoy),
               ogz = gko * xoz + gka * (xiz - uu * xoz);
@@ -612,7 +621,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     }
 #pragma unroll 1
     for (int s = 1; s <= 16 && a.m0_only; ++s) {
-      // m = 0 truncation: sum_l [r_i^l / r_o^{l+1} - f_l / (r_i r_o)^{l+1}] P_l(cos t_i) P_l(cos t_o)
+      // m = 0 truncation: sum_l r_i^l / r_o^{l+1} P_l(cos t_i) P_l(cos t_o)
       const int src = (lane + s) & 31;
       const T pex = __shfl_sync(0xffffffffu, ex, src);
       const T pey = __shfl_sync(0xffffffffu, ey, src);
@@ -626,12 +635,11 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T xix = me_inner ? ex : pex, xiy = me_inner ? ey : pey, xiz = me_inner ? ez : pez;
       const T xox = me_inner ? pex : ex, xoy = me_inner ? pey : ey, xoz = me_inner ? pez : ez;
       const T sr = ri * iro;
-      const T tt = iri * iro;
       const T ui = xiz, uo = xoz;  // cos of the polar angles
       T Pim = T(1), Pi = ui, Dim = T(0), Di = T(1);
       T Pom = T(1), Po = uo, Dom = T(0), Do = T(1);
-      T sp = sr, tp = tt * tt;     // s^l and t^{l+1} at l = 1
-      T A1 = T(0), A2 = T(0), A3 = T(0), C1 = T(0), C2 = T(0);
+      T sp = sr;  // s^l at l = 1
+      T A1 = T(0), A3 = T(0), C1 = T(0), C2 = T(0);
 #pragma unroll
       for (int l = 1; l <= L; ++l) {
         if (l > 1) {
@@ -641,19 +649,16 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
           Pim = Pi; Pi = Pin; Dim = Di; Di = Din;
           Pom = Po; Po = Pon; Dom = Do; Do = Don;
           sp *= sr;
-          tp *= tt;
         }
-        const T bl = a.f[l] * tp;
         const T pp = Pi * Po;
         A1 += T(l + 1) * sp * pp;
-        A2 += T(l + 1) * bl * pp;
         A3 += T(l) * sp * pp;
-        const T wgt = sp * iro - bl;
+        const T wgt = sp * iro;
         C1 += wgt * Pi * Do;
         C2 += wgt * Di * Po;
       }
       // grad at the outer point and at the inner point
-      const T go = -A1 * iro * iro + A2 * iro, gi = (A3 * iro + A2) * iri;
+      const T go = -A1 * iro * iro, gi = A3 * iro * iri;
       const T ogx = go * xox - C1 * iro * uo * xox, ogy = go * xoy - C1 * iro * uo * xoy,
               ogz = go * xoz + C1 * iro * (T(1) - uo * xoz);
       const T igx = gi * xix - C2 * iri * ui * xix, igy = gi * xiy - C2 * iri * ui * xiy,
@@ -669,14 +674,62 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
         Nz += __shfl_sync(0xffffffffu, tz, dst);
       }
     }
+    if (img_in_tile) {
+      // image terms of the other particles of the tile: grad at x_k of
+      // -sum_l f_l P_l(u) / (r_k r_i)^{l+1}, u = x^_k . x^_i (m0_only:
+      // P_l(cos t_k) P_l(cos t_i) in place of P_l(u)); d is the direction
+      // along which u varies (x^_i, or z^ for m0_only)
+      T Gx = T(0), Gy = T(0), Gz = T(0);
+#pragma unroll 1
+      for (int s = 1; s < 32; ++s) {
+        const int src = (lane + s) & 31;
+        const T pex = __shfl_sync(0xffffffffu, ex, src);
+        const T pey = __shfl_sync(0xffffffffu, ey, src);
+        const T pez = __shfl_sync(0xffffffffu, ez, src);
+        const T pir = __shfl_sync(0xffffffffu, ir, src);
+        const T pm = __shfl_sync(0xffffffffu, vmask, src);
+        const T uu = a.m0_only ? ez : ex * pex + ey * pey + ez * pez;
+        const T dx = a.m0_only ? T(0) : pex, dy = a.m0_only ? T(0) : pey, dz = a.m0_only ? T(1) : pez;
+        const T tau = ir * pir;
+        T Pm = T(1), P = uu, Dm = T(0), D = T(1);  // P_l(uu), P'_l(uu)
+        T Qm = T(1), Q = a.m0_only ? pez : T(1);  // P_l(cos t_i) (m0_only), else 1
+        T tp = tau * tau;                         // tau^{l+1}
+        T hr = T(0), ha = T(0);
+#pragma unroll 1
+        for (int l = 1; l <= L; ++l) {
+          if (l > 1) {
+            const T Pn = (T(2 * l - 1) * uu * P - T(l - 1) * Pm) / T(l);
+            const T Dn = Dm + T(2 * l - 1) * P;
+            Pm = P; P = Pn; Dm = D; D = Dn;
+            if (a.m0_only) {
+              const T Qn = (T(2 * l - 1) * pez * Q - T(l - 1) * Qm) / T(l);
+              Qm = Q; Q = Qn;
+            }
+            tp *= tau;
+          }
+          const T wgt = a.f[l] * tp * Q;
+          hr += T(l + 1) * wgt * P;
+          ha += wgt * D;
+        }
+        const T w = pm * vmask;
+        Gx += w * (hr * ex - ha * (dx - uu * ex));
+        Gy += w * (hr * ey - ha * (dy - uu * ey));
+        Gz += w * (hr * ez - ha * (dz - uu * ez));
+      }
+      Nx += ir * Gx; Ny += ir * Gy; Nz += ir * Gz;
+    }
     // E = -pf sum_i q_i grad phi = +pf grad phi (q_i = -1)
     const T pfT = T(a.pf);
     Ex += pfT * Nx; Ey += pfT * Ny; Ez += pfT * Nz;
   }
 
   // l = 0: electrons inside (sorted index j), ions inside, surface charge;
-  // then the self-image correction. The count difference is formed in FP64
-  // from the exact FP64 radius of the (FP32 or FP64) position.
+  // then the self-image correction. The image moments of the far field sum
+  // over all particles, the particle itself included, so without the self
+  // image (self_image = 0) its own image field is taken off again; with
+  // img_in_tile the own tile is left out of them, so with the self image
+  // (self_image = 1) it is added. The count difference is formed in FP64 from
+  // the exact FP64 radius of the (FP32 or FP64) position.
   {
     const double xd = double(X), yd = double(Y), zd = double(Z);
     const double r2d = xd * xd + yd * yd + zd * zd;  // exact for FP32 positions
@@ -693,7 +746,8 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     const double qin = fma(a.ion_coef, r2d * rd - 1.0, a.q_s - double(j));
     const T er = T(qin) * (T(a.pf) * ir2 * ir);  // multiplies x (gives r^ / r^2)
     Ex += er * X; Ey += er * Y; Ez += er * Z;
-    if (a.self_image && a.m0_only) {
+    const int self_sign = img_in_tile ? (a.self_image ? 1 : 0) : (a.self_image ? 0 : -1);
+    if (self_sign != 0 && a.m0_only) {
       // own image with the m = 0 kernel: pf sum_l f_l r^{-(2l+3)} [(l+1) P_l^2 r^ - P_l P_l' (z^ - u r^)]
       const T u = Z * ir;
       T Pm = T(1), P = u, Dm = T(0), D = T(1), rp = ir2 * ir2 * ir;  // r^{-5} at l = 1
@@ -709,17 +763,17 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
         hr += a.f[l] * T(l + 1) * P * P * rp;
         ha += a.f[l] * P * D * rp;
       }
-      const T pfT = T(a.pf);
+      const T pfT = T(self_sign * a.pf);
       // r^ = x / r, z^ - u r^ = (0, 0, 1) - u x / r
       Ex += pfT * (hr * X * ir + ha * u * X * ir);
       Ey += pfT * (hr * Y * ir + ha * u * Y * ir);
       Ez += pfT * (hr * Z * ir - ha * (T(1) - u * Z * ir));
-    } else if (a.self_image) {
+    } else if (self_sign != 0) {
       // the particle's own image: pf sum_l f_l (l+1) r^{-(2l+3)} r^
       T h = T(0);
 #pragma unroll
       for (int l = L; l >= 1; --l) h = h * ir2 + a.f[l] * T(l + 1);
-      const T es = T(a.pf) * h * ir2 * ir2 * ir2;  // r^{-(2l+3)} r^ = ir2^{l-1} ir2^3 x
+      const T es = T(self_sign * a.pf) * h * ir2 * ir2 * ir2;  // r^{-(2l+3)} r^ = ir2^{l-1} ir2^3 x
       Ex += es * X; Ey += es * Y; Ez += es * Z;
     }
   }

@@ -202,6 +202,7 @@ int run(const imrp_params* p, const double* x, int64_t n, int64_t step, double* 
   a.gbase = static_cast<const T*>(P(o.gbase));
   a.tot = static_cast<const T*>(P(o.tot));
   a.agg = static_cast<const T*>(P(o.agg));
+  a.img_in_tile = img_in_tile_for<T>(n);
   a.st = st;
   a.Eout = static_cast<T*>(P(o.eout));
   a.err = err;
