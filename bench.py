@@ -46,16 +46,17 @@ def workload_desc(w):
 def field_flops_per_particle(L):
     """FP32 flops of one particle in the field kernel (FMA = 2), counted from the
     final recurrence and fixed: gradient expansions of degree 1..L+1 (Is) and
-    0..L-1 (Rs), 20 flops per complex entry (two scalings, complex recurrence,
-    six FMAs of the contraction), 11 per real (m = 0) entry, 8 per diagonal step;
-    16 pair evaluations of the in-tile direct near field, each 13 flops per
-    degree step of the scaled Legendre recurrences (10 for the first) plus 60
-    for the pair geometry and the gradient at both ends; 50 for the l = 0 term,
-    the push and the walls, and 2 L for the removal of the particle's own image."""
+    0..L-1 (Rs) on the rescaled recurrences, 19 flops per complex entry (one
+    scaling, complex recurrence, six FMAs of the contraction), 10 per real
+    (m = 0) entry, 8 per diagonal step; 16 pair evaluations of the in-tile
+    direct near field, each 13 flops per degree step of the scaled Legendre
+    recurrences (10 for the first) plus 57 for the pair geometry and the
+    gradient at both ends; 50 for the l = 0 term, the push and the walls, and
+    2 L for the removal of the particle's own image."""
     nI = (L + 1) * (L + 4) // 2
     nR = L * (L + 1) // 2
-    far = 20 * (nI - (L + 1)) + 11 * (L + 1) + 8 * (L + 1) + 20 * (nR - L) + 11 * L + 8 * (L - 1)
-    near = 16 * (13 * (L - 1) - (3 if L >= 2 else 0) + 60)
+    far = 19 * (nI - (L + 1)) + 10 * (L + 1) + 8 * (L + 1) + 19 * (nR - L) + 10 * L + 8 * (L - 1)
+    near = 16 * (13 * (L - 1) - (3 if L >= 2 else 0) + 57)
     return far + near + 50 + 2 * L
 
 

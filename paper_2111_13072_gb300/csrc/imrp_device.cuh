@@ -67,10 +67,16 @@ template <class T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
-// Recurrence tables in constant memory, one copy per translation unit.
+// Recurrence tables in constant memory, one copy per translation unit. The
+// kernels run the recurrences on rescaled harmonics Rs_l^m / nu_lm and
+// Is_l^m / nu_lm, with nu_lm = b_lm nu_{l-2,m} (nu = 1 for l <= m + 1), for which
+//   R_l = an_lm z R_{l-1} - r^2 R_{l-2},   I_l = (an_lm z I_{l-1} - I_{l-2}) / r^2,
+//   an_lm = a_lm nu_{l-1,m} / nu_lm:
+// one product per step less. nu lies in [0.15, 1] for l <= 26; the factor is
+// put back in the tile sums and in the gradient entries.
 template <class T> struct Tables {
-  T a[kTabL * kTabL];
-  T b[kTabL * kTabL];
+  T an[kTabL * kTabL];
+  T nu[kTabL * kTabL];
   T dg[kTabL];
 };
 

@@ -13,17 +13,22 @@
 namespace imrp {
 namespace {
 
+// a_lm, b_lm of the solid-harmonic recurrences and the rescaling nu_lm.
+inline double rec_a(int l, int m) { return m < l ? (2.0 * l - 1.0) / sqrt(double(l + m) * double(l - m)) : 0.0; }
+inline double rec_b(int l, int m) {
+  return m < l ? sqrt(double(l + m - 1) * double(l - m - 1) / (double(l + m) * double(l - m))) : 0.0;
+}
+inline double rec_nu(int l, int m) {
+  double v = 1.0;
+  for (int k = l; k >= m + 2; k -= 2) v *= rec_b(k, m);
+  return v;
+}
+
 template <class T> void fill_tables(Tables<T>& t) {
   for (int l = 0; l < kTabL; ++l)
     for (int m = 0; m < kTabL; ++m) {
-      double a = 0.0, b = 0.0;
-      if (m < l) {
-        const double den = double(l + m) * double(l - m);
-        a = (2.0 * l - 1.0) / sqrt(den);
-        b = sqrt(double(l + m - 1) * double(l - m - 1) / den);
-      }
-      t.a[l * kTabL + m] = T(a);
-      t.b[l * kTabL + m] = T(b);
+      t.an[l * kTabL + m] = T(m < l ? rec_a(l, m) * rec_nu(l - 1, m) / rec_nu(l, m) : 0.0);
+      t.nu[l * kTabL + m] = T(m <= l ? rec_nu(l, m) : 0.0);
     }
   for (int m = 0; m < kTabL; ++m) t.dg[m] = m == 0 ? T(1) : T(-sqrt((2.0 * m - 1.0) / (2.0 * m)));
 }
@@ -65,14 +70,16 @@ void fill_prologue_tables() {
       if (isI) flags |= uint16_t(1u << 8);
       if (M > 0) flags |= uint16_t(1u << 9);
       r.flags = flags;
+      // ladder factors, times nu of the evaluated (rescaled) harmonic (Lp, M)
+      const double nu = rec_nu(Lp, M);
       if (isI) {
-        r.s1 = float(sqrt(double((Lp + M) * (Lp + M - 1))));
-        r.s2 = float(-sqrt(double((Lp - M) * (Lp - M - 1))));
-        r.sz = float(-sqrt(double((Lp + M) * (Lp - M))));
+        r.s1 = float(nu * sqrt(double((Lp + M) * (Lp + M - 1))));
+        r.s2 = float(-nu * sqrt(double((Lp - M) * (Lp - M - 1))));
+        r.sz = float(-nu * sqrt(double((Lp + M) * (Lp - M))));
       } else {
-        r.s1 = float(sqrt(double((Lp - M + 2) * (Lp - M + 1))));
-        r.s2 = float(-sqrt(double((Lp + M + 2) * (Lp + M + 1))));
-        r.sz = float(sqrt(double((Lp + 1 + M) * (Lp + 1 - M))));
+        r.s1 = float(nu * sqrt(double((Lp - M + 2) * (Lp - M + 1))));
+        r.s2 = float(-nu * sqrt(double((Lp + M + 2) * (Lp + M + 1))));
+        r.sz = float(nu * sqrt(double((Lp + 1 + M) * (Lp + 1 - M))));
       }
       return r;
     };

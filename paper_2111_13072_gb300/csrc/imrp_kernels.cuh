@@ -19,11 +19,11 @@ template <> __device__ __forceinline__ const Tables<double>& tab<double>() { ret
 // translation unit (filled by fill_prologue_tables at initialisation), for
 // every instantiated degree.
 // EntryRec: one gradient entry k of the shared-memory coefficient arrays.
-struct EntryRec {
+struct __align__(16) EntryRec {
   int16_t src[6];   // scratch index of c1.re, c1.im, c2.re, c2.im, c0.re, c0.im (-1: zero)
   uint16_t flags;   // bit q < 6: negate source q; bit 8: multipole (Is) part; bit 9: M > 0
   uint16_t pad;
-  float s1, s2, sz, pad2;  // ladder factors
+  float s1, s2, sz, pad2;  // ladder factors times nu of the evaluated harmonic
 };
 constexpr int kNumDegrees = 7;  // the instantiated degrees: 1, 2, 4, 8, 12, 16, 24
 __host__ __device__ constexpr int degree_at(int i) {
@@ -126,13 +126,9 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
     T acc[4 * (L + 1)];  // [j][R re, I re, R im, I im], l = m + j
 #pragma unroll
     for (int k = 0; k < 4 * (L + 1); ++k) acc[k] = T(0);
-    T cA[L + 1], cB[L + 1];  // recurrence coefficients of this column
+    T cA[L + 1];  // recurrence coefficients of this column (rescaled harmonics)
 #pragma unroll
-    for (int j = 1; j <= L; ++j) {
-      const bool in = m + j <= L;
-      cA[j] = in ? tb.a[(m + j) * kTabL + m] : T(0);
-      cB[j] = in ? tb.b[(m + j) * kTabL + m] : T(0);
-    }
+    for (int j = 1; j <= L; ++j) cA[j] = m + j <= L ? tb.an[(m + j) * kTabL + m] : T(0);
     const T dg = tb.dg[m];
 #pragma unroll 1
     for (int p = 0; p < kMomPPT; p += 2) {
@@ -167,8 +163,8 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
         if ((j - 1) % kMomBreak == 0 && m + j > L) break;
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          const T az = cA[j] * Zs[u], br = cB[j] * rs2[u];
-          const T nr = az * R1r[u] - br * R0r[u], ni = az * R1i[u] - br * R0i[u];
+          const T az = cA[j] * Zs[u];
+          const T nr = az * R1r[u] - rs2[u] * R0r[u], ni = az * R1i[u] - rs2[u] * R0i[u];
           R0r[u] = R1r[u]; R0i[u] = R1i[u]; R1r[u] = nr; R1i[u] = ni;
           sc[u] *= q[u];
           acc[4 * j + 0] += nr; acc[4 * j + 1] = fma_t(nr, sc[u], acc[4 * j + 1]);
@@ -185,7 +181,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
         const T send = odd ? acc[4 * (p + 1)] : acc[4 * (p + 1) + 1];
         const T recv = __shfl_xor_sync(0xffffffffu, send, 1);
         const T v = (odd ? acc[4 * (p + 1) + 1] : acc[4 * (p + 1)]) + recv;
-        agg_t[(2 * (e0 + p)) * ts] = v;
+        agg_t[(2 * (e0 + p)) * ts] = v * tb.nu[(p + 1) * kTabL];
       }
     } else {
       const int np = 2 * (L - m + 1);
@@ -195,7 +191,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
         const T send = odd ? acc[2 * p] : acc[2 * p + 1];
         const T recv = __shfl_xor_sync(0xffffffffu, send, 1);
         const T v = (odd ? acc[2 * p + 1] : acc[2 * p]) + recv;
-        agg_t[(2 * (e0 + p)) * ts] = v;
+        agg_t[(2 * (e0 + p)) * ts] = v * tb.nu[(m + (p >> 1)) * kTabL + m];
       }
     }
   }
@@ -286,34 +282,46 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   const T kick = T(a.st->kick);
   const bool img_in_tile = img_in_tile_for<T>(0) && a.img_in_tile;  // FP32 contexts only
 
-  // ---- phase 1: cI (coefficients of Is, s = 0) and cR (of Rs(x/r_out), s = 1)
+  // the particle of this lane, loaded first so that its latency overlaps the
+  // prologue
+  const int64_t j = tile * 32 + lane;
+  const bool valid = j < a.n;
+  T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
+  T VX = T(0), VY = T(0), VZ = T(0);
+  if (a.mode == 0 && valid) { VX = a.vx[j]; VY = a.vy[j]; VZ = a.vz[j]; }
+
+  // ---- phase 1: cI (coefficients of Is, s = 0) and cR (of Rs(x/r_out), s = 1).
+  // The loop has a fixed trip count and is unrolled, so that all loads of the
+  // scan carries are in flight at once.
   {
     const T* pt = a.pfx + tile;   // [u][tile]
     const T* gb = a.gbase + g * NC;
     const T* at = a.agg + tile;   // [u][tile]
     const uint16_t* ctab = g_comp + comp_tab_off(L);
-    for (int e = lane; e < NC / 2; e += 32) {
-      const uint16_t cr = ctab[e];
-      const int l = cr & 0xff;
-      const T rl = a.rhol[l];  // r_out^l
-      const T A = gb[2 * e] + pt[(2 * e) * ts];          // sum over inner tiles of q Rs(x_i / r_out)
-      const T B = gb[2 * e + 1] + pt[(2 * e + 1) * ts];  // sum over outer tiles of q Is(x_i)
-      // sum of q Is(x_i) of the image term: over all particles, or over the
-      // other tiles when the own tile's image pairs are summed directly
-      const T W = img_in_tile ? a.tot[2 * e + 1] - at[(2 * e + 1) * ts] : a.tot[2 * e + 1];
-      T cI = rl * A - a.f[l] * W;
-      if ((cr >> 8) & 1) cI += T(u_drive * a.cdrive[l]);
-      T cR = rl * B;
-      if (a.m0_only && ((cr >> 9) & 1)) { cI = T(0); cR = T(0); }
-      sc[2 * e] = cI;
-      sc[2 * e + 1] = cR;
+    constexpr int NIT = (NC / 2 + 31) / 32;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      const int e = int(lane) + 32 * it;
+      if (e < NC / 2) {
+        const uint16_t cr = ctab[e];
+        const int l = cr & 0xff;
+        const T rl = a.rhol[l];  // r_out^l
+        const T A = gb[2 * e] + pt[(2 * e) * ts];          // sum over inner tiles of q Rs(x_i / r_out)
+        const T B = gb[2 * e + 1] + pt[(2 * e + 1) * ts];  // sum over outer tiles of q Is(x_i)
+        // sum of q Is(x_i) of the image term: over all particles, or over the
+        // other tiles when the own tile's image pairs are summed directly
+        const T W = img_in_tile ? a.tot[2 * e + 1] - at[(2 * e + 1) * ts] : a.tot[2 * e + 1];
+        T cI = rl * A - a.f[l] * W;
+        if ((cr >> 8) & 1) cI += T(u_drive * a.cdrive[l]);
+        T cR = rl * B;
+        if (a.m0_only && ((cr >> 9) & 1)) { cI = T(0); cR = T(0); }
+        sc[2 * e] = cI;
+        sc[2 * e + 1] = cR;
+      }
     }
   }
   __syncwarp();
   // ---- phase 3: the particle of this lane
-  const int64_t j = tile * 32 + lane;
-  const bool valid = j < a.n;
-  T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
   const T r2 = X * X + Y * Y + Z * Z;
   const T ir2 = T(1) / r2;
   const T ir = rsqrt_t(r2);
@@ -328,32 +336,37 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   const EntryRec* etab = g_ent + ent_off(L);
   auto build = [&](int k0, int k1) {
     __syncwarp();
-    for (int k = k0 + int(lane); k < k1; k += 32) {
-      const EntryRec er = etab[k];
-      T c[6];
+    constexpr int NB = (CH + 31) / 32;  // at most CH entries per build
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        const int si = er.src[q];
-        const T val = si >= 0 ? sc[si] : T(0);
-        c[q] = ((er.flags >> q) & 1) ? -val : val;
+    for (int it = 0; it < NB; ++it) {
+      const int k = k0 + int(lane) + 32 * it;
+      if (k < k1) {
+        const EntryRec er = etab[k];
+        T c[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const int si = er.src[q];
+          const T val = si >= 0 ? sc[si] : T(0);
+          c[q] = ((er.flags >> q) & 1) ? -val : val;
+        }
+        const T c1r = c[0], c1i = c[1], c2r = c[2], c2i = c[3], c0r = c[4], c0i = c[5];
+        const T s1 = T(er.s1), s2 = T(er.s2), sz = T(er.sz);
+        const bool isI = (er.flags >> 8) & 1;
+        const int M = (er.flags >> 9) & 1;
+        // dx = (s1 c1 + s2 c2)/2 ; dy = (i/2)(s1 c1 - s2 c2) ; dz = sz c0
+        const T dxr = T(0.5) * (s1 * c1r + s2 * c2r), dxi = T(0.5) * (s1 * c1i + s2 * c2i);
+        const T tr = s1 * c1r - s2 * c2r, ti = s1 * c1i - s2 * c2i;
+        const T dyr = T(-0.5) * ti, dyi = T(0.5) * tr;
+        const T dzr = sz * c0r, dzi = sz * c0i;
+        T w = (M > 0 ? T(2) : T(1)) * mpf;
+        if (!isI) w *= a.rho_inv;
+        V4 ca;
+        V2 cb;
+        ca.x = w * dxr; ca.y = w * dyr; ca.z = w * dzr; ca.w = w * dxi;
+        cb.x = w * dyi; cb.y = w * dzi;
+        coefA[k - k0] = ca;
+        coefB[k - k0] = cb;
       }
-      const T c1r = c[0], c1i = c[1], c2r = c[2], c2i = c[3], c0r = c[4], c0i = c[5];
-      const T s1 = T(er.s1), s2 = T(er.s2), sz = T(er.sz);
-      const bool isI = (er.flags >> 8) & 1;
-      const int M = (er.flags >> 9) & 1;
-      // dx = (s1 c1 + s2 c2)/2 ; dy = (i/2)(s1 c1 - s2 c2) ; dz = sz c0
-      const T dxr = T(0.5) * (s1 * c1r + s2 * c2r), dxi = T(0.5) * (s1 * c1i + s2 * c2i);
-      const T tr = s1 * c1r - s2 * c2r, ti = s1 * c1i - s2 * c2i;
-      const T dyr = T(-0.5) * ti, dyi = T(0.5) * tr;
-      const T dzr = sz * c0r, dzi = sz * c0i;
-      T w = (M > 0 ? T(2) : T(1)) * mpf;
-      if (!isI) w *= a.rho_inv;
-      V4 ca;
-      V2 cb;
-      ca.x = w * dxr; ca.y = w * dyr; ca.z = w * dzr; ca.w = w * dxi;
-      cb.x = w * dyi; cb.y = w * dzi;
-      coefA[k - k0] = ca;
-      coefB[k - k0] = cb;
     }
     __syncwarp();
   };
@@ -370,12 +383,12 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T Zir2 = Z * ir2;
       T dr = ir, di = T(0);
       constexpr int QI = chunked(L) ? nchunkI(L) : 1;
-  #pragma unroll
+#pragma unroll
       for (int q = 0; q < QI; ++q) {
         const int m0 = chunked(L) ? chunkI(L, q) : 0, m1 = chunked(L) ? chunkI(L, q + 1) : L + 2;
         const int k0 = chunked(L) ? offI(L, m0) : 0;
         if constexpr (chunked(L)) build(k0, offI(L, m1));
-  #pragma unroll
+#pragma unroll
         for (int m = m0; m < m1; ++m) {
           if (m > 0) {
             const T c = tb.dg[m];
@@ -385,10 +398,10 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
             di = ni;
           }
           T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
-  #pragma unroll
+#pragma unroll
           for (int l = m; l <= L + 1; ++l) {
             if (l > m) {
-              const T A = tb.a[l * kTabL + m] * Zir2, B = tb.b[l * kTabL + m] * ir2;
+              const T A = tb.an[l * kTabL + m] * Zir2, B = ir2;
               const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
               c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
             }
@@ -410,12 +423,12 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T rs2 = r2 * a.rho_inv * a.rho_inv;
       T dr = T(1), di = T(0);
       constexpr int QR = chunked(L) ? nchunkR(L) : 1;
-  #pragma unroll
+#pragma unroll
       for (int q = 0; q < QR; ++q) {
         const int m0 = chunked(L) ? chunkR(L, q) : 0, m1 = chunked(L) ? chunkR(L, q + 1) : L;
         const int k0 = chunked(L) ? NI + offR(L, m0) : 0;
         if constexpr (chunked(L)) build(k0, NI + offR(L, m1));
-  #pragma unroll
+#pragma unroll
         for (int m = m0; m < m1; ++m) {
           if (m > 0) {
             const T c = tb.dg[m];
@@ -425,10 +438,10 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
             di = ni;
           }
           T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
-  #pragma unroll
+#pragma unroll
           for (int l = m; l <= L - 1; ++l) {
             if (l > m) {
-              const T A = tb.a[l * kTabL + m] * Zs, B = tb.b[l * kTabL + m] * rs2;
+              const T A = tb.an[l * kTabL + m] * Zs, B = rs2;
               const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
               c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
             }
@@ -449,16 +462,16 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T Zir2 = Z * ir2;
       T dr = ir, di = T(0);
       constexpr int QI = chunked(L) ? nchunkI(L) : 1;
-  #pragma unroll
+#pragma unroll
       for (int q = 0; q < QI; ++q) {
         const int m0 = chunked(L) ? chunkI(L, q) : 0, m1 = chunked(L) ? chunkI(L, q + 1) : L + 2;
         const int k0 = chunked(L) ? offI(L, m0) : 0;
         if constexpr (chunked(L)) build(k0, offI(L, m1));
         if (m0 == 0) {
           T c1 = dr, c0 = T(0);
-  #pragma unroll
+#pragma unroll
           for (int l = 1; l <= L + 1; ++l) {
-            const T A = tb.a[l * kTabL] * Zir2, B = tb.b[l * kTabL] * ir2;
+            const T A = tb.an[l * kTabL] * Zir2, B = ir2;
             const T n1 = A * c1 - B * c0;
             c0 = c1; c1 = n1;
             const V4 ca = coefA[idxI(L, l, 0) - k0];
@@ -482,11 +495,11 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
             Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
             Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
           }
-  #pragma unroll
+#pragma unroll
           for (int j = 1; j <= L; ++j) {
             const int l = m + j;
             if (l > L + 1) break;
-            const T A = tb.a[l * kTabL + m] * Zir2, B = tb.b[l * kTabL + m] * ir2;
+            const T A = tb.an[l * kTabL + m] * Zir2, B = ir2;
             const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
             c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
             const V4 ca = coefA[eb + l];
@@ -503,17 +516,17 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T rs2 = r2 * a.rho_inv * a.rho_inv;
       T dr = T(1), di = T(0);
       constexpr int QR = chunked(L) ? nchunkR(L) : 1;
-  #pragma unroll
+#pragma unroll
       for (int q = 0; q < QR; ++q) {
         const int m0 = chunked(L) ? chunkR(L, q) : 0, m1 = chunked(L) ? chunkR(L, q + 1) : L;
         const int k0 = chunked(L) ? NI + offR(L, m0) : 0;
         if constexpr (chunked(L)) build(k0, NI + offR(L, m1));
         if (m0 == 0) {
           T c1 = dr, c0 = T(0);
-  #pragma unroll
+#pragma unroll
           for (int l = 0; l <= L - 1; ++l) {
             if (l > 0) {
-              const T A = tb.a[l * kTabL] * Zs, B = tb.b[l * kTabL] * rs2;
+              const T A = tb.an[l * kTabL] * Zs, B = rs2;
               const T n1 = A * c1 - B * c0;
               c0 = c1; c1 = n1;
             }
@@ -538,11 +551,11 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
             Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
             Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
           }
-  #pragma unroll
+#pragma unroll
           for (int j = 1; j <= L - 1; ++j) {
             const int l = m + j;
             if (l > L - 1) break;
-            const T A = tb.a[l * kTabL + m] * Zs, B = tb.b[l * kTabL + m] * rs2;
+            const T A = tb.an[l * kTabL + m] * Zs, B = rs2;
             const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
             c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
             const V4 ca = coefA[eb + l];
@@ -575,12 +588,8 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       const T pir = __shfl_sync(0xffffffffu, ir, src);
       const T pm = __shfl_sync(0xffffffffu, vmask, src);
       const bool me_inner = int(lane) < src;
-      const T ri = me_inner ? rk : prk;
-      const T iri = me_inner ? ir : pir, iro = me_inner ? pir : ir;
-      const T xix = me_inner ? ex : pex, xiy = me_inner ? ey : pey, xiz = me_inner ? ez : pez;
-      const T xox = me_inner ? pex : ex, xoy = me_inner ? pey : ey, xoz = me_inner ? pez : ez;
-      const T sr = ri * iro;
-      const T uu = xix * xox + xiy * xoy + xiz * xoz;
+      const T sr = me_inner ? rk * pir : prk * ir;  // r_inner / r_outer
+      const T uu = ex * pex + ey * pey + ez * pez;
       // Q_l = s^l P_l(u) and E_l = s^(l-1) P'_l(u), scaled (leg_c, leg_eps) so
       // that each step is one product with a per-degree constant less:
       // S0 = sum Q_l, S1 = sum l Q_l, S2 = sum s E_l = sum s^l P'_l(u).
@@ -597,22 +606,23 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
         S2 = fma_t(T(leg_eps(l + 1)), e, S2);
       }
       S2 *= sr;
-      const T iro2 = iro * iro;
-      // grad of phi = sum_l r_i^l/r_o^{l+1} P_l(u)
-      const T gko = -(S0 + S1) * iro2, gka = S2 * iro2;  // outer point
-      const T gio = S1 * iro * iri, gia = S2 * iro * iri;  // inner point
-      // outer: gko x^_o + gka (x^_i - u x^_o); inner: gio x^_i + gia (x^_o - u x^_i)
-      const T ogx = gko * xox + gka * (xix - uu * xox), ogy = gko * xoy + gka * (xiy - uu * xoy),
-              ogz = gko * xoz + gka * (xiz - uu * xoz);
-      const T igx = gio * xix + gia * (xox - uu * xix), igy = gio * xiy + gia * (xoy - uu * xiy),
-              igz = gio * xiz + gia * (xoz - uu * xiz);
+      // grad of phi = sum_l r_i^l/r_o^{l+1} P_l(u): at the inner end
+      // (S1 r^_i + S2 (r^_o - u r^_i)) / (r_i r_o), at the outer end
+      // (-(S0 + S1) r^_o + S2 (r^_i - u r^_o)) / r_o^2; radial (r) and angular
+      // (a) factors of my end and of the partner's, with the validity mask
       const T w = pm * vmask;
-      const T mx = w * (me_inner ? igx : ogx), my = w * (me_inner ? igy : ogy),
-              mz = w * (me_inner ? igz : ogz);
-      Nx += mx; Ny += my; Nz += mz;
+      const T wab = w * ir * pir;                          // w / (r_i r_o)
+      const T wo2 = w * (me_inner ? pir * pir : ir * ir);  // w / r_o^2
+      const T in_r = S1 * wab, in_a = S2 * wab;
+      const T out_r = -(S0 + S1) * wo2, out_a = S2 * wo2;
+      const T mr = me_inner ? in_r : out_r, ma = me_inner ? in_a : out_a;
+      Nx += mr * ex + ma * (pex - uu * ex);
+      Ny += mr * ey + ma * (pey - uu * ey);
+      Nz += mr * ez + ma * (pez - uu * ez);
       if (s < 16) {
-        const T tx = w * (me_inner ? ogx : igx), ty = w * (me_inner ? ogy : igy),
-                tz = w * (me_inner ? ogz : igz);
+        const T pr = me_inner ? out_r : in_r, pa = me_inner ? out_a : in_a;
+        const T tx = pr * pex + pa * (ex - uu * pex), ty = pr * pey + pa * (ey - uu * pey),
+                tz = pr * pez + pa * (ez - uu * pez);
         const int dst = (lane - s) & 31;
         Nx += __shfl_sync(0xffffffffu, tx, dst);
         Ny += __shfl_sync(0xffffffffu, ty, dst);
@@ -789,7 +799,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   if (!valid) return;
 
   // ---- leapfrog: v += kick (q/m) E with q/m = -1; x += dt v
-  T VX = a.vx[j] - kick * Ex, VY = a.vy[j] - kick * Ey, VZ = a.vz[j] - kick * Ez;
+  VX -= kick * Ex; VY -= kick * Ey; VZ -= kick * Ez;
   X += a.dt * VX; Y += a.dt * VY; Z += a.dt * VZ;
 
   // ---- walls (Sec. 4): mirror the radius back, keep the speed
