@@ -61,9 +61,15 @@ def field_flops_per_particle(L):
 
 
 def kernel_hash():
+    """Hash of the sources the field kernel is built from (its template, the
+    device helpers and the per-degree instantiation units): a DRAM traffic
+    record under profiles/ applies only while these are unchanged."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2111_13072_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    csrc = os.path.join(ROOT, "paper_2111_13072_gb300", "csrc")
+    files = ["imrp_kernels.cuh", "imrp_device.cuh", "imrp_inst.cuh"] + sorted(
+        os.path.basename(f) for f in glob.glob(os.path.join(csrc, "imrp_inst_*.cu")))
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
