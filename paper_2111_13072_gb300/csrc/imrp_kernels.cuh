@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   auto build = [&](int k0, int k1) {
     __syncwarp();
     constexpr int NB = (CH + 31) / 32;  // at most CH entries per build
-#pragma unroll
+#pragma unroll 1
     for (int it = 0; it < NB; ++it) {
       const int k = k0 + int(lane) + 32 * it;
       if (k < k1) {
