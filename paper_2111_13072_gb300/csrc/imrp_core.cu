@@ -64,24 +64,32 @@ __global__ void __launch_bounds__(256) k_sort_rowscan(uint32_t* __restrict__ his
   if (threadIdx.x == 0) rowtot[blockIdx.x] = carry;
 }
 
-// Scatter of one pass. Each key gets its block-local position in digit order
-// (digit start within the block + earlier slots of the same digit + rank in
-// its warp: stable); the block's keys and slots are then staged in shared
-// memory in that order, so that consecutive threads write consecutive
-// positions of each digit's run in the output (coalesced even when the
-// digits are uniformly spread).
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
+// Scatter of one pass. Warp w of the block owns the keys base + 256 w ..
+// base + 256 w + 255 (item i of lane l is key base + 256 w + 32 i + l), so the
+// order (warp, item, lane) is the key order. The items of a warp are ranked
+// one after the other against the warp's running digit counts whist[w][d];
+// a key's block-local position is then (start of its digit in the block) +
+// (keys of that digit in earlier warps) + (its rank in its warp): stable.
+// The block's keys and slots are staged in shared memory in that order, so
+// that consecutive threads write consecutive positions of each digit's run
+// in the output (coalesced even when the digits are uniformly spread). About
+// 22 KB of shared memory and at most 36 registers per thread: 7 blocks per SM,
+// so all blocks of N = 2e6 keys are resident at once.
+__global__ void __launch_bounds__(kSortThreads, 7) k_sort_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, int64_t nblk,
     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ rowtot) {
-  constexpr int kSlots = kSortItems * (kSortThreads / 32);
-  static_assert(kSlots * 256 * sizeof(uint16_t) >= 2 * kSortTile * sizeof(uint32_t), "staging fits the counts");
-  __shared__ __align__(16) uint16_t cnt[kSlots][256];  // later: staged keys and slots
+  constexpr int kWarps = kSortThreads / 32;
+  static_assert(kSortItems * 32 <= 256 && kSortTile <= 65535, "per-warp counts fit 16 bits");
+  __shared__ uint16_t whist[kWarps][256];
+  __shared__ __align__(16) uint32_t sk[kSortTile];
+  __shared__ __align__(16) uint32_t sv[kSortTile];
   __shared__ uint32_t dbase[256];   // global start of digit d for this block
   __shared__ uint32_t lstart[256];  // block-local start of digit d
-  __shared__ uint32_t wsum[8];
+  __shared__ uint32_t wsum[kWarps];
   const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  for (int s = 0; s < kSlots; ++s) cnt[s][t] = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) whist[w][t] = 0;
   // exclusive scan of the digit totals -> global start of each digit
   {
     const uint32_t v = rowtot[t];
@@ -97,28 +105,36 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     for (unsigned w = 0; w < warp; ++w) woff += wsum[w];
     dbase[t] = woff + s - v + hist[int64_t(t) * nblk + blockIdx.x];
   }
-  __syncthreads();
   const int64_t base = int64_t(blockIdx.x) * kSortTile;
+  const int64_t wbase = base + int64_t(warp) * (32 * kSortItems);
   const unsigned lt = (1u << lane) - 1u;
-  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+  uint32_t key[kSortItems];
+  uint32_t wrank[(kSortItems + 3) / 4] = {};  // rank in the warp (< 256), one byte per item
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    const int64_t idx = base + int64_t(i) * kSortThreads + t;
-    const bool ok = idx < n;
-    key[i] = ok ? kin[idx] : 0u;
-    val[i] = ok ? vin[idx] : 0u;
+    const int64_t idx = wbase + 32 * i + lane;
+    key[i] = idx < n ? kin[idx] : 0u;
+  }
+  __syncthreads();  // whist zeroed, wsum consumed
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const bool ok = wbase + 32 * i + lane < n;
     const unsigned d = ok ? ((key[i] >> shift) & 255u) : 256u;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
-    rank[i] = __popc(peers & lt);
-    if (ok && lane == unsigned(__ffs(peers) - 1)) cnt[i * 8 + warp][d] = uint16_t(__popc(peers));
+    const unsigned before = ok ? unsigned(whist[warp][d]) : 0u;
+    wrank[i / 4] |= (before + __popc(peers & lt)) << (8 * (i % 4));
+    __syncwarp();
+    if (ok && lane == unsigned(__ffs(peers) - 1)) whist[warp][d] = uint16_t(before + __popc(peers));
+    __syncwarp();
   }
   __syncthreads();
-  uint32_t total;  // block count of digit t
+  uint32_t total;  // block count of digit t; whist[w][t] becomes the count in warps before w
   {
     uint32_t run = 0;
-    for (int s = 0; s < kSlots; ++s) {
-      const uint32_t c = cnt[s][t];
-      cnt[s][t] = uint16_t(run);
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = whist[w][t];
+      whist[w][t] = uint16_t(run);
       run += c;
     }
     total = run;
@@ -139,21 +155,14 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     lstart[t] = woff + s - total;
   }
   __syncthreads();
-  uint32_t lpos[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    const int64_t idx = base + int64_t(i) * kSortThreads + t;
-    const unsigned d = (key[i] >> shift) & 255u;
-    lpos[i] = idx < n ? lstart[d] + cnt[i * 8 + warp][d] + rank[i] : 0xffffffffu;
-  }
-  __syncthreads();  // the counts are consumed: their storage now stages the block
-  uint32_t* sk = reinterpret_cast<uint32_t*>(&cnt[0][0]);
-  uint32_t* sv = sk + kSortTile;
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    if (lpos[i] != 0xffffffffu) {
-      sk[lpos[i]] = key[i];
-      sv[lpos[i]] = val[i];
+    const int64_t idx = wbase + 32 * i + lane;
+    if (idx < n) {
+      const unsigned d = (key[i] >> shift) & 255u;
+      const uint32_t lpos = lstart[d] + whist[warp][d] + ((wrank[i / 4] >> (8 * (i % 4))) & 255u);
+      sk[lpos] = key[i];
+      sv[lpos] = vin[idx];
     }
   }
   __syncthreads();
