@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(kGsWarps * 32) k_group_sums(const double* __re
                                                               T* __restrict__ tot, double* __restrict__ totd,
                                                               int64_t ngroups, int nc, int64_t G, int nseg) {
   __shared__ double ws[kGsWarps][32];
+  __shared__ double sst[kGsMaxSeg][32];  // the segment sums of this column block (last CTA)
   __shared__ bool last;
   const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
@@ -431,13 +432,17 @@ __global__ void __launch_bounds__(kGsWarps * 32) k_group_sums(const double* __re
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // all warps stage the segment sums (independent loads in flight together),
+  // then warp 0 scans them from shared memory in a fixed order
+  for (int k = int(warp); k < nseg; k += kGsWarps) sst[k][lane] = okc ? __ldcg(ssum + int64_t(k) * nc + c) : 0.0;
+  __syncthreads();
   if (warp == 0 && okc) {
     double all = 0.0;
     const bool suffix = (c & 1) != 0;
     for (int k = 0; k < nseg; ++k) {
       const int s2 = suffix ? nseg - 1 - k : k;
       sbase[int64_t(s2) * nc + c] = all;
-      all += __ldcg(ssum + int64_t(s2) * nc + c);
+      all += sst[s2][lane];
     }
     tot[c] = T(all);
     totd[c] = all;

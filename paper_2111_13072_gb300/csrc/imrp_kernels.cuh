@@ -488,6 +488,9 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
             di = ni;
           }
           const int eb = offI(L, m) - k0 - (m > 1 ? m : 1);  // entry of degree l: eb + l
+          T cA[L + 1];  // the column's recurrence coefficients, loaded before its steps
+#pragma unroll
+          for (int j = 1; j <= L; ++j) cA[j] = m + j <= L + 1 ? tb.an[(m + j) * kTabL + m] : T(0);
           T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
           {
             const V4 ca = coefA[eb + m];
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
           for (int j = 1; j <= L; ++j) {
             const int l = m + j;
             if (l > L + 1) break;
-            const T A = tb.an[l * kTabL + m] * Zir2, B = ir2;
+            const T A = cA[j] * Zir2, B = ir2;
             const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
             c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
             const V4 ca = coefA[eb + l];
@@ -544,6 +547,9 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
             di = ni;
           }
           const int eb = NI + offR(L, m) - k0 - m;  // entry of degree l: eb + l
+          T cA[L];  // the column's recurrence coefficients, loaded before its steps
+#pragma unroll
+          for (int j = 1; j <= L - 1; ++j) cA[j] = m + j <= L - 1 ? tb.an[(m + j) * kTabL + m] : T(0);
           T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
           {
             const V4 ca = coefA[eb + m];
@@ -555,7 +561,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
           for (int j = 1; j <= L - 1; ++j) {
             const int l = m + j;
             if (l > L - 1) break;
-            const T A = tb.an[l * kTabL + m] * Zs, B = rs2;
+            const T A = cA[j] * Zs, B = rs2;
             const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
             c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
             const V4 ca = coefA[eb + l];
