@@ -213,6 +213,38 @@ def serving_measure(n_requests, steps, rate=20.0):
                         "l_max in {8,16}, mixed precision"}
 
 
+def drude_measure(temps=(2.0, 3.0, 5.0), N=500000, steps=10000):
+    """The paper's temperature diagnostic (Sec. 4) on its own case (R = 4 mm,
+    1 mm dielectric, n = 1e15 m^-3, 1 < r < 10, l <= 1 / m = 0 kernel, one
+    kick u_asy = 1, dt = 0.01) with the uniform Maxwellian shell in place of
+    its sheath: for each T_e one run, the admittance, the Drude dipole fit over
+    0 < w <= w_pe and K = nu_eff R / lambda_D. The paper, with its sheath,
+    reports nu_eff in {0.105, 0.128, 0.167} and K = 1.264."""
+    import torch
+    from paper_2111_13072_gb300 import imrp
+    from paper_2111_13072_gb300.inputs import paper_variant, workload_state
+    out = []
+    t0 = time.perf_counter()
+    for T in temps:
+        w = paper_variant(T, N=N, steps=steps)
+        x, v = workload_state(w)
+        with imrp.Sim(imrp.params_from_workload(w)) as sim:
+            sim.load(x, v)
+            sim.step_async(steps)
+            sim.sync()
+            sp = sim.spectrum(1000, 2.0, fit=True)
+        C, eta, nu, rel = imrp.drude_fit(sp["omega"], sp["reY"], sp["imY"], 0.0, 1.0)
+        out.append({"T_e_eV": T, "w_res": sp["w_res"], "dw": sp["dw"], "drude_eta": eta,
+                    "nu_eff": nu, "K": imrp.drude_k(nu, T, w.R_D_m, w.n_e_m3), "fit_rel_residual": rel,
+                    "damped_sine_b": float(sp["fit"][1])})
+    torch.cuda.synchronize()
+    return {"runs": out, "K_mean": float(np.mean([r["K"] for r in out])), "N": N, "steps": steps,
+            "seconds": time.perf_counter() - t0,
+            "workload": "paper's case: R=4 mm, R_E=3 mm, eps_D=4, n=1e15 m^-3, 1<r<10, l_max=1 m=0 kernel, "
+                        "kick u_asy=1, dt=0.01, uniform Maxwellian shell (no sheath), mixed precision",
+            "paper": {"nu_eff": [0.105, 0.128, 0.167], "K": 1.264}}
+
+
 def run_reference(args, w):
     """--impl reference: the FP64 CPU oracle as the reference arm."""
     import oracle
@@ -257,6 +289,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-drude", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -427,6 +460,7 @@ def main():
 
     serving = None if args.no_serving else serving_measure(12, 500)
     ensemble = None if args.no_ensemble else ensemble_measure(200, 4, autotune=False)
+    drude = None if (args.no_drude or rank != 0) else drude_measure()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -442,7 +476,7 @@ def main():
                            "l2": "inputs larger than L2 (per-step working set > 300 MB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks, "fp64_gpu": fp64,
-                "serving": serving, "ensemble": ensemble}
+                "serving": serving, "ensemble": ensemble, "drude": drude}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

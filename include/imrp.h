@@ -181,6 +181,31 @@ int imrp_get_particles(imrp_ctx* ctx, double* x, double* v);
 int imrp_spectrum(imrp_ctx* ctx, int64_t n_freq, double w_max, double* omega, double* reY,
                   double* imY, double* w_res, double* dw, double* fit);
 
+/* Drude fit of a kinetic admittance (Sec. 4, comparison with the Drude model):
+ * the dipole term of the Drude admittance,
+ *   Y_D(w) = C (1/(i w) + (i w + nu)/eta^2)^{-1} = C i w eta^2 / (eta^2 - w^2 + i w nu)
+ * (w, nu, eta in units of w_pe; eta w_pe is the resonance, nu the collision
+ * rate), is fitted to Y(w) = reY + i imY by least squares of the integral of
+ * |Y_D - Y|^2 over w_lo <= w <= w_hi (the paper integrates from 0 to w_pe),
+ * with the trapezoid rule on the given points. The sheath thickness of the
+ * paper enters Y_D only through C and eta, which are fitted directly; the
+ * vacuum term i w C_vac is left out, as in Q_diff (Sec. 4). The fitted nu is
+ * the effective collision rate nu_eff. Host computation (no GPU), on host
+ * arrays of n points with increasing omega.
+ * out[4]: C, eta, nu, and the relative residual
+ * sqrt(int |Y_D - Y|^2 / int |Y|^2).
+ * Errors: IMRP_E_INVAL (fewer than 5 points in the window, non-finite input,
+ * no positive peak of reY in the window). */
+int imrp_drude_fit(const double* omega, const double* reY, const double* imY, int64_t n,
+                   double w_lo, double w_hi, double* out);
+
+/* The paper's temperature diagnostic (Sec. 4): nu_eff = K lambda_D w_pe / R
+ * with lambda_D = sqrt(eps0 T_e / (n_e e)). imrp_drude_k gives K from nu_eff
+ * (in units of w_pe), T_e (eV), R (m) and n_e (m^-3); imrp_drude_te inverts it
+ * for T_e (eV) given K. Errors: IMRP_E_INVAL (non-positive argument). */
+int imrp_drude_k(double nu_eff_wpe, double T_e_eV, double R_m, double n_e_m3, double* K);
+int imrp_drude_te(double nu_eff_wpe, double K, double R_m, double n_e_m3, double* T_e_eV);
+
 /* Derived quantities of the context. */
 int imrp_get_info(const imrp_ctx* ctx, imrp_info* info);
 

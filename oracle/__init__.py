@@ -339,3 +339,60 @@ def fit_damped_sine(qd, dt, t_fit, w0, b0, t_start=0.0):
     if a < 0:
         a, ph = -a, ph + np.pi
     return np.array([a, b, c, np.mod(ph, 2 * np.pi)])
+
+
+def drude_admittance(omega, C, eta, nu):
+    """Dipole term of the Drude admittance (Sec. 4), w in units of w_pe:
+    Y_D = C (1/(i w) + (i w + nu)/eta^2)^{-1}."""
+    omega = np.asarray(omega, dtype=np.float64)
+    return C / (1.0 / (1j * omega) + (1j * omega + nu) / eta ** 2)
+
+
+def drude_fit(omega, Y, w_lo=0.0, w_hi=1.0):
+    """Least squares of int_{w_lo}^{w_hi} |Y_D(C, eta, nu; w) - Y(w)|^2 dw (Sec. 4:
+    the integral I, here of the squared modulus, trapezoid rule on the given
+    points) over C, eta > 0, nu > 0. Starting point: eta at the largest Re Y,
+    nu its full width at half maximum. Returns (C, eta, nu, relative residual)."""
+    from scipy.optimize import least_squares
+    omega = np.asarray(omega, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.complex128)
+    m = (omega >= w_lo) & (omega <= w_hi)
+    w, y = omega[m], Y[m]
+    if w.size < 5:
+        raise ValueError("fewer than 5 points in the window")
+    h = np.diff(w)
+    wt = np.zeros(w.size)
+    wt[:-1] += 0.5 * h
+    wt[1:] += 0.5 * h
+    sw = np.sqrt(wt)
+    eta0, nu0 = peak_and_fwhm(w, y.real)
+    if not nu0 > 0:
+        nu0 = 0.1 * eta0
+    g0 = drude_admittance(w, 1.0, eta0, nu0)
+    C0 = float(np.sum(wt * (g0.conj() * y).real) / np.sum(wt * np.abs(g0) ** 2))
+
+    def res(p):
+        d = sw * (drude_admittance(w, p[0], p[1], p[2]) - y)
+        return np.concatenate([d.real, d.imag])
+
+    sol = least_squares(res, [C0, eta0, nu0], bounds=([-np.inf, 1e-12, 1e-12], [np.inf, np.inf, np.inf]),
+                        xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=20000)
+    C, eta, nu = sol.x
+    rel = float(np.sqrt(np.sum(res(sol.x) ** 2) / np.sum(wt * np.abs(y) ** 2)))
+    return float(C), float(eta), float(nu), rel
+
+
+def debye_over_R(T_e_eV, n_e_m3, R_m):
+    """lambda_D / R with lambda_D = sqrt(eps0 T_e / (n_e e)) (T_e in eV)."""
+    return float(np.sqrt(EPS0 * T_e_eV / (n_e_m3 * E_CHARGE)) / R_m)
+
+
+def drude_K(nu_eff_wpe, T_e_eV, R_m, n_e_m3):
+    """K of the paper's diagnostic nu_eff = K lambda_D w_pe / R (Sec. 4)."""
+    return float(nu_eff_wpe / debye_over_R(T_e_eV, n_e_m3, R_m))
+
+
+def drude_Te(nu_eff_wpe, K, R_m, n_e_m3):
+    """T_e (eV) from nu_eff (units of w_pe) and K, the inverse of drude_K."""
+    lam = nu_eff_wpe * R_m / K
+    return float(lam * lam * n_e_m3 * E_CHARGE / EPS0)

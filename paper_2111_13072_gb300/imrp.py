@@ -22,7 +22,8 @@ EXPORTS = [
     "imrp_get_field", "imrp_get_particles", "imrp_spectrum", "imrp_get_info", "imrp_profile_steps",
     "imrp_field_noalloc", "imrp_autotune", "imrp_batch_create", "imrp_batch_step", "imrp_batch_sync",
     "imrp_batch_destroy", "imrp_batch_last_error", "imrp_batch_set_stream", "imrp_footprint",
-    "imrp_load_particles_async", "imrp_copy_qdiff_async",
+    "imrp_load_particles_async", "imrp_copy_qdiff_async", "imrp_drude_fit", "imrp_drude_k",
+    "imrp_drude_te",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -99,6 +100,9 @@ def load_library(path: str = LIB_PATH):
     L.imrp_batch_last_error.argtypes = [c_void_p]
     L.imrp_batch_last_error.restype = ctypes.c_char_p
     L.imrp_field_noalloc.argtypes = [P(Params), c_void_p, ctypes.c_int64, ctypes.c_int64, c_void_p, c_void_p]
+    L.imrp_drude_fit.argtypes = [pd, pd, pd, ctypes.c_int64, ctypes.c_double, ctypes.c_double, pd]
+    L.imrp_drude_k.argtypes = [ctypes.c_double] * 4 + [pd]
+    L.imrp_drude_te.argtypes = [ctypes.c_double] * 4 + [pd]
     for name in EXPORTS:
         if name not in ("imrp_default_params", "imrp_last_error", "imrp_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -136,6 +140,37 @@ def field_noalloc(params: Params, x_dev_ptr: int, n: int, step: int, E_dev_ptr: 
                                            ctypes.c_void_p(E_dev_ptr), ctypes.c_void_p(stream_ptr or 0))
     if rc != 0:
         raise IMRPError(rc, "imrp_field_noalloc failed")
+
+
+def drude_fit(omega, reY, imY, w_lo: float = 0.0, w_hi: float = 1.0):
+    """imrp_drude_fit: (C, eta, nu, relative residual) of the Drude dipole
+    admittance fitted to Y = reY + i imY over w_lo <= omega <= w_hi (units of w_pe)."""
+    w = np.ascontiguousarray(omega, dtype=np.float64)
+    re = np.ascontiguousarray(reY, dtype=np.float64)
+    im = np.ascontiguousarray(imY, dtype=np.float64)
+    out = np.zeros(4)
+    rc = load_library().imrp_drude_fit(_ptr(w), _ptr(re), _ptr(im), w.size, w_lo, w_hi, _ptr(out))
+    if rc != 0:
+        raise IMRPError(rc, "imrp_drude_fit failed")
+    return tuple(float(v) for v in out)
+
+
+def drude_k(nu_eff_wpe: float, T_e_eV: float, R_m: float, n_e_m3: float) -> float:
+    """imrp_drude_k: K of nu_eff = K lambda_D w_pe / R."""
+    out = np.zeros(1)
+    rc = load_library().imrp_drude_k(nu_eff_wpe, T_e_eV, R_m, n_e_m3, _ptr(out))
+    if rc != 0:
+        raise IMRPError(rc, "imrp_drude_k failed")
+    return float(out[0])
+
+
+def drude_te(nu_eff_wpe: float, K: float, R_m: float, n_e_m3: float) -> float:
+    """imrp_drude_te: T_e (eV) from nu_eff (units of w_pe) and K."""
+    out = np.zeros(1)
+    rc = load_library().imrp_drude_te(nu_eff_wpe, K, R_m, n_e_m3, _ptr(out))
+    if rc != 0:
+        raise IMRPError(rc, "imrp_drude_te failed")
+    return float(out[0])
 
 
 def footprint(params: Params, n_steps: int) -> int:

@@ -40,6 +40,7 @@ class Workload:
     R_D_m: float = 5e-3
     eps_D: float = 4.0
     outer_debye: float = 20.0          # outer wall at R_D + outer_debye * lambda_D
+    outer_R: float = 0.0               # if > 0: outer wall at outer_R * R_D instead
     dt: float = 0.05
     steps: int = 2000
     drive_kind: int = 0                # 0 Gaussian pulse, 1 impulse, 2 off
@@ -54,6 +55,8 @@ class Workload:
 
     @property
     def R_out_m(self) -> float:
+        if self.outer_R > 0:
+            return self.outer_R * self.R_D_m
         return self.R_D_m + self.outer_debye * debye_length_m(self.n_e_m3, self.T_e_eV)
 
     @property
@@ -78,6 +81,18 @@ WORKLOADS = {
     "mixed_n1.6e7_l24": Workload("mixed_n1.6e7_l24", N=16000000, l_max=24, T_e_eV=2.0,
                                  n_e_m3=1e16, outer_debye=40.0, steps=5000, precision=1, seed=0),
 }
+
+
+def paper_variant(T_e_eV: float, N: int = 500000, steps: int = 10000, seed: int = 0) -> Workload:
+    """The paper's own case (Sec. 4): probe radius R = 4 mm with a 1 mm dielectric
+    (R_E = 3 mm), n = 1e15 m^-3, domain 1 < r < 10, the l <= 1, m = 0 kernel
+    (Sec. 3), a single kick u_asy = 1 at the first step (289 V in the units
+    eps0 V / (n e R^2) = u), dt = 0.01. The plasma here is the uniform
+    Maxwellian shell, not the paper's sheath equilibrium (App. D), and
+    eps_D = 4 (the paper does not state it)."""
+    return Workload(f"paper_m0_l1_T{T_e_eV:g}", N=N, l_max=1, T_e_eV=T_e_eV, n_e_m3=1e15,
+                    R_E_m=3e-3, R_D_m=4e-3, eps_D=4.0, outer_R=10.0, dt=0.01, steps=steps,
+                    drive_kind=1, V_volts=289.0, precision=1, seed=seed, m0_only=1)
 
 
 def maxwellian_shell(N: int, r_out: float, sigma_v: float, seed: int = 0,

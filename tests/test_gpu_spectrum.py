@@ -2,9 +2,11 @@
 fit) of the GPU path against the FP64 oracle.
 
 1. The spectrum computation itself on the same recorded Q_diff and u_asy
-   series: the GPU's FP64 DFT and host fit against the oracle's.
+   series: the GPU's FP64 DFT and host fits (damped sine, Drude dipole term)
+   against the oracle's.
 2. Whole runs from the same seeded state: trajectories are chaotic, so the
-   comparison is statistical -- resonance within 1 %, half-width within 5 %.
+   comparison is statistical -- resonance within 1 %, half-width and the
+   Drude fit's nu_eff within 5 %.
 """
 import numpy as np
 import pytest
@@ -61,6 +63,10 @@ def test_spectrum_computation_matches_oracle(imrp, prec):
     assert sp["dw"] == pytest.approx(dw, rel=1e-9)
     fo = oracle.fit_damped_sine(q, W.dt, op.t0 + 3 * op.sigma, wr, dw / 2)
     np.testing.assert_allclose(sp["fit"][:3], fo[:3], rtol=1e-4)
+    # Drude dipole fit over 0 < w <= w_pe (Sec. 4) of the same admittance
+    dg = imrp.drude_fit(sp["omega"], sp["reY"], sp["imY"], 0.0, 1.0)
+    do = oracle.drude_fit(om, Y, 0.0, 1.0)
+    np.testing.assert_allclose(dg[:3], do[:3], rtol=1e-6)
 
 
 SEEDS = (0, 1, 2, 3, 4, 5)
@@ -68,14 +74,15 @@ NRUN = 800
 
 
 def _avg_spectrum(runs):
-    """Ensemble average of Y over runs of (q, u); peak and width of the mean Re Y."""
+    """Ensemble average of Y over runs of (q, u); peak and width of the mean Re Y
+    and the oracle's Drude fit of the mean Y."""
     Ys = []
     for q, u in runs:
         om, Y, _, _ = oracle.spectrum(q, u, W.dt, NF, WMAX)
         Ys.append(Y)
     Ym = np.mean(Ys, axis=0)
     wr, dw = oracle.peak_and_fwhm(om, Ym.real)
-    return wr, dw
+    return wr, dw, oracle.drude_fit(om, Ym, 0.0, 1.0)[2]
 
 
 @pytest.fixture(scope="module")
@@ -96,7 +103,7 @@ def oracle_ensemble():
 def test_run_spectrum_statistics(imrp, oracle_ensemble, prec):
     """Ensemble of 6 seeds on each side (same seeded states, same wall keys):
     the mean admittance peaks within 1 % and its half-width within 5 %."""
-    runs = []
+    runs, spectra = [], []
     for seed in SEEDS:
         w = Workload("spectrum", N=W.N, l_max=W.l_max, T_e_eV=W.T_e_eV, n_e_m3=W.n_e_m3,
                      drive_kind=W.drive_kind, V_volts=W.V_volts, width_wpe=W.width_wpe, seed=seed)
@@ -104,8 +111,14 @@ def test_run_spectrum_statistics(imrp, oracle_ensemble, prec):
         with imrp.Sim(imrp.params_from_workload(w, precision=prec)) as sim:
             sim.load(x, v)
             q, u = sim.step(NRUN)
+            spectra.append(sim.spectrum(NF, WMAX, fit=False))
         runs.append((q, u))
-    wr, dw = _avg_spectrum(runs)
-    wr_o, dw_o = oracle_ensemble
+    wr, dw, _ = _avg_spectrum(runs)
+    wr_o, dw_o, nu_o = oracle_ensemble
     assert wr == pytest.approx(wr_o, rel=0.01)
     assert dw == pytest.approx(dw_o, rel=0.05)
+    # the library's Drude fit of the GPU-computed mean admittance
+    reY = np.mean([sp["reY"] for sp in spectra], axis=0)
+    imY = np.mean([sp["imY"] for sp in spectra], axis=0)
+    nu = imrp.drude_fit(spectra[0]["omega"], reY, imY, 0.0, 1.0)[2]
+    assert nu == pytest.approx(nu_o, rel=0.05)
