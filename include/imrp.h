@@ -181,6 +181,31 @@ int imrp_get_particles(imrp_ctx* ctx, double* x, double* v);
 int imrp_spectrum(imrp_ctx* ctx, int64_t n_freq, double w_max, double* omega, double* reY,
                   double* imY, double* w_res, double* dw, double* fit);
 
+/* Admittance of a given series (Sec. 4), the transform of imrp_spectrum applied
+ * to host arrays q[ns] (Q_diff at t_n = n dt) and u[ns] (u_asy at t_n): for
+ * example the difference of two runs from the same state with and without the
+ * kick (the spontaneous fluctuations, identical in both, cancel), or an
+ * ensemble mean. Y(w) = i w Q^(w)/U^(w), Q^ = dt sum_n (q_n - q_0) e^{-i w t_n},
+ * U^ = sum_n k_n u_n e^{-i w t_n} with k_0 = first_kick and k_n = dt after it,
+ * at w_j = (j+1) w_max / n_freq; the sums run on the GPU (current device) in
+ * FP64. omega, reY, imY: host arrays of n_freq (any may be NULL).
+ * Errors: IMRP_E_INVAL (ns < 8, n_freq < 3, w_max <= 0, dt <= 0), IMRP_E_NOMEM,
+ * IMRP_E_CUDA. */
+int imrp_admittance(const double* q, const double* u, int64_t ns, double dt, double first_kick,
+                    int64_t n_freq, double w_max, double* omega, double* reY, double* imY);
+
+/* Damped-sine fit of a given series (Sec. 4, the paper's fit of the charge
+ * difference, s = 1): least squares of a e^{-b tau} sin(c tau + phi),
+ * tau = t - t_fit, against q_n - q_0 over t_fit <= t_n = n dt <= t_end, from
+ * the starting rate b0 and frequency w0 (best of four starting phases), as
+ * imrp_spectrum does for a context's own series. After a kick of unit area its
+ * transform is the Drude dipole term with nu = 2 b, eta = sqrt(b^2 + c^2),
+ * C = a c / eta^2. fit[4] = a, b, c, phi (a >= 0, c >= 0, 0 <= phi < 2 pi).
+ * Host computation. Errors: IMRP_E_INVAL (fewer than 8 points in the window,
+ * non-positive w0, b0 or dt, no convergence). */
+int imrp_fit_damped_sine(const double* q, int64_t ns, double dt, double t_fit, double t_end, double w0,
+                         double b0, double* fit);
+
 /* Drude fit of a kinetic admittance (Sec. 4, comparison with the Drude model):
  * the dipole term of the Drude admittance,
  *   Y_D(w) = C (1/(i w) + (i w + nu)/eta^2)^{-1} = C i w eta^2 / (eta^2 - w^2 + i w nu)

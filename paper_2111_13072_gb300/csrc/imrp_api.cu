@@ -1048,6 +1048,26 @@ double fit_model(const std::vector<double>& tau, const std::vector<double>& y, d
   return cur;
 }
 
+// Best of four starting phases; reports a >= 0, c >= 0, phi in [0, 2 pi).
+void fit_damped(const std::vector<double>& tau, const std::vector<double>& y, double b0, double w0,
+                double best[4]) {
+  for (int k = 0; k < 4; ++k) best[k] = NAN;
+  if (tau.size() < 8) return;
+  double amax = 0;
+  for (double v : y) amax = std::max(amax, fabs(v));
+  double bres = INFINITY;
+  const double phs[4] = {0.0, kPi / 2, kPi, -kPi / 2};
+  for (double ph : phs) {
+    double pp[4] = {amax > 0 ? amax : 1.0, b0, w0, ph};
+    const double r = fit_model(tau, y, pp);
+    if (r < bres && std::isfinite(r)) { bres = r; memcpy(best, pp, 4 * sizeof(double)); }
+  }
+  if (best[2] < 0) { best[2] = -best[2]; best[3] = kPi - best[3]; }
+  if (best[0] < 0) { best[0] = -best[0]; best[3] += kPi; }
+  best[3] = fmod(best[3], 2.0 * kPi);
+  if (best[3] < 0) best[3] += 2.0 * kPi;
+}
+
 }  // namespace
 
 extern "C" int imrp_spectrum(imrp_ctx* ctx, int64_t n_freq, double w_max, double* omega, double* reY,
@@ -1089,30 +1109,66 @@ extern "C" int imrp_spectrum(imrp_ctx* ctx, int64_t n_freq, double w_max, double
   if (fit) {
     const double tfit = ctx->p.drive_kind == 0 ? ctx->t0 + 3.0 * ctx->p.width_wpe : 0.0;
     std::vector<double> tau, y;
-    double amax = 0;
     for (int64_t k = 0; k < ns; ++k) {
       const double t = k * dt;
       if (t >= tfit) {
         tau.push_back(t - tfit);
         y.push_back(q[k] - q[0]);
-        amax = std::max(amax, fabs(q[k] - q[0]));
       }
     }
-    double best[4] = {NAN, NAN, NAN, NAN}, bres = INFINITY;
-    if (tau.size() >= 8) {
-      const double phs[4] = {0.0, kPi / 2, kPi, -kPi / 2};
-      for (double ph : phs) {
-        double pp[4] = {amax > 0 ? amax : 1.0, std::max(0.5 * width, 1e-3), wr, ph};
-        const double r = fit_model(tau, y, pp);
-        if (r < bres && std::isfinite(r)) { bres = r; memcpy(best, pp, sizeof(pp)); }
-      }
-      // one curve, several parameter sets: report a >= 0, c >= 0, phi in [0, 2 pi)
-      if (best[2] < 0) { best[2] = -best[2]; best[3] = kPi - best[3]; }
-      if (best[0] < 0) { best[0] = -best[0]; best[3] += kPi; }
-      best[3] = fmod(best[3], 2.0 * kPi);
-      if (best[3] < 0) best[3] += 2.0 * kPi;
+    fit_damped(tau, y, std::max(0.5 * width, 1e-3), wr, fit);
+  }
+  return IMRP_OK;
+}
+
+extern "C" int imrp_fit_damped_sine(const double* q, int64_t ns, double dt, double t_fit, double t_end,
+                                    double w0, double b0, double* fit) {
+  if (!q || !fit || ns < 1 || !(dt > 0) || !(t_end > t_fit) || !(w0 > 0) || !(b0 > 0)) return IMRP_E_INVAL;
+  std::vector<double> tau, y;
+  for (int64_t k = 0; k < ns; ++k) {
+    const double t = k * dt;
+    if (t >= t_fit && t <= t_end) {
+      tau.push_back(t - t_fit);
+      y.push_back(q[k] - q[0]);
     }
-    memcpy(fit, best, sizeof(best));
+  }
+  if (tau.size() < 8) return IMRP_E_INVAL;
+  fit_damped(tau, y, b0, w0, fit);
+  return std::isfinite(fit[0]) ? IMRP_OK : IMRP_E_INVAL;
+}
+
+extern "C" int imrp_admittance(const double* q, const double* u, int64_t ns, double dt, double first_kick,
+                               int64_t n_freq, double w_max, double* omega, double* reY, double* imY) {
+  if (!q || !u || ns < 8 || n_freq < 3 || !(w_max > 0) || !(dt > 0)) return IMRP_E_INVAL;
+  double *dq = nullptr, *du = nullptr, *dout = nullptr;
+  const size_t bs = size_t(ns) * sizeof(double), bo = size_t(4 * n_freq) * sizeof(double);
+  if (cudaMalloc(&dq, bs) != cudaSuccess || cudaMalloc(&du, bs) != cudaSuccess ||
+      cudaMalloc(&dout, bo) != cudaSuccess) {
+    cudaFree(dq);
+    cudaFree(du);
+    cudaFree(dout);
+    return IMRP_E_NOMEM;
+  }
+  std::vector<double> h(4 * n_freq);
+  cudaError_t e = cudaMemcpy(dq, q, bs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(du, u, bs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    launch_dft(dq, du, ns, dt, first_kick, n_freq, w_max, dout, 0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h.data(), dout, bo, cudaMemcpyDeviceToHost);
+  cudaFree(dq);
+  cudaFree(du);
+  cudaFree(dout);
+  if (e != cudaSuccess) return IMRP_E_CUDA;
+  for (int64_t j = 0; j < n_freq; ++j) {
+    const double w = double(j + 1) * (w_max / double(n_freq));
+    const double Qr = h[4 * j], Qi = h[4 * j + 1], Ur = h[4 * j + 2], Ui = h[4 * j + 3];
+    const double den = Ur * Ur + Ui * Ui;
+    const double Rr = (Qr * Ur + Qi * Ui) / den, Ri = (Qi * Ur - Qr * Ui) / den;  // Q/U
+    if (omega) omega[j] = w;
+    if (reY) reY[j] = -w * Ri;
+    if (imY) imY[j] = w * Rr;
   }
   return IMRP_OK;
 }

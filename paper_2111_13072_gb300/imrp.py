@@ -23,7 +23,7 @@ EXPORTS = [
     "imrp_field_noalloc", "imrp_autotune", "imrp_batch_create", "imrp_batch_step", "imrp_batch_sync",
     "imrp_batch_destroy", "imrp_batch_last_error", "imrp_batch_set_stream", "imrp_footprint",
     "imrp_load_particles_async", "imrp_copy_qdiff_async", "imrp_drude_fit", "imrp_drude_k",
-    "imrp_drude_te",
+    "imrp_drude_te", "imrp_admittance", "imrp_fit_damped_sine",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -100,6 +100,9 @@ def load_library(path: str = LIB_PATH):
     L.imrp_batch_last_error.argtypes = [c_void_p]
     L.imrp_batch_last_error.restype = ctypes.c_char_p
     L.imrp_field_noalloc.argtypes = [P(Params), c_void_p, ctypes.c_int64, ctypes.c_int64, c_void_p, c_void_p]
+    L.imrp_admittance.argtypes = [pd, pd, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                  ctypes.c_double, pd, pd, pd]
+    L.imrp_fit_damped_sine.argtypes = [pd, ctypes.c_int64] + [ctypes.c_double] * 5 + [pd]
     L.imrp_drude_fit.argtypes = [pd, pd, pd, ctypes.c_int64, ctypes.c_double, ctypes.c_double, pd]
     L.imrp_drude_k.argtypes = [ctypes.c_double] * 4 + [pd]
     L.imrp_drude_te.argtypes = [ctypes.c_double] * 4 + [pd]
@@ -140,6 +143,28 @@ def field_noalloc(params: Params, x_dev_ptr: int, n: int, step: int, E_dev_ptr: 
                                            ctypes.c_void_p(E_dev_ptr), ctypes.c_void_p(stream_ptr or 0))
     if rc != 0:
         raise IMRPError(rc, "imrp_field_noalloc failed")
+
+
+def admittance(q, u, dt: float, first_kick: float, n_freq: int = 1000, w_max: float = 2.0):
+    """imrp_admittance: (omega, reY, imY) of host series q (Q_diff) and u (u_asy)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    om, re, im = np.zeros(n_freq), np.zeros(n_freq), np.zeros(n_freq)
+    rc = load_library().imrp_admittance(_ptr(q), _ptr(u), q.size, dt, first_kick, n_freq, w_max,
+                                        _ptr(om), _ptr(re), _ptr(im))
+    if rc != 0:
+        raise IMRPError(rc, "imrp_admittance failed")
+    return om, re, im
+
+
+def fit_damped_sine(q, dt: float, t_fit: float, t_end: float, w0: float, b0: float):
+    """imrp_fit_damped_sine: (a, b, c, phi) of a e^{-b tau} sin(c tau + phi)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros(4)
+    rc = load_library().imrp_fit_damped_sine(_ptr(q), q.size, dt, t_fit, t_end, w0, b0, _ptr(out))
+    if rc != 0:
+        raise IMRPError(rc, "imrp_fit_damped_sine failed")
+    return out
 
 
 def drude_fit(omega, reY, imY, w_lo: float = 0.0, w_hi: float = 1.0):

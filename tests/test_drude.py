@@ -118,3 +118,19 @@ def test_drude_fit_rejects_bad_input(imrp):
         imrp.drude_fit(w[::-1], y.real, y.imag, 0.0, 1.0)  # omega not increasing
     with pytest.raises(imrp.IMRPError):
         imrp.drude_k(-0.1, 3.0, 0.004, 1e15)
+
+
+def test_damped_sine_fit_of_a_series(imrp):
+    """The library's fit of a given series returns the paper's printed signal
+    (Sec. 4) from its samples, as the oracle's fit does, within a time window."""
+    g, _ = _golden()
+    a, b, c = g["a"], g["b"], g["c"]
+    dt = 0.01
+    t = dt * np.arange(6000)
+    q = a * np.exp(-b * t) * np.sin(c * t)
+    q[t > 40.0] += 5.0  # outside the window: must not matter
+    fit = imrp.fit_damped_sine(q, dt, 0.0, 40.0, 0.5, 0.05)
+    np.testing.assert_allclose(fit[:3], [a, b, c], rtol=1e-9)
+    assert min(fit[3], 2 * np.pi - fit[3]) < 1e-8
+    fo = oracle.fit_damped_sine(q[t <= 40.0], dt, 0.0, 0.5, 0.05)
+    np.testing.assert_allclose(fit[:3], fo[:3], rtol=1e-8)

@@ -63,6 +63,12 @@ def test_spectrum_computation_matches_oracle(imrp, prec):
     assert sp["dw"] == pytest.approx(dw, rel=1e-9)
     fo = oracle.fit_damped_sine(q, W.dt, op.t0 + 3 * op.sigma, wr, dw / 2)
     np.testing.assert_allclose(sp["fit"][:3], fo[:3], rtol=1e-4)
+    # the transform of given series (imrp_admittance) is the same computation
+    # (to the rounding of the host's FMA contraction)
+    om2, re2, im2 = imrp.admittance(q, u, W.dt, 0.5 * W.dt, NF, WMAX)
+    np.testing.assert_array_equal(om2, sp["omega"])
+    np.testing.assert_allclose(re2, sp["reY"], rtol=0, atol=1e-13 * scale)
+    np.testing.assert_allclose(im2, sp["imY"], rtol=0, atol=1e-13 * scale)
     # Drude dipole fit over 0 < w <= w_pe (Sec. 4) of the same admittance
     dg = imrp.drude_fit(sp["omega"], sp["reY"], sp["imY"], 0.0, 1.0)
     do = oracle.drude_fit(om, Y, 0.0, 1.0)
@@ -122,3 +128,23 @@ def test_run_spectrum_statistics(imrp, oracle_ensemble, prec):
     imY = np.mean([sp["imY"] for sp in spectra], axis=0)
     nu = imrp.drude_fit(spectra[0]["omega"], reY, imY, 0.0, 1.0)[2]
     assert nu == pytest.approx(nu_o, rel=0.05)
+
+
+def test_admittance_of_a_correlated_pair(imrp):
+    """Runs from one state with and without the drive share their spontaneous
+    fluctuations (same particles, same wall random numbers); the admittance of
+    the difference of their Q_diff is the oracle's transform of that series."""
+    x, v = workload_state(W)
+    qs = {}
+    for kind in (0, 2):
+        with imrp.Sim(imrp.params_from_workload(W, precision=1, drive_kind=kind)) as sim:
+            sim.load(x, v)
+            qs[kind] = sim.step(400)
+    dq = qs[0][0] - qs[2][0]
+    om, re, im = imrp.admittance(dq, qs[0][1], W.dt, 0.5 * W.dt, 300, WMAX)
+    omo, Yo, _, _ = oracle.spectrum(dq, qs[0][1], W.dt, 300, WMAX)
+    np.testing.assert_allclose(om, omo, rtol=1e-14)
+    scale = np.max(np.abs(Yo))
+    np.testing.assert_allclose(re, Yo.real, rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(im, Yo.imag, rtol=0, atol=1e-9 * scale)
+    assert not np.any(qs[2][1])  # no drive in the second run
