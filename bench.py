@@ -246,13 +246,20 @@ def drude_measure(temps=(2.0, 3.0, 5.0), N=500000, steps=3000, seeds=4, t_win=30
                     series[kind] = sim.qdiff()
             dqs.append(series[w.drive_kind][0] - series[2][0])
             u = series[w.drive_kind][1]
-        dq = np.mean(dqs, axis=0)
-        om, re, im = imrp.admittance(dq, u, w.dt, 0.5 * w.dt, 1000, 2.0)
-        w0 = float(om[int(np.argmax(re))])
-        a, b, c, ph = imrp.fit_damped_sine(dq, w.dt, 0.0, t_win, w0, 0.05)
+        def fit(dq):
+            om, re, im = imrp.admittance(dq, u, w.dt, 0.5 * w.dt, 1000, 2.0)
+            w0 = float(om[int(np.argmax(re))])
+            try:
+                return imrp.fit_damped_sine(dq, w.dt, 0.0, t_win, w0, 0.05)
+            except imrp.IMRPError:
+                return np.full(4, np.nan)
+
+        a, b, c, ph = fit(np.mean(dqs, axis=0))
+        h = len(dqs) // 2  # the two halves of the seeds, fitted apart: a spread
+        halves = [2.0 * float(fit(np.mean(dqs[:h], axis=0))[1]), 2.0 * float(fit(np.mean(dqs[h:], axis=0))[1])]
         nu = 2.0 * b
         out.append({"T_e_eV": T, "fit_a_b_c_phi": [float(a), float(b), float(c), float(ph)],
-                    "nu_eff": float(nu), "drude_eta": float(np.hypot(b, c)),
+                    "nu_eff": float(nu), "nu_eff_halves": halves, "drude_eta": float(np.hypot(b, c)),
                     "K": imrp.drude_k(nu, T, w.R_D_m, w.n_e_m3) if nu > 0 else None})
     torch.cuda.synchronize()
     Ks = [r["K"] for r in out if r["K"] is not None]
@@ -308,7 +315,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
-    ap.add_argument("--no-drude", action="store_true")
+    ap.add_argument("--drude", action="store_true",
+                    help="also run the T_e sweep of the temperature diagnostic on the paper's case")
+    ap.add_argument("--drude-n", type=int, default=500000)
+    ap.add_argument("--drude-seeds", type=int, default=4)
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -479,7 +489,7 @@ def main():
 
     serving = None if args.no_serving else serving_measure(12, 500)
     ensemble = None if args.no_ensemble else ensemble_measure(200, 4, autotune=False)
-    drude = None if (args.no_drude or rank != 0) else drude_measure()
+    drude = drude_measure(N=args.drude_n, seeds=args.drude_seeds) if (args.drude and rank == 0) else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
