@@ -58,7 +58,7 @@ class _FieldParams(ctypes.Structure):
 class _RunParams(ctypes.Structure):
     _fields_ = [("fp", _FieldParams), ("dt", ctypes.c_double), ("drive_kind", ctypes.c_int32),
                 ("wall_rule", ctypes.c_int32), ("v_hat", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("t0", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("t0", ctypes.c_double), ("seed", ctypes.c_uint64), ("nu_coll", ctypes.c_double)]
 
 
 _lib = None
@@ -85,6 +85,10 @@ def lib():
         _lib.orc_drive.argtypes = [P(_RunParams), i64]
         _lib.orc_drive.restype = d
         _lib.orc_run.argtypes = [P(_RunParams), i64, pd, pd, pi64, i64, i64, i32, i32, pd, pd]
+        _lib.orc_collisions.argtypes = [P(_RunParams), i64, pd, pi64, i64]
+        _lib.orc_collisions.restype = i64
+        _lib.orc_coll_threshold.argtypes = [ctypes.c_double, ctypes.c_double]
+        _lib.orc_coll_threshold.restype = ctypes.c_uint32
         _lib.orc_run.restype = i64
     return _lib
 
@@ -112,6 +116,7 @@ class Params:
     sigma: float = 2.0
     t0: float = 8.0
     seed: int = 0
+    nu_coll: float = 0.0
 
     def field(self) -> _FieldParams:
         return _FieldParams(self.d, self.eps, self.r_out, self.n_tilde, self.n_ion, self.q_s,
@@ -119,12 +124,12 @@ class Params:
 
     def run(self) -> _RunParams:
         return _RunParams(self.field(), self.dt, self.drive_kind, self.wall_rule, self.v_hat,
-                          self.sigma, self.t0, self.seed)
+                          self.sigma, self.t0, self.seed, self.nu_coll)
 
 
 def from_physical(R_E_m, R_D_m, eps_D, R_out_m, n_e_m3, T_e_eV, N, l_max, dt, drive_kind=0,
                   V_volts=1.0, width_wpe=2.0, t0_wpe=None, wall_rule=0, self_image=0,
-                  m0_only=0, seed=0) -> Params:
+                  m0_only=0, seed=0, nu_coll=0.0) -> Params:
     """Converts a physical configuration to the dimensionless problem of Sec. 4.
 
     Length unit R = R_D (outer radius of the dielectric); d = 1 - R_E/R.
@@ -141,7 +146,7 @@ def from_physical(R_E_m, R_D_m, eps_D, R_out_m, n_e_m3, T_e_eV, N, l_max, dt, dr
     t0 = 4.0 * width_wpe if t0_wpe is None else t0_wpe
     return Params(d=d, eps=eps_D, r_out=r_out, n_tilde=n_tilde, n_ion=float(N), L=l_max, dt=dt,
                   drive_kind=drive_kind, v_hat=v_hat, sigma=width_wpe, t0=t0, wall_rule=wall_rule,
-                  self_image=self_image, m0_only=m0_only, seed=seed)
+                  self_image=self_image, m0_only=m0_only, seed=seed, nu_coll=nu_coll)
 
 
 def debye_length(n_e_m3, T_e_eV):
@@ -226,6 +231,20 @@ def philox4x32_10(ctr, key):
     o = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32), _p(o, ctypes.c_uint32))
     return o
+
+
+def collisions(p: Params, v, step, ids=None):
+    """The collision operator alone on velocities v [n,3] at a step index:
+    returns (v after, number of collisions)."""
+    v = np.array(v, dtype=np.float64, order="C", copy=True)
+    ids = _ids(v.shape[0], ids)
+    rp = p.run()
+    c = lib().orc_collisions(ctypes.byref(rp), v.shape[0], _p(v), _p(ids, ctypes.c_int64), step)
+    return v, int(c)
+
+
+def coll_threshold(nu, dt):
+    return int(lib().orc_coll_threshold(nu, dt))
 
 
 def drive(p: Params, step):

@@ -76,6 +76,7 @@ typedef struct {
   double sigma;    /* Gaussian pulse width                               */
   double t0;       /* Gaussian pulse centre                              */
   uint64_t seed;   /* wall random-number key                             */
+  double nu_coll;  /* electron-neutral collision rate nu (units of omega_pe), 0: none */
 } orc_run_params;
 
 /* ------------------------------------------------------------------ */
@@ -629,6 +630,51 @@ static int orc_wall(const orc_run_params *rp, double *x, double *v, int64_t pid,
   return 1;
 }
 
+/* Electron-neutral collisions (Sec. 5 names them as the next addition; the  */
+/* Drude model of Sec. 4 damps with the collision rate nu). Reading: a      */
+/* constant rate nu; in each step an electron collides with probability     */
+/* P = 1 - exp(-nu dt) and scatters elastically and isotropically: same      */
+/* speed, direction uniform on the sphere (the neutral's recoil neglected).  */
+/* The decision and the direction come from Philox with counter             */
+/* (step, step>>32, id, 0x434F4C4C) and key (seed): collide when the top 24 */
+/* bits of the first word are below floor(P 2^24); cos(theta) = 1 - 2 u1,   */
+/* phi = 2 pi u2 from the next two words. Returns 1 on a collision.         */
+/* ------------------------------------------------------------------ */
+uint32_t orc_coll_threshold(double nu, double dt) {
+  if (!(nu > 0.0)) return 0u;
+  double p = 1.0 - exp(-nu * dt);
+  return (uint32_t)floor(p * 16777216.0);
+}
+
+static int orc_collide(const orc_run_params *rp, uint32_t thr, double *v, int64_t pid, int64_t step) {
+  if (thr == 0u) return 0;
+  uint32_t ctr[4] = {(uint32_t)(uint64_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)pid,
+                     0x434F4C4Cu};
+  uint32_t key[2] = {(uint32_t)rp->seed, (uint32_t)(rp->seed >> 32)};
+  uint32_t o[4];
+  orc_philox4x32_10(ctr, key, o);
+  if ((o[0] >> 8) >= thr) return 0;
+  double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  double u1 = (double)(o[1] >> 8) * (1.0 / 16777216.0);
+  double u2 = (double)(o[2] >> 8) * (1.0 / 16777216.0);
+  double ct = 1.0 - 2.0 * u1;
+  double st = sqrt(1.0 - ct * ct);
+  double ph = 2.0 * ORC_PI * u2;
+  v[0] = speed * st * cos(ph);
+  v[1] = speed * st * sin(ph);
+  v[2] = speed * ct;
+  return 1;
+}
+
+/* The collision operator alone on n velocities (for pins): returns the */
+/* number of collisions of this step.                                   */
+int64_t orc_collisions(const orc_run_params *rp, int64_t n, double *v, const int64_t *id, int64_t step) {
+  const uint32_t thr = orc_coll_threshold(rp->nu_coll, rp->dt);
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; ++i) c += orc_collide(rp, thr, v + 3 * i, id[i], step);
+  return c;
+}
+
 /* Drive u_asy(t_n) (Sec. 4 and the Gaussian-pulse reading). */
 double orc_drive(const orc_run_params *rp, int64_t step) {
   double t = step * rp->dt;
@@ -651,6 +697,7 @@ int64_t orc_run(const orc_run_params *rp, int64_t n, double *x, double *v, const
                 double *uasy) {
   double *E = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
   int64_t hits = 0;
+  const uint32_t thr = orc_coll_threshold(rp->nu_coll, rp->dt);
   for (int64_t s = 0; s < nsteps; ++s) {
     int64_t step = step0 + s;
     double u = orc_drive(rp, step);
@@ -663,6 +710,7 @@ int64_t orc_run(const orc_run_params *rp, int64_t n, double *x, double *v, const
       for (int c = 0; c < 3; ++c) v[3 * i + c] += kick * (-1.0) * E[3 * i + c]; /* q/m = -1 */
       for (int c = 0; c < 3; ++c) x[3 * i + c] += rp->dt * v[3 * i + c];
       hits += orc_wall(rp, x + 3 * i, v + 3 * i, id[i], step);
+      orc_collide(rp, thr, v + 3 * i, id[i], step);
     }
   }
   free(E);
