@@ -213,7 +213,42 @@ def serving_measure(n_requests, steps, rate=20.0):
                         "l_max in {8,16}, mixed precision"}
 
 
-def drude_measure(temps=(2.0, 3.0, 5.0), N=500000, steps=3000, seeds=4, t_win=30.0):
+def _paired_response_fit(T, nu_coll, N, seeds, steps, t_win):
+    """Kick-minus-no-kick Q_diff on the paper's case, averaged over seeds, and
+    the fit a e^{-bt} sin(ct + phi) over 0 <= t <= t_win of the mean and of
+    the two halves of the seeds."""
+    from paper_2111_13072_gb300 import imrp
+    from paper_2111_13072_gb300.inputs import paper_variant, workload_state
+    dqs = []
+    for seed in range(seeds):
+        w = paper_variant(T, N=N, steps=steps, seed=seed)
+        x, v = workload_state(w)
+        series = {}
+        for kind in (w.drive_kind, 2):  # the kick, then no drive
+            with imrp.Sim(imrp.params_from_workload(w, drive_kind=kind, nu_coll=nu_coll)) as sim:
+                sim.load(x, v)
+                sim.step_async(steps)
+                sim.sync()
+                series[kind] = sim.qdiff()
+        dqs.append(series[w.drive_kind][0] - series[2][0])
+        u = series[w.drive_kind][1]
+
+    def fit(dq):
+        om, re, im = imrp.admittance(dq, u, w.dt, 0.5 * w.dt, 1000, 2.0)
+        w0 = float(om[int(np.argmax(re))])
+        try:
+            return imrp.fit_damped_sine(dq, w.dt, 0.0, t_win, w0, 0.05)
+        except imrp.IMRPError:
+            return np.full(4, np.nan)
+
+    a, b, c, ph = fit(np.mean(dqs, axis=0))
+    h = len(dqs) // 2
+    halves = [2.0 * float(fit(np.mean(dqs[:h], axis=0))[1]), 2.0 * float(fit(np.mean(dqs[h:], axis=0))[1])]
+    return {"fit_a_b_c_phi": [float(a), float(b), float(c), float(ph)], "nu_eff": 2.0 * float(b),
+            "nu_eff_halves": halves, "drude_eta": float(np.hypot(b, c))}, w
+
+
+def drude_measure(temps=(2.0, 3.0, 5.0), N=500000, steps=3000, seeds=4, t_win=30.0, nus=(0.1, 0.2)):
     """The paper's temperature diagnostic (Sec. 4) on its own case (R = 4 mm,
     1 mm dielectric, n = 1e15 m^-3, 1 < r < 10, l <= 1 / m = 0 kernel, one
     kick u_asy = 1, dt = 0.01) with the uniform Maxwellian shell in place of
@@ -226,45 +261,25 @@ def drude_measure(temps=(2.0, 3.0, 5.0), N=500000, steps=3000, seeds=4, t_win=30
     a e^{-bt} sin(ct + phi) over 0 <= t <= t_win; its transform is the Drude
     dipole term with nu_eff = 2 b and eta = sqrt(b^2 + c^2), and
     K = nu_eff R / lambda_D. The paper, with its sheath, reports nu_eff in
-    {0.105, 0.128, 0.167} and K = 1.264."""
+    {0.105, 0.128, 0.167} and K = 1.264. Then, at 3 eV, electron-neutral
+    collisions at the rates `nus`: the Drude model adds nu to the damping."""
     import torch
     from paper_2111_13072_gb300 import imrp
-    from paper_2111_13072_gb300.inputs import paper_variant, workload_state
-    out = []
+    out, coll = [], []
     t0 = time.perf_counter()
     for T in temps:
-        dqs = []
-        for seed in range(seeds):
-            w = paper_variant(T, N=N, steps=steps, seed=seed)
-            x, v = workload_state(w)
-            series = {}
-            for kind in (w.drive_kind, 2):  # the kick, then no drive
-                with imrp.Sim(imrp.params_from_workload(w, drive_kind=kind)) as sim:
-                    sim.load(x, v)
-                    sim.step_async(steps)
-                    sim.sync()
-                    series[kind] = sim.qdiff()
-            dqs.append(series[w.drive_kind][0] - series[2][0])
-            u = series[w.drive_kind][1]
-        def fit(dq):
-            om, re, im = imrp.admittance(dq, u, w.dt, 0.5 * w.dt, 1000, 2.0)
-            w0 = float(om[int(np.argmax(re))])
-            try:
-                return imrp.fit_damped_sine(dq, w.dt, 0.0, t_win, w0, 0.05)
-            except imrp.IMRPError:
-                return np.full(4, np.nan)
-
-        a, b, c, ph = fit(np.mean(dqs, axis=0))
-        h = len(dqs) // 2  # the two halves of the seeds, fitted apart: a spread
-        halves = [2.0 * float(fit(np.mean(dqs[:h], axis=0))[1]), 2.0 * float(fit(np.mean(dqs[h:], axis=0))[1])]
-        nu = 2.0 * b
-        out.append({"T_e_eV": T, "fit_a_b_c_phi": [float(a), float(b), float(c), float(ph)],
-                    "nu_eff": float(nu), "nu_eff_halves": halves, "drude_eta": float(np.hypot(b, c)),
-                    "K": imrp.drude_k(nu, T, w.R_D_m, w.n_e_m3) if nu > 0 else None})
+        r, w = _paired_response_fit(T, 0.0, N, seeds, steps, t_win)
+        nu = r["nu_eff"]
+        r.update({"T_e_eV": T, "K": imrp.drude_k(nu, T, w.R_D_m, w.n_e_m3) if nu > 0 else None})
+        out.append(r)
+    for nc in nus:
+        r, w = _paired_response_fit(3.0, nc, N, seeds, steps, t_win)
+        r.update({"T_e_eV": 3.0, "nu_coll": nc})
+        coll.append(r)
     torch.cuda.synchronize()
     Ks = [r["K"] for r in out if r["K"] is not None]
-    return {"runs": out, "K_mean": float(np.mean(Ks)) if Ks else None, "N": N, "steps": steps,
-            "seeds": seeds, "t_window": t_win, "seconds": time.perf_counter() - t0,
+    return {"runs": out, "K_mean": float(np.mean(Ks)) if Ks else None, "collisions": coll, "N": N,
+            "steps": steps, "seeds": seeds, "t_window": t_win, "seconds": time.perf_counter() - t0,
             "workload": "paper's case: R=4 mm, R_E=3 mm, eps_D=4, n=1e15 m^-3, 1<r<10, l_max=1 m=0 kernel, "
                         "kick u_asy=1, dt=0.01, uniform Maxwellian shell (no sheath), mixed precision; "
                         "kick minus no-kick runs from the same state, mean over seeds",

@@ -64,6 +64,11 @@ typedef struct imrp_params {
   int32_t precision;  /* 0 FP64 throughout; 1 mixed: FP32 state, harmonics and push, FP64 carries */
   uint64_t seed;     /* key of the counter-based wall random numbers              */
   double q_s;        /* surface charge Q_S in super-particle charges (Sec. 3), usually 0 */
+  double nu_coll;    /* electron-neutral collision rate nu [omega_pe] (Sec. 5 names collisions as
+                        the next addition; the Drude model of Sec. 4 damps with nu): in each step
+                        an electron scatters elastically and isotropically (same speed, direction
+                        uniform on the sphere) with probability 1 - exp(-nu dt), decided by Philox
+                        keyed by (step, id, seed). 0: collisionless, as in the paper's runs */
 } imrp_params;
 
 /* Derived dimensionless quantities of a context (read-only). */

@@ -42,6 +42,13 @@ template <> const KernelSet<double>* find_set<double>(int L) {
   return nullptr;
 }
 
+// Collision threshold: a step's collision probability 1 - exp(-nu dt) in
+// units of 2^-24 (compared with the top 24 bits of a Philox word).
+uint32_t coll_threshold(double nu, double dt) {
+  if (!(nu > 0.0)) return 0u;
+  return uint32_t(floor((1.0 - exp(-nu * dt)) * 16777216.0));
+}
+
 // Coefficients of the library (written from App. A and Sec. 3; R = 1).
 double coef_f(int l, double d, double eps) {
   const double x = pow(1.0 - d, 2 * l + 1);
@@ -267,6 +274,7 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   a.wall_rule = ctx->p.wall_rule;
   a.self_image = ctx->p.self_image;
   a.m0_only = ctx->p.m0_only;
+  a.coll_thr = coll_threshold(ctx->p.nu_coll, ctx->p.dt);
   a.seed = ctx->p.seed;
   double rl = 1.0;
   for (int l = 0; l < kTabL; ++l) {
@@ -415,6 +423,7 @@ void imrp_default_params(imrp_params* p) {
   p->precision = 0;
   p->seed = 0;
   p->q_s = 0.0;
+  p->nu_coll = 0.0;
 }
 
 int imrp_create(const imrp_params* p, imrp_ctx** out) {
@@ -437,6 +446,7 @@ int imrp_create(const imrp_params* p, imrp_ctx** out) {
   if (p->m0_only != 0 && p->m0_only != 1) return bad("m0_only");
   if (p->precision != 0 && p->precision != 1) return bad("precision");
   if (p->drive_kind < 0 || p->drive_kind > 2 || p->wall_rule < 0 || p->wall_rule > 1) return bad("rules");
+  if (!(p->nu_coll >= 0.0) || !std::isfinite(p->nu_coll)) return bad("nu_coll");
   if (p->drive_kind == 0 && !(p->width_wpe > 0)) return bad("width");
   ctx->L = p->l_max;
   ctx->prec = p->precision;

@@ -197,6 +197,7 @@ template <class T> struct FieldArgs {
   int wall_rule;
   int self_image;
   int m0_only;        // 1: keep only the m = 0 terms of every degree (the paper's truncation)
+  uint32_t coll_thr;  // collision when the top 24 bits of a Philox word are below this (0: none)
   uint64_t seed;
   T f[kTabL];         // f_l of App. A
   T rhol[kTabL];      // r_out^l

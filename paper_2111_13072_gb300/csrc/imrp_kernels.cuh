@@ -856,6 +856,27 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       }
       rr = double(X) * double(X) + double(Y) * double(Y) + double(Z) * double(Z);
     }
+    if (a.coll_thr != 0u) {
+      // electron-neutral collision: isotropic elastic scattering with
+      // probability 1 - exp(-nu dt) (Philox counter (step, step >> 32, id,
+      // 0x434F4C4C), key = seed; top 24 bits below the threshold)
+      const uint64_t stp = uint64_t(a.st->step);
+      const uint4 o = philox4x32_10(make_uint4(uint32_t(stp), uint32_t(stp >> 32), a.id[j], 0x434F4C4Cu),
+                                    make_uint2(uint32_t(a.seed), uint32_t(a.seed >> 32)));
+      if ((o.x >> 8) < a.coll_thr) {
+        const T speed = sqrt(VX * VX + VY * VY + VZ * VZ);
+        const T u1 = T(o.y >> 8) * T(1.0 / 16777216.0);
+        const T u2 = T(o.z >> 8) * T(1.0 / 16777216.0);
+        const T ct = T(1) - T(2) * u1;
+        const T st = sqrt(T(1) - ct * ct);
+        T sp, cp;
+        if constexpr (sizeof(T) == 4) sincospif(T(2) * u2, &sp, &cp);
+        else sincospi(T(2) * u2, &sp, &cp);
+        VX = speed * st * cp;
+        VY = speed * st * sp;
+        VZ = speed * ct;
+      }
+    }
     if (!(isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(VX) && isfinite(VY) && isfinite(VZ))) {
       atomicOr(a.err, kErrNaN);
       rr = 1.0;

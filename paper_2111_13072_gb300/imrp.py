@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
         ("dt", ctypes.c_double), ("drive_kind", ctypes.c_int32), ("wall_rule", ctypes.c_int32),
         ("V_volts", ctypes.c_double), ("width_wpe", ctypes.c_double), ("t0_wpe", ctypes.c_double),
         ("self_image", ctypes.c_int32), ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
-        ("q_s", ctypes.c_double),
+        ("q_s", ctypes.c_double), ("nu_coll", ctypes.c_double),
     ]
 
 

@@ -33,7 +33,7 @@ def _pair(imrp, w: Workload, n, **over):
     op = oracle.from_physical(w.R_E_m, w.R_D_m, w.eps_D, w.R_out_m, w.n_e_m3, w.T_e_eV, n,
                               p.l_max, p.dt, drive_kind=p.drive_kind, V_volts=p.V_volts,
                               width_wpe=p.width_wpe, wall_rule=p.wall_rule,
-                              self_image=p.self_image, seed=p.seed)
+                              self_image=p.self_image, seed=p.seed, nu_coll=p.nu_coll)
     return p, op
 
 
@@ -100,6 +100,36 @@ def test_steps_match_oracle(imrp, prec):
     assert _rel(dv_g[good], dv_o[good]) < TOL[prec] * 10
     assert _rel(xg[good], xo[good]) < TOL[prec]
     np.testing.assert_allclose(q, qo, rtol=10 * TOL[prec], atol=10 * TOL[prec] * np.max(np.abs(qo)))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_collision_steps_match_oracle(imrp, prec):
+    """Five steps with electron-neutral collisions (nu = 2: about 10 % of the
+    particles scatter per step) and diffuse walls: the same particles scatter
+    on both sides (the decision is an integer compare of the same Philox word),
+    and velocities and positions agree."""
+    n = 3000
+    w = Workload("coll", N=n, l_max=8, T_e_eV=20.0, n_e_m3=1e15, drive_kind=1, V_volts=50.0)
+    x, v = workload_state(w, N=n)
+    p, op = _pair(imrp, w, n, precision=prec, nu_coll=2.0)
+    assert op.nu_coll == 2.0
+    with imrp.Sim(p) as sim:
+        sim.load(x, v)
+        q, u = sim.step(5)
+        xg, vg = sim.particles()
+    xo, vo, qo, uo, hits = oracle.run(op, x, v, 5)
+    # velocity after the collisions of the last step: a scattered particle's
+    # direction is new, so a different decision would show as an O(1) change
+    dv_g, dv_o = vg - v, vo - v
+    per = np.linalg.norm(dv_g - dv_o, axis=1) / (np.linalg.norm(vo, axis=1) + 1e-30)
+    bad = np.sum(per > 1e-2)
+    assert bad <= (0 if prec == 0 else 2), f"{bad} particles differ"
+    good = per <= 1e-2
+    assert _rel(vg[good], vo[good]) < TOL[prec] * 10
+    assert _rel(xg[good], xo[good]) < TOL[prec]
+    # speeds change only through the field and the walls: scattering keeps them
+    scattered = np.sum(np.abs(np.einsum("ij,ij->i", vo, v) / (np.linalg.norm(vo, axis=1) * np.linalg.norm(v, axis=1))) < 0.9)
+    assert scattered > 0.2 * n
 
 
 def test_qdiff_and_drive_sequence(imrp):
