@@ -23,7 +23,7 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Byte layout of the scratch for n particles, degree L, element size es.
 struct Layout {
-  size_t st[2][6], id[2], key0, idx0, key1, idx1, hist, agg, pfx, gagg, gbase, tot, totd, gswork, gsticket, eout,
+  size_t part, st[6], id, key0, idx0, key1, idx1, hist, agg, pfx, gagg, gbase, tot, totd, gswork, gsticket, eout,
       step, err, total;
 };
 constexpr Layout layout(int64_t n, int L, size_t es) {
@@ -33,9 +33,9 @@ constexpr Layout layout(int64_t n, int L, size_t es) {
   const int64_t nc = 2 * int64_t(ncomp(L));
   const int64_t nblk = (n + kSortTile - 1) / kSortTile;
   size_t at = 0;
-  for (int b = 0; b < 2; ++b)
-    for (int k = 0; k < 6; ++k) { o.st[b][k] = at; at += align256(size_t(n) * es); }
-  for (int b = 0; b < 2; ++b) { o.id[b] = at; at += align256(size_t(n) * 4); }
+  o.part = at; at += align256(size_t(n) * 8 * es);  // Part<T> records: 8 elements each
+  for (int k = 0; k < 6; ++k) { o.st[k] = at; at += align256(size_t(n) * es); }
+  o.id = at; at += align256(size_t(n) * 4);
   o.key0 = at; at += align256(size_t(n) * 4);
   o.idx0 = at; at += align256(size_t(n) * 4);
   o.key1 = at; at += align256(size_t(n) * 4);
@@ -95,30 +95,34 @@ double cprime(int lp) {
   return (((lp + 1) % 2 == 0) ? 1.0 : -1.0) * pow(0.5, lp + 1) * (4.0 * lp - 1.0) * df / fact;
 }
 
-// AoS FP64 positions -> SoA T, ids 0..n-1, zero velocities; flags positions
+// FP64 [n][3] positions -> particle records, ids 0..n-1, zero velocities; flags positions
 // outside 1 < r < r_out or non-finite.
 template <class T>
-__global__ void k_na_load(const double* __restrict__ x, T* X, T* Y, T* Z, T* VX, T* VY, T* VZ,
-                          uint32_t* id, int64_t n, double r_out, int* err) {
+__global__ void k_na_load(const double* __restrict__ x, Part<T>* st, int64_t n, double r_out, int* err) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const double a = x[3 * j], b = x[3 * j + 1], c = x[3 * j + 2];
-  const T ta = T(a), tb = T(b), tc = T(c);
-  const double r2 = double(ta) * double(ta) + double(tb) * double(tb) + double(tc) * double(tc);
+  Part<T> p;
+  p.x = T(a); p.y = T(b); p.z = T(c);
+  p.vx = T(0); p.vy = T(0); p.vz = T(0);
+  p.id = uint32_t(j);
+  const double r2 = double(p.x) * double(p.x) + double(p.y) * double(p.y) + double(p.z) * double(p.z);
   if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(err, kErrNaN);
   else if (!(r2 > 1.0 && r2 < r_out * r_out)) atomicOr(err, kErrRange);
-  X[j] = ta; Y[j] = tb; Z[j] = tc;
-  VX[j] = T(0); VY[j] = T(0); VZ[j] = T(0);
-  id[j] = uint32_t(j);
+  st[j] = p;
 }
 
-__global__ void k_na_init(StepState* st, int64_t step, int* err) {
+// Per-call set-up of what must start at zero or at the given step: the step
+// state, the error flag and the group scan's tickets (the scratch keeps the
+// previous call's contents, and another n or degree lays it out differently).
+__global__ void k_na_init(StepState* st, int64_t step, int* err, unsigned* ticket, int nticket) {
   st->step = step;
   st->next = step;
   st->u = 0.0;
   st->kick = 0.0;
   st->sync = 0;
   *err = 0;
+  for (int k = 0; k < nticket; ++k) ticket[k] = 0u;
 }
 
 template <class T>
@@ -141,25 +145,20 @@ int run(const imrp_params* p, const double* x, int64_t n, int64_t step, double* 
   const int64_t ngroups = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   const int nc = 2 * ncomp(L);
   auto P = [&](size_t off) { return static_cast<void*>(base + off); };
-  T* st0[6];
+  Part<T>* st0 = static_cast<Part<T>*>(P(o.part));
   T* st1[6];
-  for (int k = 0; k < 6; ++k) {
-    st0[k] = static_cast<T*>(P(o.st[0][k]));
-    st1[k] = static_cast<T*>(P(o.st[1][k]));
-  }
-  uint32_t* id0 = static_cast<uint32_t*>(P(o.id[0]));
-  uint32_t* id1 = static_cast<uint32_t*>(P(o.id[1]));
+  for (int k = 0; k < 6; ++k) st1[k] = static_cast<T*>(P(o.st[k]));
+  uint32_t* id1 = static_cast<uint32_t*>(P(o.id));
   uint32_t* key0 = static_cast<uint32_t*>(P(o.key0));
   uint32_t* idx0 = static_cast<uint32_t*>(P(o.idx0));
   StepState* st = static_cast<StepState*>(P(o.step));
   int* err = static_cast<int*>(P(o.err));
-  k_na_init<<<1, 1, 0, s>>>(st, step, err);
-  k_na_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, st0[0], st0[1], st0[2], st0[3], st0[4], st0[5],
-                                                          id0, n, r_out, err);
-  launch_keys<T>(st0[0], st0[1], st0[2], key0, idx0, n, 4294967296.0 / (r_out * r_out - 1.0), s);
+  k_na_init<<<1, 1, 0, s>>>(st, step, err, static_cast<unsigned*>(P(o.gsticket)), gs_col_blocks(nc));
+  k_na_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, st0, n, r_out, err);
+  launch_keys<T>(st0, key0, idx0, n, 4294967296.0 / (r_out * r_out - 1.0), s);
   const uint32_t* perm = launch_radix_sort(key0, idx0, static_cast<uint32_t*>(P(o.key1)), static_cast<uint32_t*>(P(o.idx1)),
                     static_cast<uint32_t*>(P(o.hist)), n, sort_first_byte(sizeof(T) == 4 ? 1 : 0), s);
-  launch_reorder<T>(st0, st1, id0, id1, perm, n, s);
+  launch_reorder<T>(st0, st1, id1, perm, n, s);
   MomArgs<T> ma;
   ma.x = st1[0]; ma.y = st1[1]; ma.z = st1[2];
   ma.n = n;
