@@ -92,9 +92,10 @@ struct imrp_ctx {
   cudaGraphExec_t graph2 = nullptr;
   int graph_cur = -1;
   // device memory
-  void* st_buf[2][6] = {{nullptr}};
-  uint32_t* id_buf[2] = {nullptr, nullptr};
-  int cur = 0;
+  void* state = nullptr;      // Part<T>[N]: the particles in the order of the last push (or load)
+  void* srt[6] = {nullptr};   // x, y, z, vx, vy, vz in radius order (rebuilt every step)
+  uint32_t* srt_id = nullptr; // their ids
+  int cur = 0;                // stays 0: one state buffer (checked by the captured graphs)
   uint32_t *key0 = nullptr, *idx0 = nullptr, *key1 = nullptr, *idx1 = nullptr, *hist = nullptr;
   void *agg = nullptr, *pfx = nullptr, *gbase = nullptr, *tot = nullptr, *eout = nullptr;
   double *gagg = nullptr, *totd = nullptr, *gswork = nullptr;
@@ -133,15 +134,17 @@ struct imrp_ctx {
 
 namespace {
 
-template <class T> T** state_ptrs(imrp_ctx* c, int which) { return reinterpret_cast<T**>(c->st_buf[which]); }
+template <class T> T** sorted_ptrs(imrp_ctx* c) { return reinterpret_cast<T**>(c->srt); }
+template <class T> Part<T>* state_of(imrp_ctx* c) { return static_cast<Part<T>*>(c->state); }
 
 void free_all(imrp_ctx* c) {
   if (c->graph2) cudaGraphExecDestroy(c->graph2);
   c->graph2 = nullptr;
-  for (int b = 0; b < 2; ++b) {
-    for (int k = 0; k < 6; ++k) { cudaFree(c->st_buf[b][k]); c->st_buf[b][k] = nullptr; }
-    cudaFree(c->id_buf[b]); c->id_buf[b] = nullptr;
-  }
+  cudaFree(c->state);
+  c->state = nullptr;
+  for (int k = 0; k < 6; ++k) { cudaFree(c->srt[k]); c->srt[k] = nullptr; }
+  cudaFree(c->srt_id);
+  c->srt_id = nullptr;
   void* ps[] = {c->key0, c->idx0, c->key1, c->idx1, c->hist, c->agg, c->pfx, c->gbase, c->tot,
                 c->eout, c->gagg, c->totd, c->gswork, c->gsticket, c->qhist, c->uhist, c->stage, c->st,
                 c->derr, c->dft};
@@ -204,19 +207,16 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   const KernelSet<T>* ks = find_set<T>(ctx->L);
   cudaStream_t s = ctx->stream;
   const int64_t n = ctx->n;
-  T** src = state_ptrs<T>(ctx, ctx->cur);
-  T** dst = state_ptrs<T>(ctx, 1 - ctx->cur);
+  Part<T>* st = state_of<T>(ctx);
+  T** S = sorted_ptrs<T>(ctx);
   if (!ctx->keys_valid) {
-    launch_keys<T>(src[0], src[1], src[2], ctx->key0, ctx->idx0, n,
-                   4294967296.0 / (ctx->r_out * ctx->r_out - 1.0), s);
+    launch_keys<T>(st, ctx->key0, ctx->idx0, n, 4294967296.0 / (ctx->r_out * ctx->r_out - 1.0), s);
   }
   if (ev) cudaEventRecord(ev[0], s);
   const uint32_t* perm = launch_radix_sort(ctx->key0, ctx->idx0, ctx->key1, ctx->idx1, ctx->hist, n,
                                            sort_first_byte(ctx->prec), s);
   if (ev) cudaEventRecord(ev[1], s);
-  launch_reorder<T>(src, dst, ctx->id_buf[ctx->cur], ctx->id_buf[1 - ctx->cur], perm, n, s);
-  ctx->cur = 1 - ctx->cur;
-  T** S = dst;
+  launch_reorder<T>(st, S, ctx->srt_id, perm, n, s);
   MomArgs<T> ma;
   ma.x = S[0]; ma.y = S[1]; ma.z = S[2];
   ma.n = n;
@@ -248,7 +248,8 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   if (ev) cudaEventRecord(ev[4], s);
   FieldArgs<T> a;
   a.x = S[0]; a.y = S[1]; a.z = S[2]; a.vx = S[3]; a.vy = S[4]; a.vz = S[5];
-  a.id = ctx->id_buf[ctx->cur];
+  a.id = ctx->srt_id;
+  a.out = st;
   a.key = ctx->key0;
   a.kidx = ctx->idx0;
   a.n = n;
@@ -345,7 +346,8 @@ size_t footprint_bytes(int64_t N, int L, int prec) {
   const int64_t ngroups = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   const int64_t nc = 2 * int64_t(ncomp(L));
   size_t b = 0;
-  b += 2 * (6 * N * es + N * 4);                    // state ping-pong + ids
+  b += N * (es == 4 ? sizeof(Part<float>) : sizeof(Part<double>));  // state records
+  b += 6 * N * es + N * 4;                          // radius-ordered copy + ids
   b += 4 * size_t(N) * 4;                           // keys and slots
   b += size_t(256 * sort_blocks(N) + 256) * 4;      // histogram
   b += 2 * size_t(tile_stride(ntiles) * nc) * es;   // tile sums and in-group scans
@@ -362,10 +364,9 @@ int alloc_ctx(imrp_ctx* ctx) {
   const int64_t ntiles = (N + 31) / 32;
   const int64_t ngroups = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   const int nc = 2 * ncomp(ctx->L);
-  for (int b = 0; b < 2; ++b) {
-    for (int k = 0; k < 6; ++k) CK(cudaMalloc(&ctx->st_buf[b][k], N * es));
-    CK(cudaMalloc(&ctx->id_buf[b], N * sizeof(uint32_t)));
-  }
+  CK(cudaMalloc(&ctx->state, N * (ctx->prec == 1 ? sizeof(Part<float>) : sizeof(Part<double>))));
+  for (int k = 0; k < 6; ++k) CK(cudaMalloc(&ctx->srt[k], N * es));
+  CK(cudaMalloc(&ctx->srt_id, N * sizeof(uint32_t)));
   CK(cudaMalloc(&ctx->key0, N * sizeof(uint32_t)));
   CK(cudaMalloc(&ctx->idx0, N * sizeof(uint32_t)));
   CK(cudaMalloc(&ctx->key1, N * sizeof(uint32_t)));
@@ -528,11 +529,11 @@ int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t
   CK(cudaMemcpyAsync(ctx->stage + 3 * n, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   ctx->cur = 0;
   if (ctx->prec == 1)
-    launch_load<float>(ctx->stage, ctx->stage + 3 * n, state_ptrs<float>(ctx, 0), ctx->id_buf[0], n, ctx->r_out,
-                       ctx->derr, ctx->stream);
+    launch_load<float>(ctx->stage, ctx->stage + 3 * n, state_of<float>(ctx), n, ctx->r_out, ctx->derr,
+                       ctx->stream);
   else
-    launch_load<double>(ctx->stage, ctx->stage + 3 * n, state_ptrs<double>(ctx, 0), ctx->id_buf[0], n, ctx->r_out,
-                        ctx->derr, ctx->stream);
+    launch_load<double>(ctx->stage, ctx->stage + 3 * n, state_of<double>(ctx), n, ctx->r_out, ctx->derr,
+                        ctx->stream);
   StepState s0{};
   s0.step = 0;
   s0.next = 0;
@@ -601,10 +602,9 @@ int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, i
   CK(cudaEventRecord(ctx->ev_copied[s], ctx->copy_stream));
   CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[s], 0));
   if (ctx->prec == 1)
-    launch_load<float>(S, S + 3 * n, state_ptrs<float>(ctx, 0), ctx->id_buf[0], n, ctx->r_out, ctx->derr, ctx->stream);
+    launch_load<float>(S, S + 3 * n, state_of<float>(ctx), n, ctx->r_out, ctx->derr, ctx->stream);
   else
-    launch_load<double>(S, S + 3 * n, state_ptrs<double>(ctx, 0), ctx->id_buf[0], n, ctx->r_out, ctx->derr,
-                        ctx->stream);
+    launch_load<double>(S, S + 3 * n, state_of<double>(ctx), n, ctx->r_out, ctx->derr, ctx->stream);
   CK(cudaEventRecord(ctx->ev_free[s], ctx->stream));
   launch_init_step(ctx->st, ctx->stream);
   CK(cudaGetLastError());
@@ -652,11 +652,11 @@ int imrp_get_field(imrp_ctx* ctx, double* E) {
   if (ctx->prec == 1) {
     const float* e = static_cast<const float*>(ctx->eout);
     const float* cs[3] = {e, e + n, e + 2 * n};
-    launch_scatter_by_id<float>(cs, 3, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
+    launch_scatter_by_id<float>(cs, 3, ctx->srt_id, ctx->stage, n, ctx->stream);
   } else {
     const double* e = static_cast<const double*>(ctx->eout);
     const double* cs[3] = {e, e + n, e + 2 * n};
-    launch_scatter_by_id<double>(cs, 3, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
+    launch_scatter_by_id<double>(cs, 3, ctx->srt_id, ctx->stage, n, ctx->stream);
   }
   CK(cudaMemcpyAsync(E, ctx->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return check_err(ctx);
@@ -667,19 +667,8 @@ int imrp_get_particles(imrp_ctx* ctx, double* x, double* v) {
   if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "get_particles before load");
   const int64_t n = ctx->n;
   // positions to stage[0, 3n) and velocities to stage[3n, 6n), each [n][3] in id order
-  if (ctx->prec == 1) {
-    float** s = state_ptrs<float>(ctx, ctx->cur);
-    const float* cx[3] = {s[0], s[1], s[2]};
-    const float* cv[3] = {s[3], s[4], s[5]};
-    launch_scatter_by_id<float>(cx, 3, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
-    launch_scatter_by_id<float>(cv, 3, ctx->id_buf[ctx->cur], ctx->stage + 3 * n, n, ctx->stream);
-  } else {
-    double** s = state_ptrs<double>(ctx, ctx->cur);
-    const double* cx[3] = {s[0], s[1], s[2]};
-    const double* cv[3] = {s[3], s[4], s[5]};
-    launch_scatter_by_id<double>(cx, 3, ctx->id_buf[ctx->cur], ctx->stage, n, ctx->stream);
-    launch_scatter_by_id<double>(cv, 3, ctx->id_buf[ctx->cur], ctx->stage + 3 * n, n, ctx->stream);
-  }
+  if (ctx->prec == 1) launch_state_out<float>(state_of<float>(ctx), ctx->stage, ctx->stage + 3 * n, n, ctx->stream);
+  else launch_state_out<double>(state_of<double>(ctx), ctx->stage, ctx->stage + 3 * n, n, ctx->stream);
   if (x) CK(cudaMemcpyAsync(x, ctx->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   if (v) CK(cudaMemcpyAsync(v, ctx->stage + 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return check_err(ctx);
@@ -743,13 +732,8 @@ namespace {
 int ensure_keys(imrp_ctx* ctx) {
   if (ctx->keys_valid) return IMRP_OK;
   const double ks = 4294967296.0 / (ctx->r_out * ctx->r_out - 1.0);
-  if (ctx->prec == 1) {
-    float** s = state_ptrs<float>(ctx, ctx->cur);
-    launch_keys<float>(s[0], s[1], s[2], ctx->key0, ctx->idx0, ctx->n, ks, ctx->stream);
-  } else {
-    double** s = state_ptrs<double>(ctx, ctx->cur);
-    launch_keys<double>(s[0], s[1], s[2], ctx->key0, ctx->idx0, ctx->n, ks, ctx->stream);
-  }
+  if (ctx->prec == 1) launch_keys<float>(state_of<float>(ctx), ctx->key0, ctx->idx0, ctx->n, ks, ctx->stream);
+  else launch_keys<double>(state_of<double>(ctx), ctx->key0, ctx->idx0, ctx->n, ks, ctx->stream);
   CK(cudaGetLastError());
   ctx->keys_valid = true;
   return IMRP_OK;

@@ -201,34 +201,40 @@ const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint
 // ============================================================================
 // State movement
 // ============================================================================
-template <class T> struct Ptr7 { const T* s[6]; T* d[6]; };
+template <class T> struct SoA { T* d[6]; uint32_t* id; };
 
+// Gather of the state into radius order: sorted position j takes the record
+// perm[j] (one particle: whole sectors) and splits it into the component
+// arrays the moments and field kernels read.
 template <class T>
-__global__ void k_reorder(Ptr7<T> p, const uint32_t* __restrict__ id_src, uint32_t* __restrict__ id_dst,
-                          const uint32_t* __restrict__ perm, int64_t n) {
+__global__ void k_reorder(const Part<T>* __restrict__ src, SoA<T> dst, const uint32_t* __restrict__ perm,
+                          int64_t n) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const uint32_t q = perm[j];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) p.d[c][j] = p.s[c][q];
-  id_dst[j] = id_src[q];
+  const Part<T> p = src[perm[j]];
+  dst.d[0][j] = p.x; dst.d[1][j] = p.y; dst.d[2][j] = p.z;
+  dst.d[3][j] = p.vx; dst.d[4][j] = p.vy; dst.d[5][j] = p.vz;
+  dst.id[j] = p.id;
 }
 
 template <class T>
-void launch_reorder(const T* const* src, T* const* dst, const uint32_t* id_src, uint32_t* id_dst,
-                    const uint32_t* perm, int64_t n, cudaStream_t s) {
-  Ptr7<T> p;
-  for (int c = 0; c < 6; ++c) { p.s[c] = src[c]; p.d[c] = dst[c]; }
-  k_reorder<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(p, id_src, id_dst, perm, n);
+void launch_reorder(const Part<T>* src, T* const* dst, uint32_t* id_dst, const uint32_t* perm, int64_t n,
+                    cudaStream_t s) {
+  SoA<T> d;
+  for (int c = 0; c < 6; ++c) d.d[c] = dst[c];
+  d.id = id_dst;
+  k_reorder<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, d, perm, n);
 }
 
+// Radius keys of the state in its storage order (after a load or a field
+// evaluation; a step's field kernel writes the next keys itself).
 template <class T>
-__global__ void k_keys(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z,
-                       uint32_t* __restrict__ key, uint32_t* __restrict__ kidx, int64_t n,
-                       double kscale) {
+__global__ void k_keys(const Part<T>* __restrict__ st, uint32_t* __restrict__ key, uint32_t* __restrict__ kidx,
+                       int64_t n, double kscale) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const double xd = x[j], yd = y[j], zd = z[j];
+  const Part<T> p = st[j];
+  const double xd = p.x, yd = p.y, zd = p.z;
   double kf = (xd * xd + yd * yd + zd * zd - 1.0) * kscale;
   kf = kf < 0.0 ? 0.0 : (kf > 4294967295.0 ? 4294967295.0 : kf);
   key[j] = uint32_t(kf);
@@ -236,18 +242,14 @@ __global__ void k_keys(const T* __restrict__ x, const T* __restrict__ y, const T
 }
 
 template <class T>
-void launch_keys(const T* x, const T* y, const T* z, uint32_t* key, uint32_t* kidx, int64_t n,
-                 double kscale, cudaStream_t s) {
-  k_keys<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, y, z, key, kidx, n, kscale);
+void launch_keys(const Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, double kscale, cudaStream_t s) {
+  k_keys<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(st, key, kidx, n, kscale);
 }
 
-template <class T> struct Ptr6 { T* d[6]; };
-
-// FP64 positions x[n][3] and velocities v[n][3] -> SoA T, ids = 0..n-1; flags
-// positions outside 1 < r < r_out or non-finite values.
+// Host FP64 [n][3] positions and velocities into the state, ids 0..n-1.
 template <class T>
-__global__ void k_load(const double* __restrict__ xs, const double* __restrict__ vs, Ptr6<T> p,
-                       uint32_t* __restrict__ id, int64_t n, double r_out, int* err) {
+__global__ void k_load(const double* __restrict__ xs, const double* __restrict__ vs, Part<T>* __restrict__ st,
+                       int64_t n, double r_out, int* err) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double v[6];
@@ -259,27 +261,26 @@ __global__ void k_load(const double* __restrict__ xs, const double* __restrict__
   }
 #pragma unroll
   for (int c = 0; c < 6; ++c) fin = fin && isfinite(v[c]);
-  T t[6];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) t[c] = T(v[c]);
-  const double r2 = double(t[0]) * double(t[0]) + double(t[1]) * double(t[1]) + double(t[2]) * double(t[2]);
+  Part<T> p;
+  p.x = T(v[0]); p.y = T(v[1]); p.z = T(v[2]);
+  p.vx = T(v[3]); p.vy = T(v[4]); p.vz = T(v[5]);
+  p.id = uint32_t(j);
+  const double r2 = double(p.x) * double(p.x) + double(p.y) * double(p.y) + double(p.z) * double(p.z);
   if (!fin) atomicOr(err, kErrNaN);
   else if (!(r2 > 1.0 && r2 < r_out * r_out)) atomicOr(err, kErrRange);
-#pragma unroll
-  for (int c = 0; c < 6; ++c) p.d[c][j] = t[c];
-  id[j] = uint32_t(j);
+  st[j] = p;
 }
 
 template <class T>
-void launch_load(const double* xs, const double* vs, T* const* dst, uint32_t* id, int64_t n, double r_out,
-                 int* err, cudaStream_t s) {
-  Ptr6<T> p;
-  for (int c = 0; c < 6; ++c) p.d[c] = dst[c];
-  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(xs, vs, p, id, n, r_out, err);
+void launch_load(const double* x, const double* v, Part<T>* st, int64_t n, double r_out, int* err,
+                 cudaStream_t s) {
+  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, v, st, n, r_out, err);
 }
 
+// out[id[j]][c] = comp_c[j] for c < nc (field values in radius order to id order)
+template <class T> struct Ptr6 { const T* d[6]; };
 template <class T>
-__global__ void k_scatter_by_id(Ptr6<const T> p, int nc, const uint32_t* __restrict__ id,
+__global__ void k_scatter_by_id(Ptr6<T> p, int nc, const uint32_t* __restrict__ id,
                                 double* __restrict__ out, int64_t n) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
@@ -288,11 +289,28 @@ __global__ void k_scatter_by_id(Ptr6<const T> p, int nc, const uint32_t* __restr
 }
 
 template <class T>
-void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, double* out,
-                          int64_t n, cudaStream_t s) {
-  Ptr6<const T> p;
-  for (int c = 0; c < 6; ++c) p.d[c] = c < ncomp ? comps[c] : nullptr;
+void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, double* out, int64_t n,
+                          cudaStream_t s) {
+  Ptr6<T> p;
+  for (int c = 0; c < ncomp; ++c) p.d[c] = comps[c];
   k_scatter_by_id<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(p, ncomp, id, out, n);
+}
+
+// The state in id order: x[id][3] and v[id][3], FP64.
+template <class T>
+__global__ void k_state_out(const Part<T>* __restrict__ st, double* __restrict__ x, double* __restrict__ v,
+                            int64_t n) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const Part<T> p = st[j];
+  const int64_t k = p.id;
+  x[3 * k] = p.x; x[3 * k + 1] = p.y; x[3 * k + 2] = p.z;
+  v[3 * k] = p.vx; v[3 * k + 1] = p.vy; v[3 * k + 2] = p.vz;
+}
+
+template <class T>
+void launch_state_out(const Part<T>* st, double* x, double* v, int64_t n, cudaStream_t s) {
+  k_state_out<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(st, x, v, n);
 }
 
 // ============================================================================
@@ -575,14 +593,14 @@ void launch_dft(const double* q, const double* u, int64_t ns, double dt, double 
 
 // explicit instantiations
 #define IMRP_INST_CORE(T)                                                                          \
-  template void launch_reorder<T>(const T* const*, T* const*, const uint32_t*, uint32_t*,         \
-                                  const uint32_t*, int64_t, cudaStream_t);                         \
-  template void launch_keys<T>(const T*, const T*, const T*, uint32_t*, uint32_t*, int64_t, double, \
+  template void launch_reorder<T>(const Part<T>*, T* const*, uint32_t*, const uint32_t*, int64_t,  \
+                                  cudaStream_t);                                                   \
+  template void launch_keys<T>(const Part<T>*, uint32_t*, uint32_t*, int64_t, double, cudaStream_t); \
+  template void launch_load<T>(const double*, const double*, Part<T>*, int64_t, double, int*,      \
                                cudaStream_t);                                                      \
-  template void launch_load<T>(const double*, const double*, T* const*, uint32_t*, int64_t, double, \
-                               int*, cudaStream_t);                                                \
   template void launch_scatter_by_id<T>(const T* const*, int, const uint32_t*, double*, int64_t,   \
                                         cudaStream_t);                                             \
+  template void launch_state_out<T>(const Part<T>*, double*, double*, int64_t, cudaStream_t);     \
   template void launch_tile_scan<T>(const T*, T*, double*, int64_t, int, cudaStream_t);                \
   template void launch_group_scan<T>(const double*, double*, unsigned*, T*, T*, double*, int64_t, int, \
                                      int, cudaStream_t);

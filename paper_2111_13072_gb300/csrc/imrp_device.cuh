@@ -148,6 +148,18 @@ __host__ __device__ inline int64_t gs_nseg(int64_t ngroups, int gseg) {
 __host__ __device__ constexpr int64_t gs_work_doubles(int nc) { return int64_t(kGsMaxSeg) * (kGsWarps + 2) * nc; }
 __host__ __device__ constexpr int gs_col_blocks(int nc) { return (nc + 31) / 32; }
 
+// One particle of the persistent state: position, velocity and id in one
+// record (32 bytes in FP32, 64 in FP64). The state is kept in the order of
+// the last push and gathered into radius order by index each step; whole
+// records make that gather read whole sectors instead of one sector per
+// component.
+template <class T> struct alignas(16) Part {
+  T x, y, z, vx, vy, vz;
+  uint32_t id;
+  uint32_t pad[sizeof(T) == 4 ? 1 : 3];
+};
+static_assert(sizeof(Part<float>) == 32 && sizeof(Part<double>) == 64, "particle record sizes");
+
 template <class T> struct MomArgs {
   const T* x;
   const T* y;
@@ -171,8 +183,9 @@ __host__ __device__ constexpr int idxI(int L, int l, int m) { return offI(L, m) 
 __host__ __device__ constexpr int idxR(int L, int l, int m) { return offR(L, m) + l - m; }
 
 template <class T> struct FieldArgs {
-  T *x, *y, *z, *vx, *vy, *vz;
+  const T *x, *y, *z, *vx, *vy, *vz;  // the particles in radius order
   const uint32_t* id;
+  Part<T>* out;       // push mode: the pushed particle j is written to out[j]
   uint32_t* key;      // next radius key (push mode)
   uint32_t* kidx;     // identity payload for the next sort (push mode)
   int64_t n;

@@ -31,19 +31,23 @@ const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint
                                   int64_t n, int first_byte, cudaStream_t s);
 
 // ---- state movement and keys (imrp_core.cu) ---------------------------------
+// The state is an array of Part<T> records in the order of the last push (or
+// load); each step gathers it into radius order as component arrays.
 template <class T>
-void launch_reorder(const T* const* src, T* const* dst, const uint32_t* id_src, uint32_t* id_dst,
-                    const uint32_t* perm, int64_t n, cudaStream_t s);
+void launch_reorder(const Part<T>* src, T* const* dst, uint32_t* id_dst, const uint32_t* perm, int64_t n,
+                    cudaStream_t s);
 template <class T>
-void launch_keys(const T* x, const T* y, const T* z, uint32_t* key, uint32_t* kidx, int64_t n,
-                 double kscale, cudaStream_t s);
+void launch_keys(const Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, double kscale, cudaStream_t s);
 template <class T>
-void launch_load(const double* x /* [n][3] */, const double* v /* [n][3] */, T* const* dst,
-                 uint32_t* id, int64_t n, double r_out, int* err, cudaStream_t s);
-// out[id[j]][c] = comp_c[j] for c < 3 (and c < 6 with the velocity arrays)
+void launch_load(const double* x /* [n][3] */, const double* v /* [n][3] */, Part<T>* st, int64_t n,
+                 double r_out, int* err, cudaStream_t s);
+// out[id[j]][c] = comp_c[j] for c < ncomp
 template <class T>
 void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, double* out,
                           int64_t n, cudaStream_t s);
+// the state in id order: x[n][3], v[n][3] (FP64)
+template <class T>
+void launch_state_out(const Part<T>* st, double* x, double* v, int64_t n, cudaStream_t s);
 
 // ---- scans (imrp_core.cu) ---------------------------------------------------
 // in-group scans of agg[u][tile] into pfx (row stride tile_stride(ntiles)),

@@ -886,8 +886,11 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     a.key[j] = uint32_t(kf);
     a.kidx[j] = uint32_t(j);
   }
-  a.x[j] = X; a.y[j] = Y; a.z[j] = Z;
-  a.vx[j] = VX; a.vy[j] = VY; a.vz[j] = VZ;
+  Part<T> rec;
+  rec.x = X; rec.y = Y; rec.z = Z;
+  rec.vx = VX; rec.vy = VY; rec.vz = VZ;
+  rec.id = a.id[j];
+  a.out[j] = rec;
 }
 
 }  // namespace imrp
