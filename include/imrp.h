@@ -292,7 +292,7 @@ const char* imrp_batch_last_error(const imrp_batch* b);
  * Green's function, the ions, Q_S and the drive at step `step`), for a
  * particle set given in device memory, with no context and no allocation: its
  * intermediate buffers live in one static device array of fixed size (about
- * 7 MB), which every GPU that loads this library holds until the process
+ * 10 MB), which every GPU that loads this library holds until the process
  * exits.
  *
  *   p       physical parameters as for imrp_create (p->N is ignored, m0_only = 0);
