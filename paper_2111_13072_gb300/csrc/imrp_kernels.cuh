@@ -205,46 +205,6 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
   }
 }
 
-// Column of a position in a column-major triangle: the largest m in [m_lo,
-// m_hi] with off(m) <= k, for an increasing offset function off. Starts from a
-// closed-form guess and corrects by at most a few steps.
-template <class Off>
-__device__ __forceinline__ int find_col(int k, int m_lo, int m_hi, float guess, Off off) {
-  int m = int(guess);
-  m = m < m_lo ? m_lo : (m > m_hi ? m_hi : m);
-  while (m < m_hi && off(m + 1) <= k) ++m;
-  while (m > m_lo && off(m) > k) --m;
-  return m;
-}
-
-// Decodes packed component e (0 <= e < ncomp(L)) into (l, m, part).
-__device__ __forceinline__ void decode_comp(int L, int e, int& l, int& m, int& part) {
-  if (e < L) { l = e + 1; m = 0; part = 0; return; }
-  // col_off(m) = L + 2 (m-1)(L+1) - (m-1) m for m >= 1: solve for m
-  const float j = float(e - L);
-  const float bq = float(2 * L + 3);
-  const float g = 1.0f + 0.5f * (bq - sqrtf(fmaxf(bq * bq - 4.0f * j, 0.0f)));
-  m = find_col(e, 1, L, g, [L](int mm) { return col_off(L, mm); });
-  const int r = e - col_off(L, m);
-  l = m + (r >> 1);
-  part = r & 1;
-}
-
-// Fetch of a complex coefficient c_l^m (any sign of m) from the packed real
-// set (stride 2, offset s) with X^{-m} = (-1)^m conj(X^m); zero outside
-// 1 <= l <= L, |m| <= l.
-template <class T>
-__device__ __forceinline__ void fetch_c(const T* sc, int s, int L, int l, int m, T& re, T& im) {
-  const int am = m < 0 ? -m : m;
-  if (l < 1 || l > L || am > l) { re = T(0); im = T(0); return; }
-  re = sc[2 * comp_idx(L, l, am, 0) + s];
-  im = am > 0 ? sc[2 * comp_idx(L, l, am, 1) + s] : T(0);
-  if (m < 0) {
-    im = -im;
-    if (am & 1) { re = -re; im = -im; }
-  }
-}
-
 // Constants of the scaled Legendre recurrences of the near field. With
 // c_l = (2l-1)!!/l! (the leading coefficient of P_l), q_l = s^l P_l(u) / c_l
 // follows q_{l+1} = (s u) q_l - g_l s^2 q_{l-1}, g_l = l^2 / (4 l^2 - 1)
