@@ -380,9 +380,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2111_13072_gb300 import build, imrp
+    from paper_2111_13072_gb300.replicas import max_over_ranks, rank_seed, throughput
     build.build()
     x, v = workload_state(w)
-    p = imrp.params_from_workload(w, seed=w.seed + rank)
+    p = imrp.params_from_workload(w, seed=rank_seed(w.seed, rank))
     sim = imrp.Sim(p)
     stream = torch.cuda.Stream()
     sim.set_stream(stream.cuda_stream)
@@ -404,13 +405,9 @@ def main():
         e1.record(stream)
         sim.sync()
         barrier()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks([e0.elapsed_time(e1)], dist, "cuda")[0]
     N = w.N
-    value = N * args.steps * world / (ms / 1e3)
+    value = throughput(N, args.steps, world, ms / 1e3)
     clocks = clk.summary()
 
     # per-stage device time (real steps launched one by one, CUDA events)
@@ -475,17 +472,14 @@ def main():
         sim.step_ptr(1, qb.data_ptr())
     barrier()
     tb = time.perf_counter() - tb0
-    if dist is not None:
-        t = torch.tensor([te, tb], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te, tb = float(t[0].item()), float(t[1].item())
-    e2e = {"value": N * ne * world / te, "unit": UNIT, "h2d_bytes_per_step": 48 * N,
+    te, tb = max_over_ranks([te, tb], dist, "cuda")
+    e2e = {"value": throughput(N, ne, world, te), "unit": UNIT, "h2d_bytes_per_step": 48 * N,
            "d2h_bytes_per_step": 8, "steps": ne, "mode": "streamed (H2D of step k+1 overlaps step k)",
-           "blocking_value": N * ne * world / tb}
+           "blocking_value": throughput(N, ne, world, tb)}
 
     fp64 = None
     if not args.no_fp64:
-        p64 = imrp.params_from_workload(w, precision=0, seed=w.seed + rank)
+        p64 = imrp.params_from_workload(w, precision=0, seed=rank_seed(w.seed, rank))
         with imrp.Sim(p64) as s64:
             s64.set_stream(stream.cuda_stream)
             s64.load(x, v)
