@@ -65,6 +65,12 @@ typedef struct {
   int32_t m0_only; /* 1: keep only the m = 0 terms of every degree        */
   int32_t self_image; /* 1: a particle also feels its own image         */
   int32_t pad;
+  /* Immobile ions of a given radial profile (App. D) in place of the uniform
+   * background: ion_q[k] is the ion charge inside r_k = 1 + k (r_out - 1) /
+   * (ion_n - 1), in super-particle charges; between the nodes it is linear in
+   * r, outside [1, r_out] constant. NULL: the uniform background n_ion. */
+  const double *ion_q;
+  int64_t ion_n;
 } orc_field_params;
 
 typedef struct {
@@ -247,23 +253,49 @@ double orc_qdiff(const orc_field_params *p, int64_t n, const double *x) {
   return s / p->n_tilde; /* -(1/n~) * (-1) * sum Psi */
 }
 
-/* Electric field of the immobile uniform ion background (density
- * n_ion / V_shell on 1 <= r <= r_out) through the l = 0 part 1/(4 pi r_>) of
+/* Ion charge inside radius r in super-particle charges: the uniform
+ * background (density n_ion / V_shell on 1 <= r <= r_out), or the linear
+ * interpolation of the given profile ion_q. */
+static double orc_ion_charge(const orc_field_params *p, double r) {
+  double rc = r < 1.0 ? 1.0 : (r > p->r_out ? p->r_out : r);
+  if (!p->ion_q) return p->n_ion * (rc * rc * rc - 1.0) / (p->r_out * p->r_out * p->r_out - 1.0);
+  double h = (p->r_out - 1.0) / (double)(p->ion_n - 1);
+  int64_t k = (int64_t)floor((rc - 1.0) / h);
+  if (k > p->ion_n - 2) k = p->ion_n - 2;
+  if (k < 0) k = 0;
+  double r0 = 1.0 + k * h;
+  return p->ion_q[k] + (rc - r0) / h * (p->ion_q[k + 1] - p->ion_q[k]);
+}
+
+/* Electric field of the immobile ions through the l = 0 part 1/(4 pi r_>) of
  * G~, i.e. Gauss's law: E = (1/n~) Q_enc(r) / (4 pi r^2) r^. */
 static void orc_ion_field(const orc_field_params *p, const double *x, double *E) {
   double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-  double rc = r < 1.0 ? 1.0 : (r > p->r_out ? p->r_out : r);
-  double qenc = p->n_ion * (rc * rc * rc - 1.0) / (p->r_out * p->r_out * p->r_out - 1.0);
-  double s = qenc / (4.0 * ORC_PI * p->n_tilde * r * r * r);
+  double s = orc_ion_charge(p, r) / (4.0 * ORC_PI * p->n_tilde * r * r * r);
   for (int k = 0; k < 3; ++k) E[k] += s * x[k];
 }
 
-/* Potential of the same background (for the energy diagnostic):
- * (n_ion/V_shell/n~) [ (r^3-1)/(3r) + (r_out^2 - r^2)/2 ]. */
+/* Potential of the same ions (for the energy diagnostic), zero outside r_out:
+ * (1/(4 pi n~)) [Q(r)/r + int_r^r_out Q'(s)/s ds]. Uniform background:
+ * (n_ion/V_shell/n~) [ (r^3-1)/(3r) + (r_out^2 - r^2)/2 ]. Profile: Q' is
+ * constant on each interval of the table, so the integral is a sum of
+ * Q' ln(s_b/s_a). */
 static double orc_ion_potential(const orc_field_params *p, double r) {
-  double vsh = 4.0 * ORC_PI / 3.0 * (p->r_out * p->r_out * p->r_out - 1.0);
-  double rho = p->n_ion / vsh;
-  return rho / p->n_tilde * ((r * r * r - 1.0) / (3.0 * r) + 0.5 * (p->r_out * p->r_out - r * r));
+  if (!p->ion_q) {
+    double vsh = 4.0 * ORC_PI / 3.0 * (p->r_out * p->r_out * p->r_out - 1.0);
+    double rho = p->n_ion / vsh;
+    return rho / p->n_tilde * ((r * r * r - 1.0) / (3.0 * r) + 0.5 * (p->r_out * p->r_out - r * r));
+  }
+  double rc = r < 1.0 ? 1.0 : (r > p->r_out ? p->r_out : r);
+  double h = (p->r_out - 1.0) / (double)(p->ion_n - 1);
+  double s = 0.0;
+  for (int64_t k = 0; k + 1 < p->ion_n; ++k) {
+    double a = 1.0 + k * h, b = 1.0 + (k + 1) * h;
+    if (b <= rc) continue;
+    if (a < rc) a = rc;
+    s += (p->ion_q[k + 1] - p->ion_q[k]) / h * log(b / a);
+  }
+  return (orc_ion_charge(p, r) / r + s) / (4.0 * ORC_PI * p->n_tilde);
 }
 
 /* Field of the surface charge, -grad(Q_S/(4 pi n~ r)), and of the drive,
