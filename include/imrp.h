@@ -236,6 +236,45 @@ int imrp_drude_fit(const double* omega, const double* reY, const double* imY, in
 int imrp_drude_k(double nu_eff_wpe, double T_e_eV, double R_m, double n_e_m3, double* K);
 int imrp_drude_te(double nu_eff_wpe, double K, double R_m, double n_e_m3, double* T_e_eV);
 
+/* Floating probe-plasma equilibrium (App. D), the initial condition of the
+ * simulation. Units of Sec. 4: r in R, densities in n_inf, psi = e Phi / T_e,
+ * charges in e n_inf R^3. It solves
+ *   lambda^2 (1/r^2) (r^2 psi')' = exp(psi) - Rhat^2 / (r^2 sqrt(-2 psi))
+ * (Boltzmann electrons; cold ions falling in from infinity with the constant
+ * flux 4 pi Rhat^2 n_inf sqrt(T_e/m_i)) with the floating condition
+ * Rhat^2 = sqrt(m_i/(2 pi m_e)) exp(psi(1)) (Hertz-Langmuir electron flux equal
+ * to the ion flux), by shooting from the quasi-neutral branch
+ * (exp(psi) = n_i, -1/2 < psi < 0) at r_out inwards to the probe.
+ *   lambda      lambda_D / R (> 0)
+ *   mass_ratio  m_i / m_e (> 2 pi)
+ *   r_out       outer radius of the domain in R (> 1)
+ *   n_grid      nodes of the output grid r_k = 1 + k (r_out - 1)/(n_grid - 1) (>= 2)
+ *   psi, dpsi   psi and psi' at the nodes (host arrays of n_grid, or NULL)
+ *   q_ion, q_elec  ion and electron charge between 1 and r_k (n_grid, or NULL)
+ *   out[5]      Rhat, psi(1), psi'(1), the probe's surface charge
+ *               Q_S = -4 pi lambda^2 psi'(1) (Gauss's law), and the residual
+ *               of the floating condition.
+ * Host computation (no GPU, no context). Errors: IMRP_E_INVAL (argument out
+ * of range, or no equilibrium whose Bohm radius lies inside r_out). */
+int imrp_sheath_solve(double lambda, double mass_ratio, double r_out, int64_t n_grid, double* psi,
+                      double* dpsi, double* q_ion, double* q_elec, double* out);
+
+/* Replaces the context's uniform immobile ion background by a radial ion
+ * profile, e.g. the equilibrium of imrp_sheath_solve (App. D: the simulation
+ * starts from that equilibrium). q_ion[k] (host array of n_tab >= 2, copied)
+ * is the ion charge between 1 and r_k = 1 + k (r_out - 1)/(n_tab - 1) in units
+ * of e n_inf R^3; between nodes it is taken linear in r, outside [1, r_out]
+ * constant. q_elec_total (> 0, same unit) is the electron charge that the
+ * loaded super-particles represent, so n~ = N / q_elec_total at every load;
+ * q_s (same unit) replaces the surface charge Q_S. The ions stay immobile: on
+ * the electron time scale of the runs they move little (m_i/m_e ~ 7e4). Takes
+ * effect for the following steps (before or after a load). n_tab = 0 restores
+ * the uniform background and the parameters' Q_S. Errors: IMRP_E_INVAL
+ * (n_tab == 1, a non-finite or decreasing table, q_elec_total <= 0),
+ * IMRP_E_NOMEM, IMRP_E_CUDA. */
+int imrp_set_ion_profile(imrp_ctx* ctx, const double* q_ion, int64_t n_tab, double q_elec_total,
+                         double q_s);
+
 /* Derived quantities of the context. */
 int imrp_get_info(const imrp_ctx* ctx, imrp_info* info);
 

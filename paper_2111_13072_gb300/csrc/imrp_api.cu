@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -112,6 +113,12 @@ struct imrp_ctx {
   int* derr = nullptr;
   double* dft = nullptr;
   int64_t dft_cap = 0;
+  // radial ion profile (App. D) in place of the uniform background
+  double* ion_q = nullptr;    // device copy, units e n_inf R^3
+  int64_t ion_n = 0;
+  int64_t ion_cap = 0;
+  double ion_qe = 0.0;        // electron charge the loaded particles represent
+  double ion_qs = 0.0;        // surface charge, units e n_inf R^3
 
   int fail(int code, const char* fmt, ...) {
     char b[512];
@@ -137,6 +144,13 @@ namespace {
 template <class T> T** sorted_ptrs(imrp_ctx* c) { return reinterpret_cast<T**>(c->srt); }
 template <class T> Part<T>* state_of(imrp_ctx* c) { return static_cast<Part<T>*>(c->state); }
 
+// Super-particles per unit cube at density n_inf: N over the shell volume
+// for the uniform start, N over the electron charge of the given profile.
+double n_tilde_of(const imrp_ctx* c, int64_t n) {
+  if (c->ion_n) return double(n) / c->ion_qe;
+  return double(n) / (4.0 * kPi / 3.0 * (c->r_out * c->r_out * c->r_out - 1.0));
+}
+
 void free_all(imrp_ctx* c) {
   if (c->graph2) cudaGraphExecDestroy(c->graph2);
   c->graph2 = nullptr;
@@ -149,6 +163,9 @@ void free_all(imrp_ctx* c) {
                 c->eout, c->gagg, c->totd, c->gswork, c->gsticket, c->qhist, c->uhist, c->stage, c->st,
                 c->derr, c->dft};
   for (void* p : ps) cudaFree(p);
+  cudaFree(c->ion_q);
+  c->ion_q = nullptr;
+  c->ion_n = c->ion_cap = 0;
   c->key0 = c->idx0 = c->key1 = c->idx1 = c->hist = nullptr;
   c->agg = c->pfx = c->gbase = c->tot = c->eout = nullptr;
   c->gagg = c->totd = c->gswork = c->qhist = c->uhist = c->stage = c->dft = nullptr;
@@ -267,7 +284,11 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   a.rho_inv = T(1.0 / ctx->r_out);
   a.pf = 1.0 / (4.0 * kPi * ctx->n_tilde);
   a.ion_coef = ctx->n_ion / (ctx->r_out * ctx->r_out * ctx->r_out - 1.0);
-  a.q_s = ctx->p.q_s;
+  a.ion_q = ctx->ion_n ? ctx->ion_q : nullptr;
+  a.ion_n = int(ctx->ion_n);
+  a.ion_inv_h = ctx->ion_n ? double(ctx->ion_n - 1) / (ctx->r_out - 1.0) : 0.0;
+  a.ion_scale = ctx->n_tilde;
+  a.q_s = ctx->ion_n ? ctx->ion_qs * ctx->n_tilde : ctx->p.q_s;
   a.r_out2 = ctx->r_out * ctx->r_out;
   a.kscale = 4294967296.0 / (ctx->r_out * ctx->r_out - 1.0);
   a.dt = T(ctx->p.dt);
@@ -521,6 +542,45 @@ int imrp_set_stream(imrp_ctx* ctx, void* stream) {
   return IMRP_OK;
 }
 
+int imrp_set_ion_profile(imrp_ctx* ctx, const double* q_ion, int64_t n_tab, double q_elec_total,
+                         double q_s) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (n_tab == 0) {
+    ctx->ion_n = 0;
+  } else {
+    if (n_tab < 2 || n_tab > (int64_t(1) << 30) || !q_ion)
+      return ctx->fail(IMRP_E_INVAL, "set_ion_profile: table of %lld nodes", (long long)n_tab);
+    if (!(q_elec_total > 0.0) || !std::isfinite(q_elec_total) || !std::isfinite(q_s))
+      return ctx->fail(IMRP_E_INVAL, "set_ion_profile: electron charge %g, surface charge %g",
+                       q_elec_total, q_s);
+    for (int64_t k = 0; k < n_tab; ++k)
+      if (!std::isfinite(q_ion[k]) || (k > 0 && q_ion[k] < q_ion[k - 1]))
+        return ctx->fail(IMRP_E_INVAL, "set_ion_profile: node %lld not finite or decreasing",
+                         (long long)k);
+    // the previous table may still be read by queued steps
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (n_tab > ctx->ion_cap) {
+      cudaFree(ctx->ion_q);
+      ctx->ion_q = nullptr;
+      ctx->ion_cap = 0;
+      if (cudaMalloc(&ctx->ion_q, n_tab * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ion_n = 0;
+        return ctx->fail(IMRP_E_NOMEM, "set_ion_profile: %lld nodes", (long long)n_tab);
+      }
+      ctx->ion_cap = n_tab;
+    }
+    CK(cudaMemcpy(ctx->ion_q, q_ion, n_tab * sizeof(double), cudaMemcpyHostToDevice));
+    ctx->ion_n = n_tab;
+    ctx->ion_qe = q_elec_total;
+    ctx->ion_qs = q_s;
+  }
+  if (ctx->loaded) ctx->n_tilde = n_tilde_of(ctx, ctx->n);
+  // the captured step pair holds the old field arguments
+  if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+  return IMRP_OK;
+}
+
 int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t n) {
   if (!ctx) return IMRP_E_INVAL;
   if (!x || !v || n < 1 || n > ctx->cap) return ctx->fail(IMRP_E_INVAL, "load: n = %lld out of range [1, %lld]", (long long)n, (long long)ctx->cap);
@@ -544,7 +604,7 @@ int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t
   int rc = check_err(ctx);
   if (rc) { ctx->loaded = false; return rc; }
   ctx->n = n;
-  ctx->n_tilde = double(n) / (4.0 * kPi / 3.0 * (ctx->r_out * ctx->r_out * ctx->r_out - 1.0));
+  ctx->n_tilde = n_tilde_of(ctx, n);
   ctx->n_ion = double(n);
   ctx->ntiles = (n + 31) / 32;
   ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
@@ -611,7 +671,7 @@ int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, i
   const bool same_n = ctx->loaded && ctx->n == n;
   ctx->cur = 0;
   ctx->n = n;
-  ctx->n_tilde = double(n) / (4.0 * kPi / 3.0 * (ctx->r_out * ctx->r_out * ctx->r_out - 1.0));
+  ctx->n_tilde = n_tilde_of(ctx, n);
   ctx->n_ion = double(n);
   ctx->ntiles = (n + 31) / 32;
   ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;

@@ -201,7 +201,11 @@ template <class T> struct FieldArgs {
   int L;              // degree (equals the template L)
   T rho, rho_inv;     // r_out and 1 / r_out
   double pf;          // 1 / (4 pi n~)
-  double ion_coef;    // n_ion / (r_out^3 - 1)
+  double ion_coef;    // n_ion / (r_out^3 - 1) (uniform ions, used when ion_q is null)
+  const double* ion_q;  // radial ion profile (App. D): ion charge inside r_k = 1 + k h, units e n_inf R^3
+  double ion_inv_h;   // 1 / h
+  double ion_scale;   // n~: super-particle charges per e n_inf R^3
+  int ion_n;          // nodes of ion_q (>= 2 when ion_q is set)
   double q_s;         // surface charge
   double r_out2;      // r_out^2
   double kscale;      // 2^32 / (r_out^2 - 1)

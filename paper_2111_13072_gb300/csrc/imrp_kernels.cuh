@@ -727,7 +727,17 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     }
     // inner charge in units of e: ions inside minus electrons inside (+ Q_S); the
     // difference is small, so it is formed in FP64 and then scaled in T
-    const double qin = fma(a.ion_coef, r2d * rd - 1.0, a.q_s - double(j));
+    double qion;
+    if (a.ion_q) {
+      // radial profile, linear between the nodes, constant outside [1, r_out]
+      const double t = fmin(fmax((rd - 1.0) * a.ion_inv_h, 0.0), double(a.ion_n - 1));
+      const int k = min(int(t), a.ion_n - 2);
+      const double q0 = __ldg(a.ion_q + k), q1 = __ldg(a.ion_q + k + 1);
+      qion = a.ion_scale * fma(t - double(k), q1 - q0, q0);
+    } else {
+      qion = a.ion_coef * (r2d * rd - 1.0);
+    }
+    const double qin = qion + (a.q_s - double(j));
     const T er = T(qin) * (T(a.pf) * ir2 * ir);  // multiplies x (gives r^ / r^2)
     Ex += er * X; Ey += er * Y; Ez += er * Z;
     const int self_sign = img_in_tile ? (a.self_image ? 1 : 0) : (a.self_image ? 0 : -1);

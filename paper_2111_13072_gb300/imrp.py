@@ -23,7 +23,8 @@ EXPORTS = [
     "imrp_field_noalloc", "imrp_autotune", "imrp_batch_create", "imrp_batch_step", "imrp_batch_sync",
     "imrp_batch_destroy", "imrp_batch_last_error", "imrp_batch_set_stream", "imrp_footprint",
     "imrp_load_particles_async", "imrp_copy_qdiff_async", "imrp_drude_fit", "imrp_drude_k",
-    "imrp_drude_te", "imrp_admittance", "imrp_fit_damped_sine",
+    "imrp_drude_te", "imrp_admittance", "imrp_fit_damped_sine", "imrp_sheath_solve",
+    "imrp_set_ion_profile",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -106,6 +107,8 @@ def load_library(path: str = LIB_PATH):
     L.imrp_drude_fit.argtypes = [pd, pd, pd, ctypes.c_int64, ctypes.c_double, ctypes.c_double, pd]
     L.imrp_drude_k.argtypes = [ctypes.c_double] * 4 + [pd]
     L.imrp_drude_te.argtypes = [ctypes.c_double] * 4 + [pd]
+    L.imrp_sheath_solve.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int64] + [pd] * 5
+    L.imrp_set_ion_profile.argtypes = [c_void_p, pd, ctypes.c_int64, ctypes.c_double, ctypes.c_double]
     for name in EXPORTS:
         if name not in ("imrp_default_params", "imrp_last_error", "imrp_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -196,6 +199,21 @@ def drude_te(nu_eff_wpe: float, K: float, R_m: float, n_e_m3: float) -> float:
     if rc != 0:
         raise IMRPError(rc, "imrp_drude_te failed")
     return float(out[0])
+
+
+def sheath_solve(lam: float, mass_ratio: float, r_out: float, n_grid: int = 1025) -> dict:
+    """imrp_sheath_solve: the floating equilibrium of App. D on the grid
+    r_k = 1 + k (r_out - 1)/(n_grid - 1): rhat, psi_wall, dpsi_wall, q_s,
+    residual, and the arrays r, psi, dpsi, q_ion, q_elec."""
+    psi, dpsi, qi, qe = (np.zeros(n_grid) for _ in range(4))
+    out = np.zeros(5)
+    rc = load_library().imrp_sheath_solve(lam, mass_ratio, r_out, n_grid, _ptr(psi), _ptr(dpsi),
+                                          _ptr(qi), _ptr(qe), _ptr(out))
+    if rc != 0:
+        raise IMRPError(rc, "imrp_sheath_solve failed")
+    r = 1.0 + (r_out - 1.0) * np.arange(n_grid) / (n_grid - 1)
+    return dict(rhat=out[0], psi_wall=out[1], dpsi_wall=out[2], q_s=out[3], residual=out[4], r=r,
+                psi=psi, dpsi=dpsi, q_ion=qi, q_elec=qe)
 
 
 def footprint(params: Params, n_steps: int) -> int:
@@ -292,6 +310,15 @@ class Sim:
         v = np.ascontiguousarray(v, dtype=np.float64)
         assert x.shape == v.shape and x.ndim == 2 and x.shape[1] == 3
         self._check(self._lib.imrp_load_particles(self._h, _ptr(x), _ptr(v), x.shape[0]))
+
+    def set_ion_profile(self, q_ion, q_elec_total: float, q_s: float):
+        """imrp_set_ion_profile: immobile ions of a radial profile (units e n_inf R^3);
+        q_ion = None restores the uniform background."""
+        if q_ion is None:
+            self._check(self._lib.imrp_set_ion_profile(self._h, None, 0, 1.0, 0.0))
+            return
+        q = np.ascontiguousarray(q_ion, dtype=np.float64)
+        self._check(self._lib.imrp_set_ion_profile(self._h, _ptr(q), q.size, q_elec_total, q_s))
 
     def load_ptr(self, x_ptr: int, v_ptr: int, n: int):
         """Loads from host pointers (e.g. pinned torch tensors)."""

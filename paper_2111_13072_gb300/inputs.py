@@ -115,6 +115,31 @@ def maxwellian_shell(N: int, r_out: float, sigma_v: float, seed: int = 0,
     return np.ascontiguousarray(x), np.ascontiguousarray(v)
 
 
+def radial_profile_shell(N: int, r_grid, cum, sigma_v: float, seed: int = 0):
+    """Returns (x [N,3], v [N,3]) like maxwellian_shell, with radii drawn from a
+    given radial distribution instead of the uniform one: cum[k] is the
+    (unnormalised, non-decreasing) number of particles inside r_grid[k], taken
+    linear between nodes, so a radius is the inverse of that piecewise-linear
+    function at a uniform fraction of cum[-1]. The table is an input (e.g. the
+    electron charge of an equilibrium profile); nothing here computes it."""
+    r_grid = np.asarray(r_grid, dtype=np.float64)
+    cum = np.asarray(cum, dtype=np.float64)
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    u = rng.random(N)
+    lo = r_grid[0] * (1.0 + 1e-6)
+    hi = r_grid[-1] * (1.0 - 1e-6)
+    r = np.clip(np.interp(u * cum[-1], cum, r_grid), lo, hi)
+    d = rng.standard_normal((N, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    x = (d * r[:, None]).astype(np.float32).astype(np.float64)
+    rr = np.linalg.norm(x, axis=1)
+    bad = (rr < lo) | (rr > hi)
+    if np.any(bad):
+        x[bad] = (x[bad] / rr[bad, None] * np.clip(rr[bad], lo, hi)[:, None]).astype(np.float32)
+    v = (rng.standard_normal((N, 3)) * sigma_v).astype(np.float32).astype(np.float64)
+    return np.ascontiguousarray(x), np.ascontiguousarray(v)
+
+
 def workload_state(w: Workload, N: int | None = None):
     """Initial state of a workload (optionally with a different particle count)."""
     return maxwellian_shell(w.N if N is None else N, w.r_out, w.sigma_v, w.seed)
