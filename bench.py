@@ -213,19 +213,32 @@ def serving_measure(n_requests, steps, rate=20.0):
                         "l_max in {8,16}, mixed precision"}
 
 
-def _paired_response_fit(T, nu_coll, N, seeds, steps, t_win):
+ARGON_MASS_RATIO = 39.948 * 1822.888486  # m_i / m_e; the paper names no gas
+
+
+def _paired_response_fit(T, nu_coll, N, seeds, steps, t_win, sheath=False):
     """Kick-minus-no-kick Q_diff on the paper's case, averaged over seeds, and
     the fit a e^{-bt} sin(ct + phi) over 0 <= t <= t_win of the mean and of
-    the two halves of the seeds."""
+    the two halves of the seeds. sheath: start from the floating equilibrium
+    (App. D; immobile ions of its profile, its surface charge, electrons drawn
+    from its Boltzmann density) instead of the uniform shell."""
     from paper_2111_13072_gb300 import imrp
-    from paper_2111_13072_gb300.inputs import paper_variant, workload_state
+    from paper_2111_13072_gb300.inputs import paper_variant, radial_profile_shell, workload_state
     dqs = []
+    eq = None
     for seed in range(seeds):
         w = paper_variant(T, N=N, steps=steps, seed=seed)
-        x, v = workload_state(w)
+        if sheath:
+            if eq is None:
+                eq = imrp.sheath_solve(w.sigma_v, ARGON_MASS_RATIO, w.r_out, 4097)
+            x, v = radial_profile_shell(N, eq["r"], eq["q_elec"], w.sigma_v, seed=seed)
+        else:
+            x, v = workload_state(w)
         series = {}
         for kind in (w.drive_kind, 2):  # the kick, then no drive
             with imrp.Sim(imrp.params_from_workload(w, drive_kind=kind, nu_coll=nu_coll)) as sim:
+                if sheath:
+                    sim.set_ion_profile(eq["q_ion"], eq["q_elec"][-1], eq["q_s"])
                 sim.load(x, v)
                 sim.step_async(steps)
                 sim.sync()
@@ -244,11 +257,16 @@ def _paired_response_fit(T, nu_coll, N, seeds, steps, t_win):
     a, b, c, ph = fit(np.mean(dqs, axis=0))
     h = len(dqs) // 2
     halves = [2.0 * float(fit(np.mean(dqs[:h], axis=0))[1]), 2.0 * float(fit(np.mean(dqs[h:], axis=0))[1])]
-    return {"fit_a_b_c_phi": [float(a), float(b), float(c), float(ph)], "nu_eff": 2.0 * float(b),
-            "nu_eff_halves": halves, "drude_eta": float(np.hypot(b, c))}, w
+    r = {"fit_a_b_c_phi": [float(a), float(b), float(c), float(ph)], "nu_eff": 2.0 * float(b),
+         "nu_eff_halves": halves, "drude_eta": float(np.hypot(b, c))}
+    if eq is not None:
+        r["sheath"] = {"rhat": float(eq["rhat"]), "psi_wall": float(eq["psi_wall"]),
+                       "q_s": float(eq["q_s"])}
+    return r, w
 
 
-def drude_measure(temps=(2.0, 3.0, 5.0), N=500000, steps=3000, seeds=4, t_win=30.0, nus=(0.1, 0.2)):
+def drude_measure(temps=(2.0, 3.0, 5.0), N=500000, steps=3000, seeds=4, t_win=30.0, nus=(0.1, 0.2),
+                  sheath=False):
     """The paper's temperature diagnostic (Sec. 4) on its own case (R = 4 mm,
     1 mm dielectric, n = 1e15 m^-3, 1 < r < 10, l <= 1 / m = 0 kernel, one
     kick u_asy = 1, dt = 0.01) with the uniform Maxwellian shell in place of
@@ -262,18 +280,20 @@ def drude_measure(temps=(2.0, 3.0, 5.0), N=500000, steps=3000, seeds=4, t_win=30
     dipole term with nu_eff = 2 b and eta = sqrt(b^2 + c^2), and
     K = nu_eff R / lambda_D. The paper, with its sheath, reports nu_eff in
     {0.105, 0.128, 0.167} and K = 1.264. Then, at 3 eV, electron-neutral
-    collisions at the rates `nus`: the Drude model adds nu to the damping."""
+    collisions at the rates `nus`: the Drude model adds nu to the damping.
+    sheath: every run starts from the floating equilibrium of App. D instead
+    (argon ions, immobile)."""
     import torch
     from paper_2111_13072_gb300 import imrp
     out, coll = [], []
     t0 = time.perf_counter()
     for T in temps:
-        r, w = _paired_response_fit(T, 0.0, N, seeds, steps, t_win)
+        r, w = _paired_response_fit(T, 0.0, N, seeds, steps, t_win, sheath)
         nu = r["nu_eff"]
         r.update({"T_e_eV": T, "K": imrp.drude_k(nu, T, w.R_D_m, w.n_e_m3) if nu > 0 else None})
         out.append(r)
     for nc in nus:
-        r, w = _paired_response_fit(3.0, nc, N, seeds, steps, t_win)
+        r, w = _paired_response_fit(3.0, nc, N, seeds, steps, t_win, sheath)
         r.update({"T_e_eV": 3.0, "nu_coll": nc})
         coll.append(r)
     torch.cuda.synchronize()
@@ -281,8 +301,10 @@ def drude_measure(temps=(2.0, 3.0, 5.0), N=500000, steps=3000, seeds=4, t_win=30
     return {"runs": out, "K_mean": float(np.mean(Ks)) if Ks else None, "collisions": coll, "N": N,
             "steps": steps, "seeds": seeds, "t_window": t_win, "seconds": time.perf_counter() - t0,
             "workload": "paper's case: R=4 mm, R_E=3 mm, eps_D=4, n=1e15 m^-3, 1<r<10, l_max=1 m=0 kernel, "
-                        "kick u_asy=1, dt=0.01, uniform Maxwellian shell (no sheath), mixed precision; "
-                        "kick minus no-kick runs from the same state, mean over seeds",
+                        "kick u_asy=1, dt=0.01, "
+                        + ("floating sheath equilibrium (App. D, argon, immobile ions)" if sheath
+                           else "uniform Maxwellian shell (no sheath)")
+                        + ", mixed precision; kick minus no-kick runs from the same state, mean over seeds",
             "paper": {"nu_eff": [0.105, 0.128, 0.167], "K": 1.264}}
 
 
@@ -334,6 +356,8 @@ def main():
                     help="also run the T_e sweep of the temperature diagnostic on the paper's case")
     ap.add_argument("--drude-n", type=int, default=500000)
     ap.add_argument("--drude-seeds", type=int, default=4)
+    ap.add_argument("--drude-sheath", action="store_true",
+                    help="start the --drude runs from the floating sheath equilibrium (App. D)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -498,7 +522,8 @@ def main():
 
     serving = None if args.no_serving else serving_measure(12, 500)
     ensemble = None if args.no_ensemble else ensemble_measure(200, 4, autotune=False)
-    drude = drude_measure(N=args.drude_n, seeds=args.drude_seeds) if (args.drude and rank == 0) else None
+    drude = (drude_measure(N=args.drude_n, seeds=args.drude_seeds, sheath=args.drude_sheath)
+             if (args.drude and rank == 0) else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
