@@ -589,11 +589,11 @@ int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t
   CK(cudaMemcpyAsync(ctx->stage + 3 * n, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   ctx->cur = 0;
   if (ctx->prec == 1)
-    launch_load<float>(ctx->stage, ctx->stage + 3 * n, state_of<float>(ctx), n, ctx->r_out, ctx->derr,
-                       ctx->stream);
+    launch_load<float>(ctx->stage, ctx->stage + 3 * n, state_of<float>(ctx), ctx->key0, ctx->idx0, n,
+                       ctx->r_out, ctx->derr, ctx->stream);
   else
-    launch_load<double>(ctx->stage, ctx->stage + 3 * n, state_of<double>(ctx), n, ctx->r_out, ctx->derr,
-                        ctx->stream);
+    launch_load<double>(ctx->stage, ctx->stage + 3 * n, state_of<double>(ctx), ctx->key0, ctx->idx0, n,
+                        ctx->r_out, ctx->derr, ctx->stream);
   StepState s0{};
   s0.step = 0;
   s0.next = 0;
@@ -610,7 +610,7 @@ int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t
   ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   ctx->host_step = 0;
   ctx->loaded = true;
-  ctx->keys_valid = false;
+  ctx->keys_valid = true;  // the load kernel wrote the keys of its order
   if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
   return IMRP_OK;
 }
@@ -662,9 +662,11 @@ int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, i
   CK(cudaEventRecord(ctx->ev_copied[s], ctx->copy_stream));
   CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[s], 0));
   if (ctx->prec == 1)
-    launch_load<float>(S, S + 3 * n, state_of<float>(ctx), n, ctx->r_out, ctx->derr, ctx->stream);
+    launch_load<float>(S, S + 3 * n, state_of<float>(ctx), ctx->key0, ctx->idx0, n, ctx->r_out, ctx->derr,
+                       ctx->stream);
   else
-    launch_load<double>(S, S + 3 * n, state_of<double>(ctx), n, ctx->r_out, ctx->derr, ctx->stream);
+    launch_load<double>(S, S + 3 * n, state_of<double>(ctx), ctx->key0, ctx->idx0, n, ctx->r_out, ctx->derr,
+                        ctx->stream);
   CK(cudaEventRecord(ctx->ev_free[s], ctx->stream));
   launch_init_step(ctx->st, ctx->stream);
   CK(cudaGetLastError());
@@ -677,7 +679,7 @@ int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, i
   ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   ctx->host_step = 0;
   ctx->loaded = true;
-  ctx->keys_valid = false;
+  ctx->keys_valid = true;  // the load kernel wrote the keys of its order
   // a captured step pair depends on n only through its launch shapes and scalars
   if (!same_n && ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
   return IMRP_OK;

@@ -246,10 +246,13 @@ void launch_keys(const Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, do
   k_keys<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(st, key, kidx, n, kscale);
 }
 
-// Host FP64 [n][3] positions and velocities into the state, ids 0..n-1.
+// Host FP64 [n][3] positions and velocities into the state, ids 0..n-1, with
+// the radius keys of that order (the same expression as k_keys), so that the
+// first step after a load needs no separate key pass.
 template <class T>
 __global__ void k_load(const double* __restrict__ xs, const double* __restrict__ vs, Part<T>* __restrict__ st,
-                       int64_t n, double r_out, int* err) {
+                       uint32_t* __restrict__ key, uint32_t* __restrict__ kidx, int64_t n, double r_out,
+                       double kscale, int* err) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double v[6];
@@ -265,16 +268,22 @@ __global__ void k_load(const double* __restrict__ xs, const double* __restrict__
   p.x = T(v[0]); p.y = T(v[1]); p.z = T(v[2]);
   p.vx = T(v[3]); p.vy = T(v[4]); p.vz = T(v[5]);
   p.id = uint32_t(j);
-  const double r2 = double(p.x) * double(p.x) + double(p.y) * double(p.y) + double(p.z) * double(p.z);
+  const double xd = p.x, yd = p.y, zd = p.z;
+  const double r2 = xd * xd + yd * yd + zd * zd;
   if (!fin) atomicOr(err, kErrNaN);
   else if (!(r2 > 1.0 && r2 < r_out * r_out)) atomicOr(err, kErrRange);
   st[j] = p;
+  double kf = (r2 - 1.0) * kscale;
+  kf = kf < 0.0 ? 0.0 : (kf > 4294967295.0 ? 4294967295.0 : kf);
+  key[j] = uint32_t(kf);
+  kidx[j] = uint32_t(j);
 }
 
 template <class T>
-void launch_load(const double* x, const double* v, Part<T>* st, int64_t n, double r_out, int* err,
-                 cudaStream_t s) {
-  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, v, st, n, r_out, err);
+void launch_load(const double* x, const double* v, Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n,
+                 double r_out, int* err, cudaStream_t s) {
+  const double kscale = 4294967296.0 / (r_out * r_out - 1.0);
+  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, v, st, key, kidx, n, r_out, kscale, err);
 }
 
 // out[id[j]][c] = comp_c[j] for c < nc (field values in radius order to id order)
@@ -596,8 +605,8 @@ void launch_dft(const double* q, const double* u, int64_t ns, double dt, double 
   template void launch_reorder<T>(const Part<T>*, T* const*, uint32_t*, const uint32_t*, int64_t,  \
                                   cudaStream_t);                                                   \
   template void launch_keys<T>(const Part<T>*, uint32_t*, uint32_t*, int64_t, double, cudaStream_t); \
-  template void launch_load<T>(const double*, const double*, Part<T>*, int64_t, double, int*,      \
-                               cudaStream_t);                                                      \
+  template void launch_load<T>(const double*, const double*, Part<T>*, uint32_t*, uint32_t*,       \
+                               int64_t, double, int*, cudaStream_t);                               \
   template void launch_scatter_by_id<T>(const T* const*, int, const uint32_t*, double*, int64_t,   \
                                         cudaStream_t);                                             \
   template void launch_state_out<T>(const Part<T>*, double*, double*, int64_t, cudaStream_t);     \

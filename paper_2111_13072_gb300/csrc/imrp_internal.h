@@ -39,8 +39,8 @@ void launch_reorder(const Part<T>* src, T* const* dst, uint32_t* id_dst, const u
 template <class T>
 void launch_keys(const Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, double kscale, cudaStream_t s);
 template <class T>
-void launch_load(const double* x /* [n][3] */, const double* v /* [n][3] */, Part<T>* st, int64_t n,
-                 double r_out, int* err, cudaStream_t s);
+void launch_load(const double* x /* [n][3] */, const double* v /* [n][3] */, Part<T>* st,
+                 uint32_t* key, uint32_t* kidx, int64_t n, double r_out, int* err, cudaStream_t s);
 // out[id[j]][c] = comp_c[j] for c < ncomp
 template <class T>
 void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, double* out,
