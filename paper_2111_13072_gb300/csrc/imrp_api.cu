@@ -90,7 +90,8 @@ struct imrp_ctx {
   int gseg = 32;  // least groups per segment of the group scan
   // streams / graphs
   cudaStream_t own_stream = nullptr, stream = nullptr;
-  cudaGraphExec_t graph2 = nullptr;
+  cudaGraphExec_t graph2 = nullptr;  // two steps
+  cudaGraphExec_t graph1 = nullptr;  // one step
   int graph_cur = -1;
   // device memory
   void* state = nullptr;      // Part<T>[N]: the particles in the order of the last push (or load)
@@ -144,6 +145,14 @@ namespace {
 template <class T> T** sorted_ptrs(imrp_ctx* c) { return reinterpret_cast<T**>(c->srt); }
 template <class T> Part<T>* state_of(imrp_ctx* c) { return static_cast<Part<T>*>(c->state); }
 
+// The captured step graphs hold the field arguments, buffer pointers and
+// launch shapes; any change of those drops them.
+void drop_graphs(imrp_ctx* c) {
+  if (c->graph2) cudaGraphExecDestroy(c->graph2);
+  if (c->graph1) cudaGraphExecDestroy(c->graph1);
+  c->graph2 = c->graph1 = nullptr;
+}
+
 // Super-particles per unit cube at density n_inf: N over the shell volume
 // for the uniform start, N over the electron charge of the given profile.
 double n_tilde_of(const imrp_ctx* c, int64_t n) {
@@ -152,8 +161,7 @@ double n_tilde_of(const imrp_ctx* c, int64_t n) {
 }
 
 void free_all(imrp_ctx* c) {
-  if (c->graph2) cudaGraphExecDestroy(c->graph2);
-  c->graph2 = nullptr;
+  drop_graphs(c);
   cudaFree(c->state);
   c->state = nullptr;
   for (int k = 0; k < 6; ++k) { cudaFree(c->srt[k]); c->srt[k] = nullptr; }
@@ -214,7 +222,7 @@ int grow_history(imrp_ctx* ctx, int64_t need) {
   ctx->qhist = q;
   ctx->uhist = u;
   ctx->hcap = ncap;
-  if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+  drop_graphs(ctx);
   return IMRP_OK;
 }
 
@@ -316,43 +324,47 @@ int enqueue_any(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nullptr) {
   return ctx->prec == 1 ? enqueue<float>(ctx, record, ev) : enqueue<double>(ctx, record, ev);
 }
 
+// Captures `count` steps (1 or 2) of the current configuration into *out.
+int capture_steps(imrp_ctx* ctx, int count, cudaGraphExec_t* out) {
+  const int cur0 = ctx->cur;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  int r = 0;
+  for (int k = 0; k < count && !r; ++k) r = enqueue_any(ctx, true);
+  cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
+  if (r) { if (g) cudaGraphDestroy(g); return r; }
+  if (ec != cudaSuccess) return ctx->fail(IMRP_E_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+  ec = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ec != cudaSuccess) return ctx->fail(IMRP_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+  ctx->cur = cur0;  // capture did not execute anything
+  return IMRP_OK;
+}
+
 int launch_steps(imrp_ctx* ctx, int64_t nsteps) {
   int rc = grow_history(ctx, ctx->host_step + nsteps + 1);
   if (rc) return rc;
   int64_t done = 0;
-  // keys must be valid before a captured pair (the pair assumes the push wrote them)
-  while (done < nsteps && (!ctx->keys_valid || (nsteps - done) < 2)) {
+  // keys must be valid before a captured step (it assumes that the push or
+  // the load wrote them)
+  while (done < nsteps && !ctx->keys_valid) {
     rc = enqueue_any(ctx, true);
     if (rc) return rc;
     CK(cudaGetLastError());
     ++done;
   }
-  if (nsteps - done >= 2) {
-    if (!ctx->graph2 || ctx->graph_cur != ctx->cur) {
-      if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
-      const int cur0 = ctx->cur;
-      cudaGraph_t g = nullptr;
-      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      int r1 = enqueue_any(ctx, true);
-      int r2 = r1 ? r1 : enqueue_any(ctx, true);
-      cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
-      if (r2) { if (g) cudaGraphDestroy(g); return r2; }
-      if (ec != cudaSuccess) return ctx->fail(IMRP_E_CUDA, "graph capture: %s", cudaGetErrorString(ec));
-      ec = cudaGraphInstantiate(&ctx->graph2, g, 0);
-      cudaGraphDestroy(g);
-      if (ec != cudaSuccess) return ctx->fail(IMRP_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
-      ctx->cur = cur0;  // capture did not execute anything
-      ctx->graph_cur = cur0;
-    }
-    while (nsteps - done >= 2) {
-      CK(cudaGraphLaunch(ctx->graph2, ctx->stream));
-      done += 2;
-    }
-    if (done < nsteps) {
-      rc = enqueue_any(ctx, true);
+  if (done < nsteps && ctx->graph_cur != ctx->cur) drop_graphs(ctx);
+  // pairs, then a single step for an odd remainder (one captured graph each)
+  while (done < nsteps) {
+    const int k = nsteps - done >= 2 ? 2 : 1;
+    cudaGraphExec_t& ge = k == 2 ? ctx->graph2 : ctx->graph1;
+    if (!ge) {
+      rc = capture_steps(ctx, k, &ge);
       if (rc) return rc;
-      ++done;
+      ctx->graph_cur = ctx->cur;
     }
+    CK(cudaGraphLaunch(ge, ctx->stream));
+    done += k;
   }
   CK(cudaGetLastError());
   ctx->host_step += nsteps;
@@ -577,7 +589,7 @@ int imrp_set_ion_profile(imrp_ctx* ctx, const double* q_ion, int64_t n_tab, doub
   }
   if (ctx->loaded) ctx->n_tilde = n_tilde_of(ctx, ctx->n);
   // the captured step pair holds the old field arguments
-  if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+  drop_graphs(ctx);
   return IMRP_OK;
 }
 
@@ -601,6 +613,7 @@ int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t
   s0.kick = 0;
   s0.sync = 1;
   CK(cudaMemcpyAsync(ctx->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->stream));
+  const bool same_n = ctx->loaded && ctx->n == n;
   int rc = check_err(ctx);
   if (rc) { ctx->loaded = false; return rc; }
   ctx->n = n;
@@ -611,7 +624,8 @@ int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t
   ctx->host_step = 0;
   ctx->loaded = true;
   ctx->keys_valid = true;  // the load kernel wrote the keys of its order
-  if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+  // the captured steps depend on n only through their launch shapes and scalars
+  if (!same_n) drop_graphs(ctx);
   return IMRP_OK;
 }
 
@@ -681,7 +695,7 @@ int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, i
   ctx->loaded = true;
   ctx->keys_valid = true;  // the load kernel wrote the keys of its order
   // a captured step pair depends on n only through its launch shapes and scalars
-  if (!same_n && ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+  if (!same_n) drop_graphs(ctx);
   return IMRP_OK;
 }
 
@@ -856,7 +870,7 @@ extern "C" int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* gseg_out) {
     }
     ctx->gseg = best_c;
   }
-  if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+  drop_graphs(ctx);
   if (wpb_out) *wpb_out = ctx->wpb;
   if (gseg_out) *gseg_out = ctx->gseg;
   return check_err(ctx);

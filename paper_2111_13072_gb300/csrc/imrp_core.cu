@@ -262,8 +262,11 @@ __global__ void k_load(const double* __restrict__ xs, const double* __restrict__
     v[c] = xs[3 * j + c];
     v[3 + c] = vs[3 * j + c];
   }
+  // finiteness from the exponent bits (integer work: FP64 operations run at a
+  // small fraction of the FP32 rate on this part and bound this kernel)
 #pragma unroll
-  for (int c = 0; c < 6; ++c) fin = fin && isfinite(v[c]);
+  for (int c = 0; c < 6; ++c)
+    fin = fin && ((uint32_t(__double_as_longlong(v[c]) >> 32) & 0x7ff00000u) != 0x7ff00000u);
   Part<T> p;
   p.x = T(v[0]); p.y = T(v[1]); p.z = T(v[2]);
   p.vx = T(v[3]); p.vy = T(v[4]); p.vz = T(v[5]);
