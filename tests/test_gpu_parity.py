@@ -139,13 +139,45 @@ def test_qdiff_and_drive_sequence(imrp):
     p, op = _pair(imrp, BASE, n, precision=0, l_max=4)
     with imrp.Sim(p) as sim:
         sim.load(x, v)
-        q1, u1 = sim.step(17)   # odd: eager steps and graph pairs
+        q1, u1 = sim.step(17)   # odd: graph pairs and a one-step graph
         q2, u2 = sim.step(23)
         qa, ua = sim.qdiff()
     xo, vo, qo, uo, _ = oracle.run(op, x, v, 40)
     np.testing.assert_allclose(np.concatenate([u1, u2]), uo, rtol=1e-12)
     np.testing.assert_allclose(qa, np.concatenate([q1, q2]), rtol=0, atol=0)
     np.testing.assert_allclose(qa, qo, rtol=1e-6, atol=1e-9 * np.max(np.abs(qo)))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_steps_pairs_and_reloads_agree(imrp, prec):
+    """Captured one-step and two-step graphs replay the same kernels: five
+    single steps, one call of five steps, and a context that first ran another
+    state of the same size and then reloaded (keeping its captured graphs)
+    give bitwise the same particles and Q_diff."""
+    n = 3001
+    x, v = workload_state(BASE, N=n)
+    x2, v2 = workload_state(BASE, N=n)[0][::-1].copy(), workload_state(BASE, N=n)[1][::-1].copy()
+    p, _ = _pair(imrp, BASE, n, precision=prec, l_max=8)
+    with imrp.Sim(p) as a, imrp.Sim(p) as b, imrp.Sim(p) as c:
+        a.load(x, v)
+        for _ in range(5):
+            a.step(1)
+        b.load(x, v)
+        b.step(5)
+        c.load(x2, v2)
+        c.step(3)
+        c.load(x, v)
+        c.step(5)
+        xa, va = a.particles()
+        xb, vb = b.particles()
+        xc, vc = c.particles()
+        qa, qb, qc = a.qdiff()[0], b.qdiff()[0], c.qdiff()[0]
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(va, vb)
+    np.testing.assert_array_equal(xc, xb)
+    np.testing.assert_array_equal(vc, vb)
+    np.testing.assert_array_equal(qa, qb)
+    np.testing.assert_array_equal(qc, qb)
 
 
 def test_errors_are_reported(imrp):
