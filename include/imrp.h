@@ -81,7 +81,7 @@ typedef struct imrp_info {
   double lambda_D;   /* Debye length in units of R                                 */
   double omega_pe;   /* electron plasma frequency [1/s]                            */
   int64_t n;         /* particles currently loaded                                 */
-  int64_t step;      /* steps taken since the last load                            */
+  int64_t step;      /* steps taken since the last load (a restore sets it)        */
   int32_t l_max;
   int32_t precision;
 } imrp_info;
@@ -172,6 +172,26 @@ int imrp_get_field(imrp_ctx* ctx, double* E);
 /* Current state in particle-id order: x[n][3] and the half-step velocity
  * v_{n-1/2}[n][3] (v synchronous with x right after a load). Either may be NULL. */
 int imrp_get_particles(imrp_ctx* ctx, double* x, double* v);
+
+/* Checkpoint of a run: the state in its storage order (the order of the last
+ * push), x[n][3], v[n][3] (the half-step velocity), the particle ids id[n],
+ * and *step, the number of steps taken since the load. Host arrays of the
+ * loaded n. With imrp_restore it continues the run bit for bit: the wall and
+ * collision random numbers are counter based on (seed, id, step), and the
+ * storage order keeps the order of equal radius keys. Errors: IMRP_E_INVAL
+ * (a NULL output), IMRP_E_STATE (nothing loaded). */
+int imrp_checkpoint(imrp_ctx* ctx, double* x, double* v, uint32_t* id, int64_t* step);
+
+/* Restores a checkpoint into a context made with the same parameters: the
+ * state in the given order with the given ids (a permutation of 0..n-1), the
+ * next step is `step`, and the velocities are taken as a half step behind
+ * the positions (as imrp_checkpoint returns them) unless step == 0. Q_diff is
+ * recorded from step `step` on: imrp_get_qdiff takes first >= step, and
+ * imrp_spectrum, which needs the series from the drive, returns IMRP_E_STATE
+ * (transform the joined series with imrp_admittance instead). Errors:
+ * IMRP_E_INVAL (n out of range, step < 0, ids not a permutation, a particle
+ * outside 1 < r < r_out), IMRP_E_NAN, IMRP_E_CUDA. */
+int imrp_restore(imrp_ctx* ctx, const double* x, const double* v, const uint32_t* id, int64_t n, int64_t step);
 
 /* Spectrum of the run since the last load (Sec. 4): admittance
  * Y(w) = i w Q^(w)/U^(w) with Q^ = dt sum_n (Q_n - Q_0) e^{-i w t_n} and

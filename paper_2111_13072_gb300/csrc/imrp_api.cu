@@ -83,6 +83,8 @@ struct imrp_ctx {
   double f[kTabL] = {0}, canti[kTabL] = {0};
   int64_t cap = 0, n = 0;
   int64_t host_step = 0;
+  int64_t hist_first = 0;     // step of the last load (0) or restore: qhist[k] is Q_diff of step hist_first + k
+  uint64_t gen = 0;           // configuration generation: bumped whenever the captured graphs are dropped
   bool loaded = false, keys_valid = false;
   int nc = 0;
   int64_t ntiles = 0, ngroups = 0;
@@ -151,6 +153,7 @@ void drop_graphs(imrp_ctx* c) {
   if (c->graph2) cudaGraphExecDestroy(c->graph2);
   if (c->graph1) cudaGraphExecDestroy(c->graph1);
   c->graph2 = c->graph1 = nullptr;
+  ++c->gen;  // batches that captured this context recapture too
 }
 
 // Super-particles per unit cube at density n_inf: N over the shell volume
@@ -260,6 +263,7 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   fa.qhist = ctx->qhist;
   fa.uhist = ctx->uhist;
   fa.cap = ctx->hcap;
+  fa.first = ctx->hist_first;
   fa.record = record ? 1 : 0;
   fa.L = ctx->L;
   fa.drive_kind = ctx->p.drive_kind;
@@ -342,7 +346,7 @@ int capture_steps(imrp_ctx* ctx, int count, cudaGraphExec_t* out) {
 }
 
 int launch_steps(imrp_ctx* ctx, int64_t nsteps) {
-  int rc = grow_history(ctx, ctx->host_step + nsteps + 1);
+  int rc = grow_history(ctx, ctx->host_step - ctx->hist_first + nsteps + 1);
   if (rc) return rc;
   int64_t done = 0;
   // keys must be valid before a captured step (it assumes that the push or
@@ -601,11 +605,11 @@ int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t
   CK(cudaMemcpyAsync(ctx->stage + 3 * n, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   ctx->cur = 0;
   if (ctx->prec == 1)
-    launch_load<float>(ctx->stage, ctx->stage + 3 * n, state_of<float>(ctx), ctx->key0, ctx->idx0, n,
-                       ctx->r_out, ctx->derr, ctx->stream);
+    launch_load<float>(ctx->stage, ctx->stage + 3 * n, nullptr, state_of<float>(ctx), ctx->key0, ctx->idx0,
+                       n, ctx->r_out, ctx->derr, ctx->stream);
   else
-    launch_load<double>(ctx->stage, ctx->stage + 3 * n, state_of<double>(ctx), ctx->key0, ctx->idx0, n,
-                        ctx->r_out, ctx->derr, ctx->stream);
+    launch_load<double>(ctx->stage, ctx->stage + 3 * n, nullptr, state_of<double>(ctx), ctx->key0, ctx->idx0,
+                        n, ctx->r_out, ctx->derr, ctx->stream);
   StepState s0{};
   s0.step = 0;
   s0.next = 0;
@@ -613,7 +617,7 @@ int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t
   s0.kick = 0;
   s0.sync = 1;
   CK(cudaMemcpyAsync(ctx->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->stream));
-  const bool same_n = ctx->loaded && ctx->n == n;
+  const bool same_n = ctx->loaded && ctx->n == n && ctx->hist_first == 0;
   int rc = check_err(ctx);
   if (rc) { ctx->loaded = false; return rc; }
   ctx->n = n;
@@ -622,6 +626,7 @@ int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t
   ctx->ntiles = (n + 31) / 32;
   ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   ctx->host_step = 0;
+  ctx->hist_first = 0;
   ctx->loaded = true;
   ctx->keys_valid = true;  // the load kernel wrote the keys of its order
   // the captured steps depend on n only through their launch shapes and scalars
@@ -645,12 +650,14 @@ int imrp_sync(imrp_ctx* ctx) {
 
 int imrp_get_qdiff(imrp_ctx* ctx, int64_t first, int64_t count, double* qd, double* ua) {
   if (!ctx) return IMRP_E_INVAL;
-  if (first < 0 || count < 0 || first + count > ctx->host_step)
-    return ctx->fail(IMRP_E_INVAL, "get_qdiff: range [%lld, %lld) outside the %lld recorded steps",
-                     (long long)first, (long long)(first + count), (long long)ctx->host_step);
+  if (first < ctx->hist_first || count < 0 || first + count > ctx->host_step)
+    return ctx->fail(IMRP_E_INVAL, "get_qdiff: range [%lld, %lld) outside the recorded steps [%lld, %lld)",
+                     (long long)first, (long long)(first + count), (long long)ctx->hist_first,
+                     (long long)ctx->host_step);
   if (count == 0) return IMRP_OK;
-  if (qd) CK(cudaMemcpyAsync(qd, ctx->qhist + first, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  if (ua) CK(cudaMemcpyAsync(ua, ctx->uhist + first, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  const int64_t h = first - ctx->hist_first;
+  if (qd) CK(cudaMemcpyAsync(qd, ctx->qhist + h, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (ua) CK(cudaMemcpyAsync(ua, ctx->uhist + h, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return check_err(ctx);
 }
 
@@ -676,15 +683,15 @@ int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, i
   CK(cudaEventRecord(ctx->ev_copied[s], ctx->copy_stream));
   CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[s], 0));
   if (ctx->prec == 1)
-    launch_load<float>(S, S + 3 * n, state_of<float>(ctx), ctx->key0, ctx->idx0, n, ctx->r_out, ctx->derr,
-                       ctx->stream);
+    launch_load<float>(S, S + 3 * n, nullptr, state_of<float>(ctx), ctx->key0, ctx->idx0, n, ctx->r_out,
+                       ctx->derr, ctx->stream);
   else
-    launch_load<double>(S, S + 3 * n, state_of<double>(ctx), ctx->key0, ctx->idx0, n, ctx->r_out, ctx->derr,
-                        ctx->stream);
+    launch_load<double>(S, S + 3 * n, nullptr, state_of<double>(ctx), ctx->key0, ctx->idx0, n, ctx->r_out,
+                        ctx->derr, ctx->stream);
   CK(cudaEventRecord(ctx->ev_free[s], ctx->stream));
   launch_init_step(ctx->st, ctx->stream);
   CK(cudaGetLastError());
-  const bool same_n = ctx->loaded && ctx->n == n;
+  const bool same_n = ctx->loaded && ctx->n == n && ctx->hist_first == 0;
   ctx->cur = 0;
   ctx->n = n;
   ctx->n_tilde = n_tilde_of(ctx, n);
@@ -692,6 +699,7 @@ int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, i
   ctx->ntiles = (n + 31) / 32;
   ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   ctx->host_step = 0;
+  ctx->hist_first = 0;
   ctx->loaded = true;
   ctx->keys_valid = true;  // the load kernel wrote the keys of its order
   // a captured step pair depends on n only through its launch shapes and scalars
@@ -701,12 +709,14 @@ int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, i
 
 int imrp_copy_qdiff_async(imrp_ctx* ctx, int64_t first, int64_t count, double* qd, double* ua) {
   if (!ctx) return IMRP_E_INVAL;
-  if (first < 0 || count < 0 || first + count > ctx->host_step)
-    return ctx->fail(IMRP_E_INVAL, "copy_qdiff_async: range [%lld, %lld) outside the %lld recorded steps",
-                     (long long)first, (long long)(first + count), (long long)ctx->host_step);
+  if (first < ctx->hist_first || count < 0 || first + count > ctx->host_step)
+    return ctx->fail(IMRP_E_INVAL, "copy_qdiff_async: range [%lld, %lld) outside the recorded steps [%lld, %lld)",
+                     (long long)first, (long long)(first + count), (long long)ctx->hist_first,
+                     (long long)ctx->host_step);
   if (count == 0) return IMRP_OK;
-  if (qd) CK(cudaMemcpyAsync(qd, ctx->qhist + first, count * sizeof(double), cudaMemcpyDefault, ctx->stream));
-  if (ua) CK(cudaMemcpyAsync(ua, ctx->uhist + first, count * sizeof(double), cudaMemcpyDefault, ctx->stream));
+  const int64_t h = first - ctx->hist_first;
+  if (qd) CK(cudaMemcpyAsync(qd, ctx->qhist + h, count * sizeof(double), cudaMemcpyDefault, ctx->stream));
+  if (ua) CK(cudaMemcpyAsync(ua, ctx->uhist + h, count * sizeof(double), cudaMemcpyDefault, ctx->stream));
   return IMRP_OK;
 }
 
@@ -750,10 +760,76 @@ int imrp_get_particles(imrp_ctx* ctx, double* x, double* v) {
   return check_err(ctx);
 }
 
+int imrp_checkpoint(imrp_ctx* ctx, double* x, double* v, uint32_t* id, int64_t* step) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (!x || !v || !id || !step) return ctx->fail(IMRP_E_INVAL, "checkpoint: null output");
+  if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "checkpoint before load");
+  const int64_t n = ctx->n;
+  uint32_t* ids = ctx->key1;  // free between steps
+  if (ctx->prec == 1)
+    launch_state_dump<float>(state_of<float>(ctx), ctx->stage, ctx->stage + 3 * n, ids, n, ctx->stream);
+  else
+    launch_state_dump<double>(state_of<double>(ctx), ctx->stage, ctx->stage + 3 * n, ids, n, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(x, ctx->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(v, ctx->stage + 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(id, ids, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  *step = ctx->host_step;
+  return check_err(ctx);
+}
+
+int imrp_restore(imrp_ctx* ctx, const double* x, const double* v, const uint32_t* id, int64_t n, int64_t step) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (!x || !v || !id || n < 1 || n > ctx->cap)
+    return ctx->fail(IMRP_E_INVAL, "restore: n = %lld out of range [1, %lld]", (long long)n, (long long)ctx->cap);
+  if (step < 0) return ctx->fail(IMRP_E_INVAL, "restore: step %lld < 0", (long long)step);
+  {
+    // the ids must be a permutation of 0..n-1 (they index the output and the random numbers)
+    std::vector<uint8_t> seen(size_t(n), 0);
+    for (int64_t j = 0; j < n; ++j) {
+      if (int64_t(id[j]) >= n || seen[id[j]])
+        return ctx->fail(IMRP_E_INVAL, "restore: ids are not a permutation of 0..n-1 (entry %lld)", (long long)j);
+      seen[id[j]] = 1;
+    }
+  }
+  CK(cudaMemcpyAsync(ctx->stage, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->stage + 3 * n, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->key1, id, n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  ctx->cur = 0;
+  if (ctx->prec == 1)
+    launch_load<float>(ctx->stage, ctx->stage + 3 * n, ctx->key1, state_of<float>(ctx), ctx->key0, ctx->idx0, n,
+                       ctx->r_out, ctx->derr, ctx->stream);
+  else
+    launch_load<double>(ctx->stage, ctx->stage + 3 * n, ctx->key1, state_of<double>(ctx), ctx->key0, ctx->idx0,
+                        n, ctx->r_out, ctx->derr, ctx->stream);
+  // the step state as the run left it: the next step is `step`, velocities a
+  // half step behind the positions unless nothing was stepped yet
+  StepState s0{};
+  s0.step = step;
+  s0.next = step;
+  s0.u = 0;
+  s0.kick = 0;
+  s0.sync = step == 0 ? 1 : 0;
+  CK(cudaMemcpyAsync(ctx->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->stream));
+  int rc = check_err(ctx);
+  if (rc) { ctx->loaded = false; return rc; }
+  ctx->n = n;
+  ctx->n_tilde = n_tilde_of(ctx, n);
+  ctx->n_ion = double(n);
+  ctx->ntiles = (n + 31) / 32;
+  ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
+  ctx->host_step = step;
+  ctx->hist_first = step;
+  ctx->loaded = true;
+  ctx->keys_valid = true;
+  drop_graphs(ctx);  // the history offset is part of the captured arguments
+  return IMRP_OK;
+}
+
 int imrp_profile_steps(imrp_ctx* ctx, int64_t n_steps, double* ms) {
   if (!ctx || !ms || n_steps < 1) return IMRP_E_INVAL;
   if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "profile before load");
-  int rc = grow_history(ctx, ctx->host_step + n_steps + 1);
+  int rc = grow_history(ctx, ctx->host_step - ctx->hist_first + n_steps + 1);
   if (rc) return rc;
   for (int k = 0; k < IMRP_N_STAGES; ++k) ms[k] = 0.0;
   std::vector<cudaEvent_t> ev(size_t(n_steps) * (IMRP_N_STAGES + 1));
@@ -885,6 +961,7 @@ struct imrp_batch {
   cudaGraphExec_t g = nullptr;
   std::vector<int> cur_at_capture;
   std::vector<const double*> hist_at_capture;
+  std::vector<uint64_t> gen_at_capture;
   std::string err;
 };
 
@@ -952,7 +1029,7 @@ extern "C" int imrp_batch_step(imrp_batch* b, int64_t n_steps) {
   const int n = int(b->c.size());
   // prior work of each context happens before the batch; histories large enough
   for (imrp_ctx* ctx : b->c) {
-    int rc = grow_history(ctx, ctx->host_step + n_steps + 1);
+    int rc = grow_history(ctx, ctx->host_step - ctx->hist_first + n_steps + 1);
     if (rc) return batch_fail(b, ctx, rc);
     rc = ensure_keys(ctx);
     if (rc) return batch_fail(b, ctx, rc);
@@ -963,7 +1040,8 @@ extern "C" int imrp_batch_step(imrp_batch* b, int64_t n_steps) {
   if (pairs > 0) {
     bool valid = b->g != nullptr;
     for (int i = 0; i < n && valid; ++i)
-      valid = b->cur_at_capture[i] == b->c[i]->cur && b->hist_at_capture[i] == b->c[i]->qhist;
+      valid = b->cur_at_capture[i] == b->c[i]->cur && b->hist_at_capture[i] == b->c[i]->qhist &&
+              b->gen_at_capture[i] == b->c[i]->gen;
     if (!valid) {
       if (b->g) { cudaGraphExecDestroy(b->g); b->g = nullptr; }
       cudaGraph_t g = nullptr;
@@ -988,9 +1066,11 @@ extern "C" int imrp_batch_step(imrp_batch* b, int64_t n_steps) {
       if (ec != cudaSuccess) { b->err = cudaGetErrorString(ec); return IMRP_E_CUDA; }
       b->cur_at_capture.resize(n);
       b->hist_at_capture.resize(n);
+      b->gen_at_capture.resize(n);
       for (int i = 0; i < n; ++i) {
         b->cur_at_capture[i] = b->c[i]->cur;
         b->hist_at_capture[i] = b->c[i]->qhist;
+        b->gen_at_capture[i] = b->c[i]->gen;
       }
     }
     for (int64_t k = 0; k < pairs; ++k)
@@ -1143,6 +1223,9 @@ void fit_damped(const std::vector<double>& tau, const std::vector<double>& y, do
 extern "C" int imrp_spectrum(imrp_ctx* ctx, int64_t n_freq, double w_max, double* omega, double* reY,
                              double* imY, double* w_res, double* dw, double* fit) {
   if (!ctx) return IMRP_E_INVAL;
+  if (ctx->hist_first != 0)
+    return ctx->fail(IMRP_E_STATE, "spectrum after a restore: the history starts at step %lld, not at the drive; "
+                     "transform the whole series with imrp_admittance", (long long)ctx->hist_first);
   const int64_t ns = ctx->host_step;
   if (ns < 8) return ctx->fail(IMRP_E_STATE, "spectrum needs at least 8 recorded steps (have %lld)", (long long)ns);
   if (n_freq < 3 || !(w_max > 0)) return ctx->fail(IMRP_E_INVAL, "spectrum: n_freq >= 3 and w_max > 0 required");

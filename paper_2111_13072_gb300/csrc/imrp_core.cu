@@ -250,9 +250,9 @@ void launch_keys(const Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, do
 // the radius keys of that order (the same expression as k_keys), so that the
 // first step after a load needs no separate key pass.
 template <class T>
-__global__ void k_load(const double* __restrict__ xs, const double* __restrict__ vs, Part<T>* __restrict__ st,
-                       uint32_t* __restrict__ key, uint32_t* __restrict__ kidx, int64_t n, double r_out,
-                       double kscale, int* err) {
+__global__ void k_load(const double* __restrict__ xs, const double* __restrict__ vs,
+                       const uint32_t* __restrict__ ids, Part<T>* __restrict__ st, uint32_t* __restrict__ key,
+                       uint32_t* __restrict__ kidx, int64_t n, double r_out, double kscale, int* err) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double v[6];
@@ -270,7 +270,7 @@ __global__ void k_load(const double* __restrict__ xs, const double* __restrict__
   Part<T> p;
   p.x = T(v[0]); p.y = T(v[1]); p.z = T(v[2]);
   p.vx = T(v[3]); p.vy = T(v[4]); p.vz = T(v[5]);
-  p.id = uint32_t(j);
+  p.id = ids ? ids[j] : uint32_t(j);
   const double xd = p.x, yd = p.y, zd = p.z;
   const double r2 = xd * xd + yd * yd + zd * zd;
   if (!fin) atomicOr(err, kErrNaN);
@@ -283,10 +283,26 @@ __global__ void k_load(const double* __restrict__ xs, const double* __restrict__
 }
 
 template <class T>
-void launch_load(const double* x, const double* v, Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n,
-                 double r_out, int* err, cudaStream_t s) {
+void launch_load(const double* x, const double* v, const uint32_t* ids, Part<T>* st, uint32_t* key,
+                 uint32_t* kidx, int64_t n, double r_out, int* err, cudaStream_t s) {
   const double kscale = 4294967296.0 / (r_out * r_out - 1.0);
-  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, v, st, key, kidx, n, r_out, kscale, err);
+  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, v, ids, st, key, kidx, n, r_out, kscale, err);
+}
+
+template <class T>
+__global__ void k_state_dump(const Part<T>* __restrict__ st, double* __restrict__ x, double* __restrict__ v,
+                             uint32_t* __restrict__ id, int64_t n) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const Part<T> p = st[j];
+  x[3 * j] = p.x; x[3 * j + 1] = p.y; x[3 * j + 2] = p.z;
+  v[3 * j] = p.vx; v[3 * j + 1] = p.vy; v[3 * j + 2] = p.vz;
+  id[j] = p.id;
+}
+
+template <class T>
+void launch_state_dump(const Part<T>* st, double* x, double* v, uint32_t* id, int64_t n, cudaStream_t s) {
+  k_state_dump<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(st, x, v, id, n);
 }
 
 // out[id[j]][c] = comp_c[j] for c < nc (field values in radius order to id order)
@@ -540,9 +556,10 @@ __global__ void k_finalize(FinalizeArgs a) {
     double q = 0.0;
     for (int l = 1; l <= a.L; l += 2) q += a.canti[l] * a.totd[2 * (l - 1) + 1];
     q *= -a.inv_ntilde;
-    if (n < a.cap) {
-      a.qhist[n] = q;
-      a.uhist[n] = u;
+    const int64_t h = n - a.first;
+    if (h >= 0 && h < a.cap) {
+      a.qhist[h] = q;
+      a.uhist[h] = u;
     }
     st->next = n + 1;
     st->sync = 0;
@@ -608,8 +625,10 @@ void launch_dft(const double* q, const double* u, int64_t ns, double dt, double 
   template void launch_reorder<T>(const Part<T>*, T* const*, uint32_t*, const uint32_t*, int64_t,  \
                                   cudaStream_t);                                                   \
   template void launch_keys<T>(const Part<T>*, uint32_t*, uint32_t*, int64_t, double, cudaStream_t); \
-  template void launch_load<T>(const double*, const double*, Part<T>*, uint32_t*, uint32_t*,       \
-                               int64_t, double, int*, cudaStream_t);                               \
+  template void launch_load<T>(const double*, const double*, const uint32_t*, Part<T>*, uint32_t*, \
+                               uint32_t*, int64_t, double, int*, cudaStream_t);                    \
+  template void launch_state_dump<T>(const Part<T>*, double*, double*, uint32_t*, int64_t,         \
+                                     cudaStream_t);                                                \
   template void launch_scatter_by_id<T>(const T* const*, int, const uint32_t*, double*, int64_t,   \
                                         cudaStream_t);                                             \
   template void launch_state_out<T>(const Part<T>*, double*, double*, int64_t, cudaStream_t);     \

@@ -39,8 +39,11 @@ void launch_reorder(const Part<T>* src, T* const* dst, uint32_t* id_dst, const u
 template <class T>
 void launch_keys(const Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, double kscale, cudaStream_t s);
 template <class T>
-void launch_load(const double* x /* [n][3] */, const double* v /* [n][3] */, Part<T>* st,
-                 uint32_t* key, uint32_t* kidx, int64_t n, double r_out, int* err, cudaStream_t s);
+void launch_load(const double* x /* [n][3] */, const double* v /* [n][3] */, const uint32_t* ids /* or null */,
+                 Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, double r_out, int* err, cudaStream_t s);
+// The state in its storage order: x[j][3], v[j][3], id[j] (checkpoint).
+template <class T>
+void launch_state_dump(const Part<T>* st, double* x, double* v, uint32_t* id, int64_t n, cudaStream_t s);
 // out[id[j]][c] = comp_c[j] for c < ncomp
 template <class T>
 void launch_scatter_by_id(const T* const* comps, int ncomp, const uint32_t* id, double* out,
@@ -65,9 +68,10 @@ void launch_group_scan(const double* gagg, double* work, unsigned* ticket, T* gb
 struct FinalizeArgs {
   StepState* st;
   const double* totd;
-  double* qhist;
+  double* qhist;     // qhist[n - first] holds Q_diff of step n (first: step of the load or restore)
   double* uhist;
   int64_t cap;
+  int64_t first;
   int record;
   int L;
   int drive_kind;

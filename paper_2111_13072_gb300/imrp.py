@@ -24,7 +24,7 @@ EXPORTS = [
     "imrp_batch_destroy", "imrp_batch_last_error", "imrp_batch_set_stream", "imrp_footprint",
     "imrp_load_particles_async", "imrp_copy_qdiff_async", "imrp_drude_fit", "imrp_drude_k",
     "imrp_drude_te", "imrp_admittance", "imrp_fit_damped_sine", "imrp_sheath_solve",
-    "imrp_set_ion_profile",
+    "imrp_set_ion_profile", "imrp_checkpoint", "imrp_restore",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -109,6 +109,9 @@ def load_library(path: str = LIB_PATH):
     L.imrp_drude_te.argtypes = [ctypes.c_double] * 4 + [pd]
     L.imrp_sheath_solve.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int64] + [pd] * 5
     L.imrp_set_ion_profile.argtypes = [c_void_p, pd, ctypes.c_int64, ctypes.c_double, ctypes.c_double]
+    pu32 = P(ctypes.c_uint32)
+    L.imrp_checkpoint.argtypes = [c_void_p, pd, pd, pu32, P(ctypes.c_int64)]
+    L.imrp_restore.argtypes = [c_void_p, pd, pd, pu32, ctypes.c_int64, ctypes.c_int64]
     for name in EXPORTS:
         if name not in ("imrp_default_params", "imrp_last_error", "imrp_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -310,6 +313,27 @@ class Sim:
         v = np.ascontiguousarray(v, dtype=np.float64)
         assert x.shape == v.shape and x.ndim == 2 and x.shape[1] == 3
         self._check(self._lib.imrp_load_particles(self._h, _ptr(x), _ptr(v), x.shape[0]))
+
+    def checkpoint(self):
+        """imrp_checkpoint: (x, v, ids, step) of the run in its storage order."""
+        n = self.info().n
+        x = np.zeros((n, 3)); v = np.zeros((n, 3))
+        ids = np.zeros(n, dtype=np.uint32)
+        step = ctypes.c_int64()
+        self._check(self._lib.imrp_checkpoint(self._h, _ptr(x), _ptr(v),
+                                              ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                              ctypes.byref(step)))
+        return x, v, ids, int(step.value)
+
+    def restore(self, x, v, ids, step: int):
+        """imrp_restore: continues a run from imrp_checkpoint's output."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        assert x.shape == v.shape and x.ndim == 2 and x.shape[1] == 3 and ids.shape == (x.shape[0],)
+        self._check(self._lib.imrp_restore(self._h, _ptr(x), _ptr(v),
+                                           ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                           x.shape[0], step))
 
     def set_ion_profile(self, q_ion, q_elec_total: float, q_s: float):
         """imrp_set_ion_profile: immobile ions of a radial profile (units e n_inf R^3);
