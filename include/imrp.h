@@ -6,7 +6,8 @@
  * One context owns one plasma instance on one GPU: N electron super-particles
  * (charge q = -1, mass m = 1 in the units below) around a metal sphere of radius
  * R_E covered by a dielectric shell (permittivity eps_D) out to R, with an
- * immobile uniform ion background filling R <= r <= R_out.
+ * immobile ion background filling R <= r <= R_out: uniform, or the radial
+ * profile of the floating sheath equilibrium (App. D, imrp_set_ion_profile).
  *
  * Units (Sec. 4 of the paper): lengths in R (= R_D, outer radius of the
  * dielectric), time in 1/omega_pe, velocities in R*omega_pe, charge in e, mass
@@ -116,9 +117,10 @@ int imrp_set_stream(imrp_ctx* ctx, void* cuda_stream);
 /* Loads n <= N particles from host FP64 arrays x[n][3] (positions, units of R,
  * each with 1 < |x| < r_out) and v[n][3] (velocities synchronous with x, units
  * of R omega_pe). Particle ids are 0..n-1 in input order. Resets the step
- * counter and the Q_diff history; the ion background is set to n ions.
- * Errors: IMRP_E_INVAL (n out of range, a position outside the shell, a
- * non-finite value). */
+ * counter and the Q_diff history; the uniform ion background is set to n
+ * ions (with a profile from imrp_set_ion_profile, n~ = n / its electron
+ * charge instead). Errors: IMRP_E_INVAL (n out of range, a position outside
+ * the shell, a non-finite value). */
 int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t n);
 
 /* Streamed form of imrp_load_particles, for callers that feed a new particle
