@@ -53,7 +53,8 @@ class _FieldParams(ctypes.Structure):
                 ("n_tilde", ctypes.c_double), ("n_ion", ctypes.c_double), ("q_s", ctypes.c_double),
                 ("L", ctypes.c_int32), ("m0_only", ctypes.c_int32), ("self_image", ctypes.c_int32),
                 ("pad", ctypes.c_int32), ("ion_q", ctypes.POINTER(ctypes.c_double)),
-                ("ion_n", ctypes.c_int64)]
+                ("ion_n", ctypes.c_int64), ("charge", ctypes.POINTER(ctypes.c_double)),
+                ("mass", ctypes.POINTER(ctypes.c_double))]
 
 
 class _RunParams(ctypes.Structure):
@@ -121,15 +122,22 @@ class Params:
     # immobile ions of a radial profile (App. D): ion charge inside
     # r_k = 1 + k (r_out - 1)/(len - 1) in super-particle charges; None: uniform n_ion
     ion_q: np.ndarray = None
+    # mobile ions as particles: charge (e) and mass (m_e) per particle, in the
+    # order of the arrays passed with these parameters; None: all electrons
+    charge: np.ndarray = None
+    mass: np.ndarray = None
 
     def field(self) -> _FieldParams:
-        if self.ion_q is None:
-            return _FieldParams(self.d, self.eps, self.r_out, self.n_tilde, self.n_ion, self.q_s,
-                                self.L, self.m0_only, self.self_image, 0, None, 0)
-        self.ion_q = np.ascontiguousarray(self.ion_q, dtype=np.float64)
-        assert self.ion_q.ndim == 1 and len(self.ion_q) >= 2
+        for name in ("ion_q", "charge", "mass"):
+            a = getattr(self, name)
+            if a is not None:
+                setattr(self, name, np.ascontiguousarray(a, dtype=np.float64))
+        if self.ion_q is not None:
+            assert self.ion_q.ndim == 1 and len(self.ion_q) >= 2
         return _FieldParams(self.d, self.eps, self.r_out, self.n_tilde, self.n_ion, self.q_s,
-                            self.L, self.m0_only, self.self_image, 0, _p(self.ion_q), len(self.ion_q))
+                            self.L, self.m0_only, self.self_image, 0, _p(self.ion_q),
+                            0 if self.ion_q is None else len(self.ion_q), _p(self.charge),
+                            _p(self.mass))
 
     def run(self) -> _RunParams:
         return _RunParams(self.field(), self.dt, self.drive_kind, self.wall_rule, self.v_hat,

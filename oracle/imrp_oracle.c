@@ -71,7 +71,16 @@ typedef struct {
    * r, outside [1, r_out] constant. NULL: the uniform background n_ion. */
   const double *ion_q;
   int64_t ion_n;
+  /* Mobile ions as particles (the paper moves its ions, Sec. 4): charge[i]
+   * in e and mass[i] in m_e of particle i in the order of the arrays passed
+   * with these parameters; NULL: every particle is an electron (q = -1,
+   * m = 1). Electron-neutral collisions act on negative particles only. */
+  const double *charge;
+  const double *mass;
 } orc_field_params;
+
+static inline double orc_q(const orc_field_params *p, int64_t i) { return p->charge ? p->charge[i] : -1.0; }
+static inline double orc_m(const orc_field_params *p, int64_t i) { return p->mass ? p->mass[i] : 1.0; }
 
 typedef struct {
   orc_field_params fp;
@@ -240,7 +249,7 @@ double orc_psi_anti(int L, double d, double eps, const double *x) {
   return orc_psi_anti_dual(L, canti, X, Y, Z).v;
 }
 
-/* Q_diff = -(1/n~) sum_i q_i Psi_anti,L(x_i), q_i = -1 (Sec. 4). */
+/* Q_diff = -(1/n~) sum_i q_i Psi_anti,L(x_i) (Sec. 4). */
 double orc_qdiff(const orc_field_params *p, int64_t n, const double *x) {
   double canti[p->L + 1];
   orc_coeffs(p->L, p->d, p->eps, NULL, NULL, NULL, NULL, NULL, canti);
@@ -248,9 +257,9 @@ double orc_qdiff(const orc_field_params *p, int64_t n, const double *x) {
   for (int64_t i = 0; i < n; ++i) {
     dual X, Y, Z;
     orc_point(x + 3 * i, &X, &Y, &Z);
-    s += orc_psi_anti_dual(p->L, canti, X, Y, Z).v;
+    s += orc_q(p, i) * orc_psi_anti_dual(p->L, canti, X, Y, Z).v;
   }
-  return s / p->n_tilde; /* -(1/n~) * (-1) * sum Psi */
+  return -s / p->n_tilde;
 }
 
 /* Ion charge inside radius r in super-particle charges: the uniform
@@ -381,11 +390,13 @@ void orc_field_brute(const orc_field_params *p, int64_t n, const double *x, cons
       const double *xi = x + 3 * i;
       double ri = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
       dual s = orc_pair_kernel(p, f, X, Y, Z, xi, orc_inner(ri, id[i], rk, id[k]), 1);
-      for (int c = 0; c < 3; ++c) g[c] += -1.0 * s.d[c]; /* q_i = -1 */
+      const double qi = orc_q(p, i);
+      for (int c = 0; c < 3; ++c) g[c] += qi * s.d[c];
     }
     if (p->self_image) {
       dual s = orc_pair_kernel(p, f, X, Y, Z, xk, 0, 0);
-      for (int c = 0; c < 3; ++c) g[c] += -1.0 * s.d[c];
+      const double qk = orc_q(p, k);
+      for (int c = 0; c < 3; ++c) g[c] += qk * s.d[c];
     }
     double *Ek = E + 3 * a;
     for (int c = 0; c < 3; ++c) Ek[c] = -g[c] / (4.0 * ORC_PI * p->n_tilde);
@@ -510,12 +521,13 @@ void orc_field_scan(const orc_field_params *p, int64_t n, const double *x, const
     orc_point(xi, &X, &Y, &Z);
     orc_solid(L, X, Y, Z, Mh, Nh);
     double ri = ord[j].r;
+    const double qj = orc_q(p, ord[j].idx);
     for (int l = 0; l <= L; ++l) {
       double sc = pow(ri, -(2 * l + 1));
       for (int m = 0; m <= l; ++m) {
         int q = l * (l + 1) / 2 + m;
-        Wn[q].re -= Nh[q].re.v; Wn[q].im -= Nh[q].im.v;
-        Wim[q].re -= Mh[q].re.v * sc; Wim[q].im -= Mh[q].im.v * sc;
+        Wn[q].re += qj * Nh[q].re.v; Wn[q].im += qj * Nh[q].im.v;
+        Wim[q].re += qj * Mh[q].re.v * sc; Wim[q].im += qj * Mh[q].im.v * sc;
       }
     }
   }
@@ -527,10 +539,11 @@ void orc_field_scan(const orc_field_params *p, int64_t n, const double *x, const
     dual X, Y, Z;
     orc_point(xk, &X, &Y, &Z);
     orc_solid(L, X, Y, Z, Mh, Nh);
+    const double qk = orc_q(p, k);
     /* suffix over outer particles = total - inclusive prefix */
     for (int q = 0; q < nt; ++q) {
-      B[q].re = Wn[q].re - Pn[q].re + Nh[q].re.v;
-      B[q].im = Wn[q].im - Pn[q].im + Nh[q].im.v;
+      B[q].re = Wn[q].re - Pn[q].re - qk * Nh[q].re.v;
+      B[q].im = Wn[q].im - Pn[q].im - qk * Nh[q].im.v;
     }
     /* image moments without particle k unless it feels its own image */
     for (int l = 0; l <= L; ++l) {
@@ -538,7 +551,7 @@ void orc_field_scan(const orc_field_params *p, int64_t n, const double *x, const
       for (int m = 0; m <= l; ++m) {
         int q = l * (l + 1) / 2 + m;
         Wk[q] = Wim[q];
-        if (!p->self_image) { Wk[q].re += Mh[q].re.v * sc; Wk[q].im += Mh[q].im.v * sc; }
+        if (!p->self_image) { Wk[q].re -= qk * Mh[q].re.v * sc; Wk[q].im -= qk * Mh[q].im.v * sc; }
       }
     }
     /* 4 pi * potential (without the 1/n~) as a function of the field point */
@@ -552,8 +565,8 @@ void orc_field_scan(const orc_field_params *p, int64_t n, const double *x, const
     orc_ion_field(p, xk, Ek);
     orc_external_field(p, canti, u, xk, Ek);
     for (int q = 0; q < nt; ++q) {
-      A[q].re -= Mh[q].re.v; A[q].im -= Mh[q].im.v;
-      Pn[q].re -= Nh[q].re.v; Pn[q].im -= Nh[q].im.v;
+      A[q].re += qk * Mh[q].re.v; A[q].im += qk * Mh[q].im.v;
+      Pn[q].re += qk * Nh[q].re.v; Pn[q].im += qk * Nh[q].im.v;
     }
   }
   free(A); free(Pn); free(Wn); free(Wim); free(B); free(Wk); free(Mh); free(Nh); free(ord);
@@ -574,7 +587,8 @@ double orc_energy(const orc_field_params *p, int64_t n, const double *x, const d
   double kin = 0.0, pot = 0.0, ext = 0.0;
   for (int64_t k = 0; k < n; ++k) {
     const double *xk = x + 3 * k, *vk = v + 3 * k;
-    kin += 0.5 * (vk[0] * vk[0] + vk[1] * vk[1] + vk[2] * vk[2]);
+    const double qk = orc_q(p, k);
+    kin += 0.5 * orc_m(p, k) * (vk[0] * vk[0] + vk[1] * vk[1] + vk[2] * vk[2]);
     double rk = sqrt(xk[0] * xk[0] + xk[1] * xk[1] + xk[2] * xk[2]);
     dual X, Y, Z;
     orc_point(xk, &X, &Y, &Z);
@@ -582,14 +596,14 @@ double orc_energy(const orc_field_params *p, int64_t n, const double *x, const d
       const double *xi = x + 3 * i;
       double ri = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
       dual s = orc_pair_kernel(p, f, X, Y, Z, xi, orc_inner(ri, id[i], rk, id[k]), 1);
-      pot += s.v / (4.0 * ORC_PI * p->n_tilde); /* q_k q_i = 1 */
+      pot += qk * orc_q(p, i) * s.v / (4.0 * ORC_PI * p->n_tilde);
     }
     if (p->self_image) {
       dual s = orc_pair_kernel(p, f, X, Y, Z, xk, 0, 0);
-      pot += 0.5 * s.v / (4.0 * ORC_PI * p->n_tilde);
+      pot += 0.5 * qk * qk * s.v / (4.0 * ORC_PI * p->n_tilde);
     }
-    ext += -1.0 * (orc_ion_potential(p, rk) + p->q_s / (4.0 * ORC_PI * p->n_tilde * rk));
-    if (u != 0.0) ext += -1.0 * u * orc_psi_anti_dual(L, canti, X, Y, Z).v;
+    ext += qk * (orc_ion_potential(p, rk) + p->q_s / (4.0 * ORC_PI * p->n_tilde * rk));
+    if (u != 0.0) ext += qk * u * orc_psi_anti_dual(L, canti, X, Y, Z).v;
   }
   return kin + pot + ext;
 }
@@ -739,10 +753,11 @@ int64_t orc_run(const orc_run_params *rp, int64_t n, double *x, double *v, const
     if (uasy) uasy[s] = u;
     double kick = (s == 0 && first_half_kick) ? 0.5 * rp->dt : rp->dt;
     for (int64_t i = 0; i < n; ++i) {
-      for (int c = 0; c < 3; ++c) v[3 * i + c] += kick * (-1.0) * E[3 * i + c]; /* q/m = -1 */
+      const double qm = orc_q(&rp->fp, i) / orc_m(&rp->fp, i);  /* -1 for electrons */
+      for (int c = 0; c < 3; ++c) v[3 * i + c] += kick * qm * E[3 * i + c];
       for (int c = 0; c < 3; ++c) x[3 * i + c] += rp->dt * v[3 * i + c];
       hits += orc_wall(rp, x + 3 * i, v + 3 * i, id[i], step);
-      orc_collide(rp, thr, v + 3 * i, id[i], step);
+      if (orc_q(&rp->fp, i) < 0.0) orc_collide(rp, thr, v + 3 * i, id[i], step);
     }
   }
   free(E);
