@@ -441,7 +441,8 @@ def main():
     K = (w.l_max + 1) ** 2
     flops_per_launch = float(field_flops_per_particle(w.l_max)) * N  # recounted model, times N
     achieved = flops_per_launch / (field_ms / 1e3) / 1e12
-    achieved_24k = 24.0 * K * N / (field_ms / 1e3) / 1e12  # the 24 K flops model of the survey
+    # coarse per-particle model: 24 K flops (harmonics, scans, three contractions), K = (L+1)^2
+    achieved_24k = 24.0 * K * N / (field_ms / 1e3) / 1e12
     sm_mhz = clocks["sm_mhz"] or 2070.0
     peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
     traffic = None
