@@ -340,6 +340,11 @@ int imrp_batch_destroy(imrp_batch* b);
 /* Issues the batch's work on a caller-owned cudaStream_t (NULL: its own). */
 int imrp_batch_set_stream(imrp_batch* b, void* cuda_stream);
 const char* imrp_batch_last_error(const imrp_batch* b);
+/* Index (in the ctxs of imrp_batch_create) of the context whose error the
+ * last imrp_batch_step or imrp_batch_sync returned, or -1 (no error, or one
+ * of the batch itself). imrp_batch_sync reports the first failing context
+ * and clears its flags; other contexts keep theirs for imrp_sync. */
+int imrp_batch_failed(const imrp_batch* b);
 
 /* ---------------------------------------------------------------------------
  * Field evaluation without any allocation. (The paper has no counterpart: this

@@ -963,6 +963,7 @@ struct imrp_batch {
   std::vector<const double*> hist_at_capture;
   std::vector<uint64_t> gen_at_capture;
   std::string err;
+  int failed = -1;  // index of the context whose error the last call returned
 };
 
 extern "C" int imrp_batch_create(imrp_ctx* const* ctxs, int n, imrp_batch** out) {
@@ -1010,9 +1011,14 @@ extern "C" const char* imrp_batch_last_error(const imrp_batch* b) { return b ? b
 namespace {
 int batch_fail(imrp_batch* b, imrp_ctx* ctx, int rc) {
   b->err = ctx ? ctx->err : std::string("batch error");
+  b->failed = -1;
+  for (size_t i = 0; ctx && i < b->c.size(); ++i)
+    if (b->c[i] == ctx) b->failed = int(i);
   return rc;
 }
 }  // namespace
+
+extern "C" int imrp_batch_failed(const imrp_batch* b) { return b ? b->failed : -1; }
 
 extern "C" int imrp_batch_set_stream(imrp_batch* b, void* stream) {
   if (!b) return IMRP_E_INVAL;
@@ -1024,6 +1030,7 @@ extern "C" int imrp_batch_set_stream(imrp_batch* b, void* stream) {
 
 extern "C" int imrp_batch_step(imrp_batch* b, int64_t n_steps) {
   if (!b) return IMRP_E_INVAL;
+  b->failed = -1;
   if (n_steps < 0) return IMRP_E_INVAL;
   if (n_steps == 0) return IMRP_OK;
   const int n = int(b->c.size());
@@ -1099,6 +1106,7 @@ extern "C" int imrp_batch_step(imrp_batch* b, int64_t n_steps) {
 
 extern "C" int imrp_batch_sync(imrp_batch* b) {
   if (!b) return IMRP_E_INVAL;
+  b->failed = -1;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) { b->err = "sync"; return IMRP_E_CUDA; }
   for (imrp_ctx* ctx : b->c) {
     int rc = check_err(ctx);

@@ -24,7 +24,7 @@ EXPORTS = [
     "imrp_batch_destroy", "imrp_batch_last_error", "imrp_batch_set_stream", "imrp_footprint",
     "imrp_load_particles_async", "imrp_copy_qdiff_async", "imrp_drude_fit", "imrp_drude_k",
     "imrp_drude_te", "imrp_admittance", "imrp_fit_damped_sine", "imrp_sheath_solve",
-    "imrp_set_ion_profile", "imrp_checkpoint", "imrp_restore",
+    "imrp_set_ion_profile", "imrp_checkpoint", "imrp_restore", "imrp_batch_failed",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -99,6 +99,7 @@ def load_library(path: str = LIB_PATH):
     L.imrp_batch_set_stream.argtypes = [c_void_p, c_void_p]
     L.imrp_footprint.argtypes = [P(Params), ctypes.c_int64, P(ctypes.c_size_t)]
     L.imrp_batch_last_error.argtypes = [c_void_p]
+    L.imrp_batch_failed.argtypes = [c_void_p]
     L.imrp_batch_last_error.restype = ctypes.c_char_p
     L.imrp_field_noalloc.argtypes = [P(Params), c_void_p, ctypes.c_int64, ctypes.c_int64, c_void_p, c_void_p]
     L.imrp_admittance.argtypes = [pd, pd, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
@@ -253,6 +254,10 @@ class Batch:
 
     def sync(self):
         self._check(self._lib.imrp_batch_sync(self._h))
+
+    def failed_index(self) -> int:
+        """imrp_batch_failed: index of the sim whose error the last call raised, or -1."""
+        return int(self._lib.imrp_batch_failed(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

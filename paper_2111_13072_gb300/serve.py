@@ -13,7 +13,10 @@ steps. The server
   arrive while others run join at the next chunk and their work overlaps on the
   GPU;
 * finishes a request when its steps are done: the spectrum is computed on the
-  GPU (imrp_spectrum), the context is freed and its memory returns to the pool.
+  GPU (imrp_spectrum), the context is freed and its memory returns to the pool;
+* evicts a request whose context reports an error (a non-finite state, a
+  particle outside the domain): its result carries the error, its memory
+  returns to the pool, and the others keep running.
 
 A request's result does not depend on what else is in the mix: batched steps
 compute bit for bit what the request's steps compute alone.
@@ -53,6 +56,7 @@ class SpectrumResult:
     arrival: float
     admitted: float
     finished: float
+    error: str | None = None      # set when the request was evicted
 
     @property
     def latency(self) -> float:
@@ -70,30 +74,53 @@ class _Slot:
 
 class SpectrumServer:
     def __init__(self, hbm_budget: int | None = None, chunk: int = 200, max_slots: int = 64,
-                 autotune: bool = False):
-        import torch
+                 autotune: bool = False, backend=None, state_fn=None):
+        """backend: the module with Sim, Batch, footprint, params_from_workload
+        and IMRPError (the library binding by default; tests pass a fake);
+        state_fn: workload -> (x, v) initial state."""
+        self.lib = imrp if backend is None else backend
+        self.state_fn = workload_state if state_fn is None else state_fn
         if hbm_budget is None:
+            import torch
             free, _ = torch.cuda.mem_get_info()
             hbm_budget = int(0.8 * free)
         self.budget = hbm_budget
         self.chunk = chunk
         self.max_slots = max_slots
         self.autotune = autotune
-        self.stats = {"chunks": 0, "max_active": 0, "peak_bytes": 0}
+        self.stats = {"chunks": 0, "max_active": 0, "peak_bytes": 0, "evicted": 0}
 
     def _admit(self, req: SpectrumRequest, now: float) -> _Slot:
-        p = imrp.params_from_workload(req.workload)
-        sim = imrp.Sim(p)
-        x, v = workload_state(req.workload)
+        p = self.lib.params_from_workload(req.workload)
+        sim = self.lib.Sim(p)
+        x, v = self.state_fn(req.workload)
         sim.load(x, v)
         if self.autotune:
             sim.autotune()
-        return _Slot(req, sim, req.steps, imrp.footprint(p, req.steps), now)
+        return _Slot(req, sim, req.steps, self.lib.footprint(p, req.steps), now)
+
+    def _failed_slots(self, batch, ids, err) -> list[tuple[int, str]]:
+        """The requests whose contexts failed in the last chunk: the one the
+        batch reported (its flags are cleared by the report) and any other
+        whose own check still fails."""
+        k = batch.failed_index()
+        if k < 0:
+            raise err  # an error of the batch itself: not one request's
+        out = [(ids[k], str(err))]
+        for i, rid in enumerate(ids):
+            if i == k:
+                continue
+            try:
+                self._active[rid].sim.sync()
+            except self.lib.IMRPError as e:
+                out.append((rid, str(e)))
+        return out
 
     def serve(self, requests: list[SpectrumRequest], realtime: bool = True) -> list[SpectrumResult]:
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         waiting: collections.deque[SpectrumRequest] = collections.deque()
         active: dict[int, _Slot] = {}
+        self._active = active
         results: list[SpectrumResult] = []
         used = 0
         batch, batch_ids = None, None
@@ -107,7 +134,7 @@ class SpectrumServer:
             # admission: FIFO, as long as a slot and the memory budget allow
             while waiting and len(active) < self.max_slots:
                 req = waiting[0]
-                need = imrp.footprint(imrp.params_from_workload(req.workload), req.steps)
+                need = self.lib.footprint(self.lib.params_from_workload(req.workload), req.steps)
                 if used + need > self.budget and active:
                     break
                 waiting.popleft()
@@ -127,17 +154,29 @@ class SpectrumServer:
             if ids != batch_ids:
                 if batch is not None:
                     batch.close()
-                batch = imrp.Batch([active[i].sim for i in ids])
+                batch = self.lib.Batch([active[i].sim for i in ids])
                 batch_ids = ids
             n = min(self.chunk, min(s.remaining for s in active.values()))
             tc = time.perf_counter()
-            batch.step(n)
-            batch.sync()
+            batch.step(n)  # a launch error is not one request's: it propagates
+            try:
+                batch.sync()
+                failed = []
+            except self.lib.IMRPError as e:
+                failed = self._failed_slots(batch, ids, e)
             self.stats["chunks"] += 1
             if not realtime:
                 vtime += time.perf_counter() - tc
             now = clock() if realtime else vtime
-            for rid in list(ids):
+            for rid, msg in failed:
+                s = active.pop(rid)
+                nan = float("nan")
+                results.append(SpectrumResult(rid, nan, nan, np.full(4, nan), np.zeros(0), np.zeros(0),
+                                              np.zeros(0), s.req.arrival, s.admitted, now, error=msg))
+                s.sim.close()
+                used -= s.footprint
+                self.stats["evicted"] += 1
+            for rid in [r for r in ids if r in active]:
                 s = active[rid]
                 s.remaining -= n
                 if s.remaining == 0:
