@@ -60,7 +60,8 @@ class _FieldParams(ctypes.Structure):
 class _RunParams(ctypes.Structure):
     _fields_ = [("fp", _FieldParams), ("dt", ctypes.c_double), ("drive_kind", ctypes.c_int32),
                 ("wall_rule", ctypes.c_int32), ("v_hat", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("t0", ctypes.c_double), ("seed", ctypes.c_uint64), ("nu_coll", ctypes.c_double)]
+                ("t0", ctypes.c_double), ("seed", ctypes.c_uint64), ("nu_coll", ctypes.c_double),
+                ("sigma_v", ctypes.c_double)]
 
 
 _lib = None
@@ -86,7 +87,8 @@ def lib():
         _lib.orc_philox4x32_10.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
         _lib.orc_drive.argtypes = [P(_RunParams), i64]
         _lib.orc_drive.restype = d
-        _lib.orc_run.argtypes = [P(_RunParams), i64, pd, pd, pi64, i64, i64, i32, i32, pd, pd]
+        _lib.orc_run.argtypes = [P(_RunParams), i64, pd, pd, pi64, i64, i64, i32, i32, pd, pd, pd, pi64]
+        _lib.orc_inject_many.argtypes = [P(_RunParams), i64, pd, pd, pi64, i64]
         _lib.orc_collisions.argtypes = [P(_RunParams), i64, pd, pi64, i64]
         _lib.orc_collisions.restype = i64
         _lib.orc_coll_threshold.argtypes = [ctypes.c_double, ctypes.c_double]
@@ -119,6 +121,7 @@ class Params:
     t0: float = 8.0
     seed: int = 0
     nu_coll: float = 0.0
+    sigma_v: float = 0.0  # thermal speed of the plasma that wall_rule 2 injects from
     # immobile ions of a radial profile (App. D): ion charge inside
     # r_k = 1 + k (r_out - 1)/(len - 1) in super-particle charges; None: uniform n_ion
     ion_q: np.ndarray = None
@@ -141,7 +144,7 @@ class Params:
 
     def run(self) -> _RunParams:
         return _RunParams(self.field(), self.dt, self.drive_kind, self.wall_rule, self.v_hat,
-                          self.sigma, self.t0, self.seed, self.nu_coll)
+                          self.sigma, self.t0, self.seed, self.nu_coll, self.sigma_v)
 
 
 def from_physical(R_E_m, R_D_m, eps_D, R_out_m, n_e_m3, T_e_eV, N, l_max, dt, drive_kind=0,
@@ -153,6 +156,8 @@ def from_physical(R_E_m, R_D_m, eps_D, R_out_m, n_e_m3, T_e_eV, N, l_max, dt, dr
     n~ = N / V_shell is the expected number of super-particles per unit cube
     at density n_inf (Sec. 4). The ion background is uniform and holds N ion
     super-particles (a neutral shell). A voltage V becomes V eps0/(n e R^2).
+    The plasma that wall_rule 2 injects has the thermal speed lambda_D omega_pe,
+    i.e. lambda_D / R in these units.
     """
     R = R_D_m
     d = 1.0 - R_E_m / R_D_m
@@ -163,7 +168,8 @@ def from_physical(R_E_m, R_D_m, eps_D, R_out_m, n_e_m3, T_e_eV, N, l_max, dt, dr
     t0 = 4.0 * width_wpe if t0_wpe is None else t0_wpe
     return Params(d=d, eps=eps_D, r_out=r_out, n_tilde=n_tilde, n_ion=float(N), L=l_max, dt=dt,
                   drive_kind=drive_kind, v_hat=v_hat, sigma=width_wpe, t0=t0, wall_rule=wall_rule,
-                  self_image=self_image, m0_only=m0_only, seed=seed, nu_coll=nu_coll)
+                  self_image=self_image, m0_only=m0_only, seed=seed, nu_coll=nu_coll,
+                  sigma_v=float(debye_length(n_e_m3, T_e_eV) / R))
 
 
 def debye_length(n_e_m3, T_e_eV):
@@ -269,8 +275,11 @@ def drive(p: Params, step):
     return lib().orc_drive(ctypes.byref(rp), step)
 
 
-def run(p: Params, x, v, nsteps, step0=0, first_half_kick=True, evaluator="scan", ids=None):
-    """Leapfrog run; returns (x, v, qdiff[nsteps], uasy[nsteps], wall_hits).
+def run(p: Params, x, v, nsteps, step0=0, first_half_kick=True, evaluator="scan", ids=None,
+        surface=False):
+    """Leapfrog run; returns (x, v, qdiff[nsteps], uasy[nsteps], wall_hits), and
+    with surface=True also Q_S after the last step and the number of probe
+    absorptions (wall_rule 2 accrues the absorbed charge into Q_S).
 
     v on input is synchronous with x when first_half_kick, else the half-step
     velocity; on output it is the half-step velocity v_{n+1/2}.
@@ -282,9 +291,25 @@ def run(p: Params, x, v, nsteps, step0=0, first_half_kick=True, evaluator="scan"
     q = np.zeros(nsteps)
     u = np.zeros(nsteps)
     rp = p.run()
+    qs = np.zeros(1)
+    nab = np.zeros(1, dtype=np.int64)
     hits = lib().orc_run(ctypes.byref(rp), n, _p(x), _p(v), _p(ids, ctypes.c_int64), step0, nsteps,
-                         int(first_half_kick), 0 if evaluator == "brute" else 1, _p(q), _p(u))
+                         int(first_half_kick), 0 if evaluator == "brute" else 1, _p(q), _p(u),
+                         _p(qs), _p(nab, ctypes.c_int64))
+    if surface:
+        return x, v, q, u, hits, float(qs[0]), int(nab[0])
     return x, v, q, u, hits
+
+
+def inject(p: Params, ids, step):
+    """The re-injection of wall_rule 2 alone for the given particle ids at a
+    step: returns (x [n,3], v [n,3])."""
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    x = np.zeros((ids.size, 3))
+    v = np.zeros((ids.size, 3))
+    rp = p.run()
+    lib().orc_inject_many(ctypes.byref(rp), ids.size, _p(x), _p(v), _p(ids, ctypes.c_int64), step)
+    return x, v
 
 
 # ---------------------------------------------------------------- spectrum

@@ -32,7 +32,10 @@
  *   push ............ leapfrog (kick-drift-kick with merged kicks) of the
  *                     canonical equations (Sec. 2).
  *   walls ........... diffuse reflection: same speed, random direction, at the
- *                     probe surface r = 1 and at the outer wall (Sec. 4).
+ *                     probe surface r = 1 and at the outer wall (Sec. 4); or
+ *                     absorption (the probe's surface charge Q_S takes the
+ *                     charge, Sec. 2) with re-injection at the outer wall from
+ *                     a flux-weighted Maxwellian.
  *
  * Two field evaluators:
  *   (a) orc_field_brute: the definition, a direct sum over all pairs with
@@ -86,12 +89,15 @@ typedef struct {
   orc_field_params fp;
   double dt;       /* time step                                          */
   int32_t drive_kind; /* 0 Gaussian pulse, 1 impulse at step 0, 2 off   */
-  int32_t wall_rule;  /* 0 diffuse reflection, 1 specular reflection    */
+  int32_t wall_rule;  /* 0 diffuse reflection, 1 specular reflection,
+                         2 absorb (probe: charge to Q_S) and re-inject at r_out */
   double v_hat;    /* drive amplitude (dimensionless voltage)            */
   double sigma;    /* Gaussian pulse width                               */
   double t0;       /* Gaussian pulse centre                              */
   uint64_t seed;   /* wall random-number key                             */
   double nu_coll;  /* electron-neutral collision rate nu (units of omega_pe), 0: none */
+  double sigma_v;  /* thermal speed lambda_D omega_pe (units of R omega_pe) of the plasma
+                      that wall_rule 2 injects from                                 */
 } orc_run_params;
 
 /* ------------------------------------------------------------------ */
@@ -635,8 +641,63 @@ void orc_philox4x32_10(const uint32_t *ctr_in, const uint32_t *key_in, uint32_t 
 /* The tangent frame is the branchless orthonormal basis of Duff et    */
 /* al., "Building an orthonormal basis, revisited", JCGT 2017.         */
 /* Specular: the radial velocity component changes sign.               */
-/* Returns 1 when the particle hit a wall.                             */
 /* ------------------------------------------------------------------ */
+
+/* Tangent frame (t1, t2) of the unit vector n (Duff et al. 2017). */
+static void orc_onb(const double *n, double *t1, double *t2) {
+  double s = n[2] >= 0.0 ? 1.0 : -1.0;
+  double a = -1.0 / (s + n[2]);
+  double b = n[0] * n[1] * a;
+  t1[0] = 1.0 + s * n[0] * n[0] * a; t1[1] = s * b; t1[2] = -s * n[0];
+  t2[0] = b; t2[1] = s + n[1] * n[1] * a; t2[2] = -n[1];
+}
+
+/* Uniform in (0, 1) from the top 24 bits of a Philox word (never 0 or 1). */
+static double orc_u24(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+/* Absorb and re-inject (wall_rule 2; north_star names "absorbs or re-injects",
+ * and the paper's floating probe collects the electrons that reach it: its
+ * surface charge Q_S is homogeneous on S, Sec. 2). The particle that left is
+ * replaced, under the same id, by one entering through the outer wall from
+ * the bulk plasma: a flux-weighted Maxwellian of thermal speed sigma_v. Six
+ * uniforms from two Philox blocks, counter (step, step>>32, id, 0x494E4A30 and
+ * 0x494E4A31), key (seed):
+ *   u1, u2: the entry point r_out n, n isotropic (cos = 1 - 2 u1, phi = 2 pi u2);
+ *   u3: inward normal speed v_n = sigma_v sqrt(-2 ln u3) (the density of the
+ *       normal speeds that cross a surface, v_n exp(-v_n^2 / (2 sigma_v^2)));
+ *   u4, u5: the two tangential components, normal with deviation sigma_v
+ *       (Box-Muller: rho = sigma_v sqrt(-2 ln u4), angle 2 pi u5);
+ *   u6: the fraction of the step since it crossed, so it sits at radius
+ *       r_out - u6 dt v_n (at least 1), on the ray of n.
+ * The velocity is -v_n n + vt1 t1 + vt2 t2 with (t1, t2) the frame of n. */
+static void orc_inject(const orc_run_params *rp, double *x, double *v, int64_t pid, int64_t step) {
+  uint32_t ctr[4] = {(uint32_t)(uint64_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)pid,
+                     0x494E4A30u};
+  uint32_t key[2] = {(uint32_t)rp->seed, (uint32_t)(rp->seed >> 32)};
+  uint32_t a[4], b[4];
+  orc_philox4x32_10(ctr, key, a);
+  ctr[3] = 0x494E4A31u;
+  orc_philox4x32_10(ctr, key, b);
+  double u1 = orc_u24(a[0]), u2 = orc_u24(a[1]), u3 = orc_u24(a[2]), u4 = orc_u24(a[3]);
+  double u5 = orc_u24(b[0]), u6 = orc_u24(b[1]);
+  double ct = 1.0 - 2.0 * u1, st = sqrt(1.0 - ct * ct), ph = 2.0 * ORC_PI * u2;
+  double n[3] = {st * cos(ph), st * sin(ph), ct};
+  double vn = rp->sigma_v * sqrt(-2.0 * log(u3));
+  double rho = rp->sigma_v * sqrt(-2.0 * log(u4)), ps = 2.0 * ORC_PI * u5;
+  double vt1 = rho * cos(ps), vt2 = rho * sin(ps);
+  double t1[3], t2[3];
+  orc_onb(n, t1, t2);
+  double r = rp->fp.r_out - u6 * rp->dt * vn;
+  if (r < 1.0) r = 1.0;
+  for (int c = 0; c < 3; ++c) {
+    x[c] = r * n[c];
+    v[c] = -vn * n[c] + vt1 * t1[c] + vt2 * t2[c];
+  }
+}
+
+/* The wall rule on one particle after its drift. Returns 0 (inside),
+ * 1 (reflected), 2 (absorbed at the probe and re-injected), 3 (left through
+ * the outer wall and re-injected). */
 static int orc_wall(const orc_run_params *rp, double *x, double *v, int64_t pid, int64_t step) {
   double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
   double r_out = rp->fp.r_out;
@@ -645,6 +706,10 @@ static int orc_wall(const orc_run_params *rp, double *x, double *v, int64_t pid,
   if (r < 1.0) { sgn = 1.0; rn = 2.0 - r; }
   else if (r > r_out) { sgn = -1.0; rn = 2.0 * r_out - r; }
   else return 0;
+  if (rp->wall_rule == 2) {
+    orc_inject(rp, x, v, pid, step);
+    return sgn > 0.0 ? 2 : 3;
+  }
   if (rn < 1.0) rn = 1.0;
   if (rn > r_out) rn = r_out;
   double e[3] = {x[0] / r, x[1] / r, x[2] / r};
@@ -666,14 +731,17 @@ static int orc_wall(const orc_run_params *rp, double *x, double *v, int64_t pid,
   double ca = 1.0 - u1;                 /* cos of the angle to the normal, (0,1] */
   double sa = sqrt(1.0 - ca * ca);
   double ph = 2.0 * ORC_PI * u2;
-  double s = nrm[2] >= 0.0 ? 1.0 : -1.0;
-  double a = -1.0 / (s + nrm[2]);
-  double b = nrm[0] * nrm[1] * a;
-  double t1[3] = {1.0 + s * nrm[0] * nrm[0] * a, s * b, -s * nrm[0]};
-  double t2[3] = {b, s + nrm[1] * nrm[1] * a, -nrm[1]};
+  double t1[3], t2[3];
+  orc_onb(nrm, t1, t2);
   double cp = cos(ph), sp = sin(ph);
   for (int c = 0; c < 3; ++c) v[c] = speed * (ca * nrm[c] + sa * (cp * t1[c] + sp * t2[c]));
   return 1;
+}
+
+/* The injection alone for n particle ids at a step (for pins): x, v [n][3]. */
+void orc_inject_many(const orc_run_params *rp, int64_t n, double *x, double *v, const int64_t *id,
+                     int64_t step) {
+  for (int64_t i = 0; i < n; ++i) orc_inject(rp, x + 3 * i, v + 3 * i, id[i], step);
 }
 
 /* Electron-neutral collisions (Sec. 5 names them as the next addition; the  */
@@ -737,29 +805,40 @@ double orc_drive(const orc_run_params *rp, int64_t step) {
  * first_half_kick = 1 (velocities synchronous with x, so the first kick is
  * dt/2). evaluator: 0 brute force, 1 sorted scan. qdiff[s] and uasy[s]
  * receive Q_diff and u_asy at the positions used by step s (either may be
- * NULL). Returns the number of wall hits. */
+ * NULL). With wall_rule 2 the charge of every particle absorbed at the probe
+ * joins the surface charge Q_S (starting from rp->fp.q_s), which the field of
+ * the following steps feels; q_s_out (may be NULL) receives Q_S after the last
+ * step and absorbed (may be NULL) the number of probe absorptions. Returns the
+ * number of wall hits (reflections, or absorptions at either wall). */
 int64_t orc_run(const orc_run_params *rp, int64_t n, double *x, double *v, const int64_t *id,
                 int64_t step0, int64_t nsteps, int first_half_kick, int evaluator, double *qdiff,
-                double *uasy) {
+                double *uasy, double *q_s_out, int64_t *absorbed) {
   double *E = malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
-  int64_t hits = 0;
+  int64_t hits = 0, nabs = 0;
+  orc_field_params fp = rp->fp; /* its q_s accrues the absorbed charge */
   const uint32_t thr = orc_coll_threshold(rp->nu_coll, rp->dt);
   for (int64_t s = 0; s < nsteps; ++s) {
     int64_t step = step0 + s;
     double u = orc_drive(rp, step);
-    if (evaluator == 0) orc_field_brute(&rp->fp, n, x, id, u, n, NULL, E);
-    else orc_field_scan(&rp->fp, n, x, id, u, E);
-    if (qdiff) qdiff[s] = orc_qdiff(&rp->fp, n, x);
+    if (evaluator == 0) orc_field_brute(&fp, n, x, id, u, n, NULL, E);
+    else orc_field_scan(&fp, n, x, id, u, E);
+    if (qdiff) qdiff[s] = orc_qdiff(&fp, n, x);
     if (uasy) uasy[s] = u;
     double kick = (s == 0 && first_half_kick) ? 0.5 * rp->dt : rp->dt;
+    double dq = 0.0;
     for (int64_t i = 0; i < n; ++i) {
-      const double qm = orc_q(&rp->fp, i) / orc_m(&rp->fp, i);  /* -1 for electrons */
+      const double qm = orc_q(&fp, i) / orc_m(&fp, i);  /* -1 for electrons */
       for (int c = 0; c < 3; ++c) v[3 * i + c] += kick * qm * E[3 * i + c];
       for (int c = 0; c < 3; ++c) x[3 * i + c] += rp->dt * v[3 * i + c];
-      hits += orc_wall(rp, x + 3 * i, v + 3 * i, id[i], step);
-      if (orc_q(&rp->fp, i) < 0.0) orc_collide(rp, thr, v + 3 * i, id[i], step);
+      int w = orc_wall(rp, x + 3 * i, v + 3 * i, id[i], step);
+      hits += w != 0;
+      if (w == 2) { dq += orc_q(&fp, i); ++nabs; }
+      if (orc_q(&fp, i) < 0.0) orc_collide(rp, thr, v + 3 * i, id[i], step);
     }
+    fp.q_s += dq;
   }
+  if (q_s_out) *q_s_out = fp.q_s;
+  if (absorbed) *absorbed = nabs;
   free(E);
   return hits;
 }
