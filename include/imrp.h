@@ -50,14 +50,23 @@ typedef struct imrp_params {
   double eps_D;      /* relative permittivity eps_r of the shell (App. A)         */
   double R_out_m;    /* radius of the outer particle wall [m] (Sec. 4)            */
   double n_e_m3;     /* electron density n_inf [m^-3] (Sec. 4 units)              */
-  double T_e_eV;     /* electron temperature [eV]; informational (the field does not use it) */
+  double T_e_eV;     /* electron temperature [eV]: the thermal speed lambda_D omega_pe of the
+                        plasma that wall_rule 2 injects (the field does not use it) */
   int64_t N;         /* capacity: maximum number of super-particles               */
   int32_t l_max;     /* truncation degree of the projection P^ (Sec. 2/3); one of 1,2,4,8,12,16,24 */
   int32_t m0_only;   /* 0: all (l, m); 1: only the m = 0 terms of each degree -- with
                         l_max = 1 the truncated kernel of Sec. 3 (cos t cos t' dipole) */
   double dt;         /* time step [1/omega_pe]                                    */
   int32_t drive_kind; /* 0 Gaussian pulse, 1 impulse at the first step (Sec. 4), 2 off */
-  int32_t wall_rule;  /* 0 diffuse reflection (Sec. 4), 1 specular reflection      */
+  int32_t wall_rule;  /* 0 diffuse reflection (Sec. 4), 1 specular reflection,
+                         2 absorb and re-inject: an electron that crosses r = R is
+                         absorbed and its charge joins the probe's surface charge
+                         Q_S (homogeneous on the surface, Sec. 2), which the field of
+                         the following steps feels (Sec. 3); one that crosses R_out
+                         leaves; either is replaced, under its id, by an electron
+                         entering through the outer wall from the bulk plasma (a
+                         flux-weighted Maxwellian of thermal speed lambda_D omega_pe,
+                         drawn from Philox keyed by (step, id, seed))            */
   double V_volts;    /* drive amplitude u_asy [V]: peak of the pulse or the impulse */
   double width_wpe;  /* Gaussian pulse standard deviation [1/omega_pe]             */
   double t0_wpe;     /* Gaussian pulse centre [1/omega_pe]; <= 0 selects 4*width   */
@@ -175,6 +184,13 @@ int imrp_get_field(imrp_ctx* ctx, double* E);
  * v_{n-1/2}[n][3] (v synchronous with x right after a load). Either may be NULL. */
 int imrp_get_particles(imrp_ctx* ctx, double* x, double* v);
 
+/* Probe surface charge Q_S (super-particle charges, Sec. 3) and the number of
+ * electrons absorbed at the probe since the load (wall_rule 2; with the other
+ * rules Q_S stays the parameters' value and the count 0). Waits for the queued
+ * work. Either pointer may be NULL. Errors: IMRP_E_STATE (nothing loaded),
+ * IMRP_E_CUDA. */
+int imrp_get_surface_charge(imrp_ctx* ctx, double* q_s, int64_t* n_absorbed);
+
 /* Checkpoint of a run: the state in its storage order (the order of the last
  * push), x[n][3], v[n][3] (the half-step velocity), the particle ids id[n],
  * and *step, the number of steps taken since the load. Host arrays of the
@@ -184,7 +200,9 @@ int imrp_get_particles(imrp_ctx* ctx, double* x, double* v);
  * (a NULL output), IMRP_E_STATE (nothing loaded). */
 int imrp_checkpoint(imrp_ctx* ctx, double* x, double* v, uint32_t* id, int64_t* step);
 
-/* Restores a checkpoint into a context made with the same parameters: the
+/* Restores a checkpoint into a context made with the same parameters (with
+ * wall_rule 2, q_s set to the surface charge that imrp_get_surface_charge
+ * returned at the checkpoint, since the accrual restarts at the restore): the
  * state in the given order with the given ids (a permutation of 0..n-1), the
  * next step is `step`, and the velocities are taken as a half step behind
  * the positions (as imrp_checkpoint returns them) unless step == 0. Q_diff is
@@ -310,6 +328,15 @@ int imrp_get_info(const imrp_ctx* ctx, imrp_info* info);
 #define IMRP_N_STAGES 5
 int imrp_profile_steps(imrp_ctx* ctx, int64_t n_steps, double* ms);
 
+/* Measured FP32 FMA throughput of the current device in TFLOP/s (the roofline
+ * denominator of the field kernel, which is FP32 arithmetic rather than a
+ * tensor-core contraction; the paper has no counterpart): independent FMA
+ * chains on every SM (the SM count is read from the device, *sm_count if not
+ * NULL), best of ten timed launches after a warm-up, at whatever clock the
+ * device runs. Allocates a few bytes and a stream; takes some tens of ms.
+ * Errors: IMRP_E_INVAL (tflops NULL), IMRP_E_NOMEM, IMRP_E_CUDA. */
+int imrp_fp32_peak(double* tflops, int* sm_count);
+
 /* ---------------------------------------------------------------------------
  * Autotuning and batched ensembles (no counterpart in the paper: they serve the
  * ensemble and request-serving workloads built on the same hot path).
@@ -373,10 +400,16 @@ int imrp_batch_failed(const imrp_batch* b);
  *           legacy default stream. The call waits for its own work on that
  *           stream before it returns.
  *
- * The first call on a device performs that device's set-up (it looks up the
- * device address of the static array with cudaGetSymbolAddress and fills the
- * kernels' constant tables), with that device current; make that first call
- * before any stream capture. Every call on a device shares the one array, and
+ * The first call on a device performs that device's set-up, with that device
+ * current: CUDA loads device code lazily, and loading reserves device memory
+ * (the code, its tables and the static array itself), so the set-up loads
+ * every kernel this entry point can launch (both precisions, every degree up
+ * to IMRP_NOALLOC_MAX_L), fills their constant tables and looks up the device
+ * address of the static array with cudaGetSymbolAddress. Make that first call
+ * at start-up, where reserving memory is allowed, and before any stream
+ * capture; later calls load and reserve nothing. The set-up does not survive
+ * a cudaDeviceReset of the device (nor does anything else of this library):
+ * do not call it across one. Every call on a device shares the one array, and
  * the array keeps the last call's contents (what must start at zero is
  * cleared by each call): calls that overlap on the GPU, from two streams or
  * two host threads, race on it and must not be made.

@@ -50,25 +50,6 @@ uint32_t coll_threshold(double nu, double dt) {
   return uint32_t(floor((1.0 - exp(-nu * dt)) * 16777216.0));
 }
 
-// Coefficients of the library (written from App. A and Sec. 3; R = 1).
-double coef_f(int l, double d, double eps) {
-  const double x = pow(1.0 - d, 2 * l + 1);
-  return (l * (eps - 1.0) + (l + eps + l * eps) * x) / ((l + 1 + l * eps) + (l + 1) * (eps - 1.0) * x);
-}
-double coef_bP(int l, double d, double eps) {
-  const double den = (l + 1) * (eps - 1.0) * pow(1.0 - d, 2 * l + 1) + l * eps + l + 1;
-  return (2 * l + 1) * eps * pow(1.0 - d, l + 1) / den;
-}
-// c_l' of Sec. 3 for odd degree l = 2l'-1: (-1/2)^{l'+1} (4l'-1) (2l'-3)!! / l'!
-double coef_cprime(int lp) {
-  double df = 1.0;
-  for (int k = 2 * lp - 3; k > 1; k -= 2) df *= k;
-  double fact = 1.0;
-  for (int k = 2; k <= lp; ++k) fact *= k;
-  double sgn = ((lp + 1) % 2 == 0) ? 1.0 : -1.0;
-  return sgn * pow(0.5, lp + 1) * (4.0 * lp - 1.0) * df / fact;
-}
-
 }  // namespace
 
 struct imrp_ctx {
@@ -306,6 +287,8 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   a.dt = T(ctx->p.dt);
   a.r_out = T(ctx->r_out);
   a.wall_rule = ctx->p.wall_rule;
+  a.nabs = &ctx->st->nabs_step;
+  a.sigma_v = ctx->lambda_D;
   a.self_image = ctx->p.self_image;
   a.m0_only = ctx->p.m0_only;
   a.coll_thr = coll_threshold(ctx->p.nu_coll, ctx->p.dt);
@@ -483,7 +466,7 @@ int imrp_create(const imrp_params* p, imrp_ctx** out) {
   if (p->N < 1 || p->N > (int64_t(1) << 31)) return bad("N");
   if (p->m0_only != 0 && p->m0_only != 1) return bad("m0_only");
   if (p->precision != 0 && p->precision != 1) return bad("precision");
-  if (p->drive_kind < 0 || p->drive_kind > 2 || p->wall_rule < 0 || p->wall_rule > 1) return bad("rules");
+  if (p->drive_kind < 0 || p->drive_kind > 2 || p->wall_rule < 0 || p->wall_rule > 2) return bad("rules");
   if (!(p->nu_coll >= 0.0) || !std::isfinite(p->nu_coll)) return bad("nu_coll");
   if (p->drive_kind == 0 && !(p->width_wpe > 0)) return bad("width");
   ctx->L = p->l_max;
@@ -499,7 +482,7 @@ int imrp_create(const imrp_params* p, imrp_ctx** out) {
   ctx->t0 = p->t0_wpe > 0 ? p->t0_wpe : 4.0 * p->width_wpe;
   for (int l = 0; l < kTabL; ++l) {
     ctx->f[l] = coef_f(l, ctx->d, p->eps_D);
-    ctx->canti[l] = (l % 2 == 1 && l <= ctx->L) ? coef_cprime((l + 1) / 2) * coef_bP(l, ctx->d, p->eps_D) : 0.0;
+    ctx->canti[l] = l <= ctx->L ? coef_canti(l, ctx->d, p->eps_D) : 0.0;
     if (l > ctx->L) ctx->f[l] = 0.0;
   }
   ctx->nc = 2 * ncomp(ctx->L);
@@ -758,6 +741,20 @@ int imrp_get_particles(imrp_ctx* ctx, double* x, double* v) {
   if (x) CK(cudaMemcpyAsync(x, ctx->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   if (v) CK(cudaMemcpyAsync(v, ctx->stage + 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return check_err(ctx);
+}
+
+int imrp_get_surface_charge(imrp_ctx* ctx, double* q_s, int64_t* n_absorbed) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (!ctx->loaded) return ctx->fail(IMRP_E_STATE, "get_surface_charge before load");
+  StepState h{};
+  CK(cudaMemcpyAsync(&h, ctx->st, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = check_err(ctx);
+  if (rc) return rc;
+  // absorptions of the last step are folded in by the next step's finalize
+  const double base = ctx->ion_n ? ctx->ion_qs * ctx->n_tilde : ctx->p.q_s;
+  if (q_s) *q_s = base + h.qs_acc - double(h.nabs_step);
+  if (n_absorbed) *n_absorbed = h.nabs_total + h.nabs_step;
+  return IMRP_OK;
 }
 
 int imrp_checkpoint(imrp_ctx* ctx, double* x, double* v, uint32_t* id, int64_t* step) {

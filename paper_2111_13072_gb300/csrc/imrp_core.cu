@@ -552,6 +552,11 @@ __global__ void k_finalize(FinalizeArgs a) {
   st->step = n;
   st->u = u;
   st->kick = st->sync ? 0.5 * a.dt : a.dt;
+  // electrons absorbed at the probe since the last fold (wall_rule 2) join Q_S
+  // (charge -1 each) before the field of this step is evaluated
+  st->qs_acc -= double(st->nabs_step);
+  st->nabs_total += st->nabs_step;
+  st->nabs_step = 0;
   if (a.record) {
     double q = 0.0;
     for (int l = 1; l <= a.L; l += 2) q += a.canti[l] * a.totd[2 * (l - 1) + 1];
@@ -576,6 +581,9 @@ __global__ void k_init_step(StepState* st) {
   st->u = 0.0;
   st->kick = 0.0;
   st->sync = 1;
+  st->nabs_step = 0;
+  st->qs_acc = 0.0;
+  st->nabs_total = 0;
 }
 
 void launch_init_step(StepState* st, cudaStream_t s) { k_init_step<<<1, 32, 0, s>>>(st); }
@@ -618,6 +626,34 @@ __global__ void k_dft(const double* __restrict__ q, const double* __restrict__ u
 void launch_dft(const double* q, const double* u, int64_t ns, double dt, double first_kick, int64_t nf,
                 double w_max, double* out, cudaStream_t s) {
   k_dft<<<unsigned((nf + 127) / 128), 128, 0, s>>>(q, u, ns, dt, first_kick, nf, w_max, out);
+}
+
+template <class T> cudaError_t preload_core_kernels_t() {
+  cudaFuncAttributes fa;
+  const void* fns[] = {
+      reinterpret_cast<const void*>(&k_reorder<T>),     reinterpret_cast<const void*>(&k_keys<T>),
+      reinterpret_cast<const void*>(&k_load<T>),        reinterpret_cast<const void*>(&k_state_dump<T>),
+      reinterpret_cast<const void*>(&k_scatter_by_id<T>), reinterpret_cast<const void*>(&k_state_out<T>),
+      reinterpret_cast<const void*>(&k_tile_scan<T>),   reinterpret_cast<const void*>(&k_group_sums<T>),
+      reinterpret_cast<const void*>(&k_group_bases<T>)};
+  for (const void* f : fns) {
+    const cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t preload_core_kernels() {
+  cudaFuncAttributes fa;
+  const void* fns[] = {reinterpret_cast<const void*>(&k_sort_hist), reinterpret_cast<const void*>(&k_sort_rowscan),
+                       reinterpret_cast<const void*>(&k_sort_scatter), reinterpret_cast<const void*>(&k_finalize),
+                       reinterpret_cast<const void*>(&k_init_step), reinterpret_cast<const void*>(&k_dft)};
+  for (const void* f : fns) {
+    const cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+  }
+  const cudaError_t e = preload_core_kernels_t<float>();
+  return e != cudaSuccess ? e : preload_core_kernels_t<double>();
 }
 
 // explicit instantiations

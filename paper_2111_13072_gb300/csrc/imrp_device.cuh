@@ -54,7 +54,10 @@ struct StepState {
   double u;         // u_asy(t_step)
   double kick;      // kick weight of this step (dt, or dt/2 right after a load)
   int32_t sync;     // 1: velocities synchronous with x (next kick is dt/2)
-  int32_t pad;
+  int32_t nabs_step;  // electrons absorbed at the probe in the step in progress (wall_rule 2)
+  double qs_acc;      // surface charge they brought since the load (super-particle charges),
+                      // folded in by the finalize kernel before each field evaluation
+  int64_t nabs_total; // electrons absorbed at the probe since the load, as folded
 };
 
 // Device error flags (bitwise or).
@@ -114,6 +117,49 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     k.y += 0xBB67AE85u;
   }
   return c;
+}
+
+// Re-injection of the absorbing wall rule (wall_rule 2): the particle that
+// left is replaced, under the same id, by one entering through the outer wall
+// from the bulk plasma, whose crossing flux is a flux-weighted Maxwellian of
+// thermal speed sigma_v. Six 24-bit uniforms u = (k + 1/2) 2^-24 from two
+// Philox blocks, counter (step, step >> 32, id, 0x494E4A30 / 0x494E4A31), key
+// seed: u1, u2 the isotropic entry direction n (cos = 1 - 2 u1, phi = 2 pi u2);
+// u3 the inward normal speed v_n = sigma_v sqrt(-2 ln u3) (density of the
+// crossing normal speeds v exp(-v^2 / 2 sigma_v^2)); u4, u5 the tangential
+// components by Box-Muller (rho = sigma_v sqrt(-2 ln u4), angle 2 pi u5) in the
+// frame of n of Duff et al.; u6 the fraction of the step since the crossing,
+// so the particle sits at radius r_out - u6 dt v_n (at least 1) on the ray of
+// n. Evaluated in FP64 in both precisions (a few particles per step), so that
+// the FP32 state is the FP64 value rounded once.
+__device__ __forceinline__ double inj_u24(uint32_t w) { return (double(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+__device__ __forceinline__ void inject_particle(uint32_t id, uint64_t step, uint64_t seed, double r_out, double dt,
+                                                double sigma_v, double* x, double* v) {
+  const uint2 key = make_uint2(uint32_t(seed), uint32_t(seed >> 32));
+  const uint4 a = philox4x32_10(make_uint4(uint32_t(step), uint32_t(step >> 32), id, 0x494E4A30u), key);
+  const uint4 b = philox4x32_10(make_uint4(uint32_t(step), uint32_t(step >> 32), id, 0x494E4A31u), key);
+  const double u1 = inj_u24(a.x), u2 = inj_u24(a.y), u3 = inj_u24(a.z), u4 = inj_u24(a.w);
+  const double u5 = inj_u24(b.x), u6 = inj_u24(b.y);
+  const double ct = 1.0 - 2.0 * u1, st = sqrt(1.0 - ct * ct);
+  double sp, cp;
+  sincospi(2.0 * u2, &sp, &cp);
+  const double n0 = st * cp, n1 = st * sp, n2 = ct;
+  const double vn = sigma_v * sqrt(-2.0 * log(u3));
+  const double rho = sigma_v * sqrt(-2.0 * log(u4));
+  double s5, c5;
+  sincospi(2.0 * u5, &s5, &c5);
+  const double vt1 = rho * c5, vt2 = rho * s5;
+  const double sg = n2 >= 0.0 ? 1.0 : -1.0;
+  const double aa = -1.0 / (sg + n2);
+  const double bb = n0 * n1 * aa;
+  const double t10 = 1.0 + sg * n0 * n0 * aa, t11 = sg * bb, t12 = -sg * n0;
+  const double t20 = bb, t21 = sg + n1 * n1 * aa, t22 = -n1;
+  double r = r_out - u6 * dt * vn;
+  r = r < 1.0 ? 1.0 : r;
+  x[0] = r * n0; x[1] = r * n1; x[2] = r * n2;
+  v[0] = -vn * n0 + vt1 * t10 + vt2 * t20;
+  v[1] = -vn * n1 + vt1 * t11 + vt2 * t21;
+  v[2] = -vn * n2 + vt1 * t12 + vt2 * t22;
 }
 
 // Scan groups: one group = 32 tiles (1024 particles), scanned by one warp
@@ -206,12 +252,14 @@ template <class T> struct FieldArgs {
   double ion_inv_h;   // 1 / h
   double ion_scale;   // n~: super-particle charges per e n_inf R^3
   int ion_n;          // nodes of ion_q (>= 2 when ion_q is set)
-  double q_s;         // surface charge
+  double q_s;         // surface charge of the parameters (the absorbed charge st->qs_acc adds to it)
   double r_out2;      // r_out^2
   double kscale;      // 2^32 / (r_out^2 - 1)
   T dt;
   T r_out;
-  int wall_rule;
+  int wall_rule;      // 0 diffuse, 1 specular, 2 absorb (probe charge to Q_S) and re-inject
+  int* nabs;          // wall_rule 2: counter of the step's probe absorptions (&st->nabs_step)
+  double sigma_v;     // thermal speed of the injected plasma (lambda_D / R)
   int self_image;
   int m0_only;        // 1: keep only the m = 0 terms of every degree (the paper's truncation)
   uint32_t coll_thr;  // collision when the top 24 bits of a Philox word are below this (0: none)

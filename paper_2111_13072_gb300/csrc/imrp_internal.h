@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <vector>
@@ -10,6 +11,32 @@
 #include "imrp_device.cuh"
 
 namespace imrp {
+
+// ---- coefficients (host; written from App. A and Sec. 3 with R = 1) ---------
+// f_l of the radial Green's function R^(p,p)_l (App. A).
+inline double coef_f(int l, double d, double eps) {
+  const double x = pow(1.0 - d, 2 * l + 1);
+  return (l * (eps - 1.0) + (l + eps + l * eps) * x) / ((l + 1 + l * eps) + (l + 1) * (eps - 1.0) * x);
+}
+// b^P_l of the characteristic function outside the dielectric (Sec. 3).
+inline double coef_bP(int l, double d, double eps) {
+  const double den = (l + 1) * (eps - 1.0) * pow(1.0 - d, 2 * l + 1) + l * eps + l + 1;
+  return (2 * l + 1) * eps * pow(1.0 - d, l + 1) / den;
+}
+// c_l' of Sec. 3 for odd degree l = 2l'-1: (-1/2)^{l'+1} (4l'-1) (2l'-3)!! / l'!
+inline double coef_cprime(int lp) {
+  double df = 1.0;
+  for (int k = 2 * lp - 3; k > 1; k -= 2) df *= k;
+  double fact = 1.0;
+  for (int k = 2; k <= lp; ++k) fact *= k;
+  const double sgn = ((lp + 1) % 2 == 0) ? 1.0 : -1.0;
+  return sgn * pow(0.5, lp + 1) * (4.0 * lp - 1.0) * df / fact;
+}
+// Coefficient of r^{-(l+1)} P_l(cos t) in Psi_anti for r >= R (Sec. 3): c_l' b^P_l
+// for odd l = 2l'-1, zero for even l.
+inline double coef_canti(int l, double d, double eps) {
+  return (l % 2 == 1) ? coef_cprime((l + 1) / 2) * coef_bP(l, d, eps) : 0.0;
+}
 
 // ---- radix sort (imrp_core.cu) ---------------------------------------------
 constexpr int kSortThreads = 256;
@@ -80,6 +107,11 @@ struct FinalizeArgs {
   double canti[kTabL];
 };
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+// Loads the device code of every degree-independent kernel of both precisions
+// (CUDA loads modules lazily, at a kernel's first launch or query, and the
+// load reserves device memory): the allocation-free entry point calls it at
+// its set-up so that later calls load nothing.
+cudaError_t preload_core_kernels();
 void launch_init_step(StepState* st, cudaStream_t s);
 
 // Spectrum sums: Qh[j] = dt sum_n (q_n - q_0) e^{-i w_j t_n},

@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   const int64_t g = tile / kTilesPerGroup;
   const double u_drive = a.st->u;
   const T kick = T(a.st->kick);
+  const double q_s = a.q_s + a.st->qs_acc;  // with the charge absorbed at the probe so far
   const bool img_in_tile = img_in_tile_for<T>(0) && a.img_in_tile;  // FP32 contexts only
 
   // the particle of this lane, loaded first so that its latency overlaps the
@@ -737,7 +738,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     } else {
       qion = a.ion_coef * (r2d * rd - 1.0);
     }
-    const double qin = qion + (a.q_s - double(j));
+    const double qin = qion + (q_s - double(j));
     const T er = T(qin) * (T(a.pf) * ir2 * ir);  // multiplies x (gives r^ / r^2)
     Ex += er * X; Ey += er * Y; Ez += er * Z;
     const int self_sign = img_in_tile ? (a.self_image ? 1 : 0) : (a.self_image ? 0 : -1);
@@ -797,7 +798,15 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       rr = xd * xd + yd * yd + zd * zd;  // exact for FP32 positions; also the next key
       hit = near_wall && (rr < 1.0 || rr > a.r_out2);
     }
-    if (hit) {
+    if (hit && a.wall_rule == 2) {
+      // absorbed (at the probe its charge joins Q_S) and replaced from the outer wall
+      if (rr < 1.0) atomicAdd(a.nabs, 1);
+      double xn[3], vn[3];
+      inject_particle(a.id[j], uint64_t(a.st->step), a.seed, double(a.r_out), double(a.dt), a.sigma_v, xn, vn);
+      X = T(xn[0]); Y = T(xn[1]); Z = T(xn[2]);
+      VX = T(vn[0]); VY = T(vn[1]); VZ = T(vn[2]);
+      rr = double(X) * double(X) + double(Y) * double(Y) + double(Z) * double(Z);
+    } else if (hit) {
       const double xd = double(X), yd = double(Y), zd = double(Z);
       const double rd = sqrt(rr);
       const bool inner = rr < 1.0;

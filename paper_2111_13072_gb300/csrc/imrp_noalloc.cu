@@ -80,21 +80,6 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kE = 1.602176634e-19;
 constexpr double kEps0 = 8.8541878128e-12;
 
-double f_coef(int l, double d, double eps) {
-  const double x = pow(1.0 - d, 2 * l + 1);
-  return (l * (eps - 1.0) + (l + eps + l * eps) * x) / ((l + 1 + l * eps) + (l + 1) * (eps - 1.0) * x);
-}
-double bp_coef(int l, double d, double eps) {
-  const double den = (l + 1) * (eps - 1.0) * pow(1.0 - d, 2 * l + 1) + l * eps + l + 1;
-  return (2 * l + 1) * eps * pow(1.0 - d, l + 1) / den;
-}
-double cprime(int lp) {
-  double df = 1.0, fact = 1.0;
-  for (int k = 2 * lp - 3; k > 1; k -= 2) df *= k;
-  for (int k = 2; k <= lp; ++k) fact *= k;
-  return (((lp + 1) % 2 == 0) ? 1.0 : -1.0) * pow(0.5, lp + 1) * (4.0 * lp - 1.0) * df / fact;
-}
-
 // FP64 [n][3] positions -> particle records, ids 0..n-1, zero velocities; flags positions
 // outside 1 < r < r_out or non-finite.
 template <class T>
@@ -121,8 +106,22 @@ __global__ void k_na_init(StepState* st, int64_t step, int* err, unsigned* ticke
   st->u = 0.0;
   st->kick = 0.0;
   st->sync = 0;
+  st->nabs_step = 0;
+  st->qs_acc = 0.0;
+  st->nabs_total = 0;
   *err = 0;
   for (int k = 0; k < nticket; ++k) ticket[k] = 0u;
+}
+
+cudaError_t preload_noalloc_kernels() {
+  cudaFuncAttributes fa;
+  const void* fns[] = {reinterpret_cast<const void*>(&k_na_load<float>),
+                       reinterpret_cast<const void*>(&k_na_load<double>), reinterpret_cast<const void*>(&k_na_init)};
+  for (const void* f : fns) {
+    const cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <class T>
@@ -173,8 +172,8 @@ int run(const imrp_params* p, const double* x, int64_t n, int64_t step, double* 
                        static_cast<T*>(P(o.tot)), static_cast<double*>(P(o.totd)), ngroups, nc, 32, s);
   double canti[kTabL] = {0}, f[kTabL] = {0};
   for (int l = 1; l <= L; ++l) {
-    f[l] = f_coef(l, d, p->eps_D);
-    canti[l] = (l % 2 == 1) ? cprime((l + 1) / 2) * bp_coef(l, d, p->eps_D) : 0.0;
+    f[l] = coef_f(l, d, p->eps_D);
+    canti[l] = coef_canti(l, d, p->eps_D);
   }
   FinalizeArgs fa;
   memset(&fa, 0, sizeof(fa));
@@ -217,6 +216,8 @@ int run(const imrp_params* p, const double* x, int64_t n, int64_t step, double* 
   a.dt = T(p->dt);
   a.r_out = T(r_out);
   a.wall_rule = p->wall_rule;
+  a.nabs = nullptr;  // field only: nothing is pushed or absorbed
+  a.sigma_v = 0.0;
   a.self_image = p->self_image;
   a.seed = p->seed;
   double rl = 1.0;
@@ -259,6 +260,17 @@ extern "C" int imrp_field_noalloc(const imrp_params* p, const double* x_dev, int
   {
     std::lock_guard<std::mutex> g(g_mu);
     if (!g_addr[dev]) {
+      // Set-up, once per device: CUDA loads device code lazily, and loading a
+      // module reserves device memory (its code and its static arrays, this
+      // file's scratch included). So every kernel that a call may launch, in
+      // both precisions and at every degree up to the limit, is loaded here,
+      // with its tables filled, and later calls load nothing.
+      if (preload_core_kernels() != cudaSuccess || preload_noalloc_kernels() != cudaSuccess)
+        return IMRP_E_CUDA;
+      for (const auto& k : g_f)
+        if (k.L <= kMaxL && k.init(dev) != 0) return IMRP_E_CUDA;
+      for (const auto& k : g_d)
+        if (k.L <= kMaxL && k.init(dev) != 0) return IMRP_E_CUDA;
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return IMRP_E_CUDA;
       g_addr[dev] = ptr;

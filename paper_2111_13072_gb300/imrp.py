@@ -25,6 +25,7 @@ EXPORTS = [
     "imrp_load_particles_async", "imrp_copy_qdiff_async", "imrp_drude_fit", "imrp_drude_k",
     "imrp_drude_te", "imrp_admittance", "imrp_fit_damped_sine", "imrp_sheath_solve",
     "imrp_set_ion_profile", "imrp_checkpoint", "imrp_restore", "imrp_batch_failed",
+    "imrp_get_surface_charge", "imrp_fp32_peak",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -113,6 +114,8 @@ def load_library(path: str = LIB_PATH):
     pu32 = P(ctypes.c_uint32)
     L.imrp_checkpoint.argtypes = [c_void_p, pd, pd, pu32, P(ctypes.c_int64)]
     L.imrp_restore.argtypes = [c_void_p, pd, pd, pu32, ctypes.c_int64, ctypes.c_int64]
+    L.imrp_get_surface_charge.argtypes = [c_void_p, pd, P(ctypes.c_int64)]
+    L.imrp_fp32_peak.argtypes = [pd, P(ctypes.c_int)]
     for name in EXPORTS:
         if name not in ("imrp_default_params", "imrp_last_error", "imrp_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -150,6 +153,15 @@ def field_noalloc(params: Params, x_dev_ptr: int, n: int, step: int, E_dev_ptr: 
                                            ctypes.c_void_p(E_dev_ptr), ctypes.c_void_p(stream_ptr or 0))
     if rc != 0:
         raise IMRPError(rc, "imrp_field_noalloc failed")
+
+
+def fp32_peak():
+    """imrp_fp32_peak: (measured FP32 FMA TFLOP/s of the current device, SM count)."""
+    t, n = ctypes.c_double(), ctypes.c_int()
+    rc = load_library().imrp_fp32_peak(ctypes.byref(t), ctypes.byref(n))
+    if rc != 0:
+        raise IMRPError(rc, "fp32_peak failed")
+    return t.value, n.value
 
 
 def admittance(q, u, dt: float, first_kick: float, n_freq: int = 1000, w_max: float = 2.0):
@@ -399,6 +411,12 @@ class Sim:
         x, v = np.zeros((n, 3)), np.zeros((n, 3))
         self._check(self._lib.imrp_get_particles(self._h, _ptr(x), _ptr(v)))
         return x, v
+
+    def surface_charge(self):
+        """imrp_get_surface_charge: (Q_S in super-particle charges, probe absorptions)."""
+        q, k = ctypes.c_double(), ctypes.c_int64()
+        self._check(self._lib.imrp_get_surface_charge(self._h, ctypes.byref(q), ctypes.byref(k)))
+        return q.value, k.value
 
     def spectrum(self, n_freq: int = 1000, w_max: float = 2.0, fit: bool = True):
         om, re, im = np.zeros(n_freq), np.zeros(n_freq), np.zeros(n_freq)

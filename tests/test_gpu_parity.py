@@ -14,7 +14,7 @@ from paper_2111_13072_gb300.inputs import WORKLOADS, Workload, maxwellian_shell,
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-5, 1: 1e-4}
+from parity_metrics import P999, TOL, check_field
 
 
 @pytest.fixture(scope="module")
@@ -58,7 +58,23 @@ def test_field_matches_oracle(imrp, prec, n, L):
         # a lone electron feels only the ions, its image is excluded: compare directly
         np.testing.assert_allclose(E, Eo, rtol=TOL[prec], atol=0)
     else:
-        assert _rel(E, Eo) < TOL[prec]
+        check_field(E, Eo, prec, f"n={n} L={L}")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,L", [(150000, 16), (100003, 24)])
+def test_field_matches_oracle_every_particle_large(imrp, prec, n, L):
+    """Every particle at sizes beyond one segment of the group scan (more than
+    64 groups of 1024 particles: the multi-segment sums, the ticketed last-CTA
+    scan and the segment bases all run), at the bench's degree and at the
+    largest one, against the oracle's scan evaluator."""
+    x, v = workload_state(BASE, N=n)
+    p, op = _pair(imrp, BASE, n, precision=prec, l_max=L, drive_kind=1, V_volts=50.0)
+    with imrp.Sim(p) as sim:
+        sim.load(x, v)
+        E = sim.field()
+    Eo = oracle.field_scan(op, x, u=oracle.drive(op, 0))
+    check_field(E, Eo, prec, f"n={n} L={L}")
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -74,7 +90,7 @@ def test_field_terms(imrp, prec, self_image, drive, V, qs):
         sim.load(x, v)
         E = sim.field()
     Eo = oracle.field_scan(op, x, u=oracle.drive(op, 0))
-    assert _rel(E, Eo) < TOL[prec]
+    check_field(E, Eo, prec, f"self_image={self_image} drive={drive}")
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -130,6 +146,42 @@ def test_collision_steps_match_oracle(imrp, prec):
     # speeds change only through the field and the walls: scattering keeps them
     scattered = np.sum(np.abs(np.einsum("ij,ij->i", vo, v) / (np.linalg.norm(vo, axis=1) * np.linalg.norm(v, axis=1))) < 0.9)
     assert scattered > 0.2 * n
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_absorbing_walls_match_oracle(imrp, prec):
+    """wall_rule = 2: electrons that reach the probe are absorbed and their
+    charge joins Q_S, those that reach the outer wall leave, and each is
+    replaced from the outer wall with the same Philox draws on both sides.
+    Six steps: positions, velocities, Q_diff, the surface charge and the
+    absorption count against the oracle's run."""
+    n = 3000
+    w = Workload("absorb", N=n, l_max=8, T_e_eV=20.0, n_e_m3=1e15, drive_kind=1, V_volts=50.0,
+                 wall_rule=2)
+    x, v = workload_state(w, N=n)
+    p, op = _pair(imrp, w, n, precision=prec)
+    assert op.wall_rule == 2 and op.sigma_v > 0
+    with imrp.Sim(p) as sim:
+        sim.load(x, v)
+        q, u = sim.step(6)
+        xg, vg = sim.particles()
+        qs_g, nab_g = sim.surface_charge()
+    xo, vo, qo, uo, hits, qs_o, nab_o = oracle.run(op, x, v, 6, surface=True)
+    assert nab_o > 5 and hits > nab_o
+    # the same particles are absorbed (an FP32 radius within rounding of a wall
+    # may decide otherwise on the mixed path)
+    assert abs(nab_g - nab_o) <= (0 if prec == 0 else 2)
+    assert qs_g == -nab_g and qs_o == -nab_o
+    per = np.linalg.norm(xg - xo, axis=1) / np.linalg.norm(xo, axis=1)
+    bad = np.sum(per > 10 * TOL[prec])
+    assert bad <= (0 if prec == 0 else 3), f"{bad} particles differ"
+    good = per <= 10 * TOL[prec]
+    assert _rel(xg[good], xo[good]) < TOL[prec]
+    assert _rel(vg[good], vo[good]) < 10 * TOL[prec]
+    np.testing.assert_allclose(q, qo, rtol=10 * TOL[prec], atol=10 * TOL[prec] * np.max(np.abs(qo)))
+    # every particle is inside the domain, and the re-injected ones moved inwards
+    r = np.linalg.norm(xg, axis=1)
+    assert np.all((r >= 1.0) & (r <= op.r_out * (1 + 1e-6)))
 
 
 def test_qdiff_and_drive_sequence(imrp):
@@ -251,7 +303,11 @@ def test_large_sampled_parity(imrp):
     order = np.argsort(np.linalg.norm(x, axis=1))
     sample = np.unique(np.concatenate([order[:3], order[-3:], rng.choice(w.N, 10, replace=False)]))
     Eo = oracle.field_brute(op, x, u=oracle.drive(op, 0), sample=sample)
-    assert _rel(E[sample], Eo) < TOL[1]
+    rel = _rel(E[sample], Eo)
+    err = np.linalg.norm(E[sample] - Eo, axis=1) / np.linalg.norm(Eo, axis=1)
+    print(f"N=2e6 sampled: ||dE||/||E|| = {rel:.3e}, largest per particle {err.max():.3e}")
+    assert rel < TOL[1]
+    assert err.max() < P999[1]
     r = np.linalg.norm(xg, axis=1)
     assert np.all(r >= 1.0) and np.all(r <= op.r_out)
     assert np.all(np.isfinite(vg)) and np.all(np.isfinite(q))
@@ -273,7 +329,7 @@ def test_m0_only_truncation_matches_oracle(imrp, prec, L, si, drive):
         q, _ = sim.step(3)
         xg, vg = sim.particles()
     Eo = oracle.field_scan(op, x, u=oracle.drive(op, 0))
-    assert _rel(E, Eo) < TOL[prec]
+    check_field(E, Eo, prec, f"m0_only L={L}")
     xo, vo, qo, _, _ = oracle.run(op, x, v, 3)
     assert _rel(vg - v, vo - v) < 10 * TOL[prec]
     np.testing.assert_allclose(q, qo, rtol=10 * TOL[prec], atol=10 * TOL[prec] * np.max(np.abs(qo)))

@@ -10,7 +10,7 @@ from paper_2111_13072_gb300.inputs import Workload, radial_profile_shell
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-5, 1: 1e-4}
+from parity_metrics import TOL, check_field
 ARGON = 39.948 * 1822.888486
 # the paper's probe and plasma (Sec. 4): R = 4 mm, R_E = 3 mm, n = 1e15 m^-3, T_e = 3 eV, r < 10 R
 PAPER = Workload("sheath", N=3000, l_max=8, T_e_eV=3.0, n_e_m3=1e15, R_E_m=3e-3, R_D_m=4e-3,
@@ -63,7 +63,7 @@ def test_field_with_ion_profile_matches_oracle(imrp, eq, prec, n, L, drive):
         sim.load(x, v)
         E = sim.field()
     Eo = oracle.field_scan(op, x, u=oracle.drive(op, 0))
-    assert _rel(E, Eo) < TOL[prec]
+    check_field(E, Eo, prec, f"ion profile n={n} L={L}")
 
 
 @pytest.mark.parametrize("prec", [0, 1])
