@@ -125,34 +125,113 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(w, budget_s=15.0, L=None):
-    """The FP64 oracle (radius-ordered scan evaluator, leapfrog, walls) on a
-    bounded sample: a smaller instance of the same workload (same geometry,
-    density, temperature and l_max), timed on one host core."""
+def _oracle_sample(w, n, seed, L=None):
     import oracle
-    from paper_2111_13072_gb300.inputs import workload_state
+    from paper_2111_13072_gb300.inputs import Workload, workload_state
     L = w.l_max if L is None else L
+    ws = Workload(w.name, N=n, l_max=L, T_e_eV=w.T_e_eV, n_e_m3=w.n_e_m3, R_E_m=w.R_E_m, R_D_m=w.R_D_m,
+                  eps_D=w.eps_D, outer_debye=w.outer_debye, outer_R=w.outer_R, dt=w.dt,
+                  drive_kind=w.drive_kind, V_volts=w.V_volts, width_wpe=w.width_wpe, seed=seed)
+    p = oracle.from_physical(w.R_E_m, w.R_D_m, w.eps_D, w.R_out_m, w.n_e_m3, w.T_e_eV, n, L, w.dt,
+                             drive_kind=w.drive_kind, V_volts=w.V_volts, width_wpe=w.width_wpe, seed=seed)
+    x, v = workload_state(ws)
+    return p, x, v
 
-    def make(n):
-        p = oracle.from_physical(w.R_E_m, w.R_D_m, w.eps_D, w.R_out_m, w.n_e_m3, w.T_e_eV, n, L, w.dt,
-                                 drive_kind=w.drive_kind, V_volts=w.V_volts, width_wpe=w.width_wpe,
-                                 seed=w.seed)
-        x, v = workload_state(w, N=n)
-        return p, x, v
 
-    p, x, v = make(1000)
+def _oracle_timed_run(args):
+    """One worker of the host baseline: `warmup` untimed then `steps` timed
+    oracle steps on its own sample; returns the timed seconds."""
+    w, n, seed, warmup, steps = args
+    import oracle
+    p, x, v = _oracle_sample(w, n, seed)
+    if warmup:
+        x, v, _, _, _ = oracle.run(p, x, v, warmup)
+    t = time.perf_counter()
+    oracle.run(p, x, v, steps, step0=warmup, first_half_kick=warmup == 0)
+    return time.perf_counter() - t
+
+
+def _oracle_per_particle_step(w):
+    import oracle
+    p, x, v = _oracle_sample(w, 1000, w.seed)
     t = time.perf_counter()
     oracle.run(p, x, v, 1)
-    per = (time.perf_counter() - t) / 1000.0
+    return (time.perf_counter() - t) / 1000.0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(w, budget_s=15.0):
+    """The FP64 oracle (radius-ordered scan evaluator, leapfrog, walls) as it
+    stands, on bounded samples of the same workload (same geometry, density,
+    temperature and l_max): once on one host core, and as one independent
+    sample per core on all host cores (spawned processes, the oracle itself
+    is single-threaded); particle-steps/s = all particles x steps / wall time."""
+    import multiprocessing as mp
+    per = _oracle_per_particle_step(w)
     ns = int(max(1000, min(20000, budget_s / 10.0 / per)))
     steps = max(1, int(budget_s / (per * ns)))
-    p, x, v = make(ns)
-    t = time.perf_counter()
-    oracle.run(p, x, v, steps)
-    dt = time.perf_counter() - t
-    return {"value": ns * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{ns} particles x {steps} steps of the same workload (l_max={L}), "
-                      f"scan evaluator, {dt:.1f} s"}
+    t1 = _oracle_timed_run((w, ns, w.seed, 0, steps))
+    single = {"value": ns * steps / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"{ns} particles x {steps} steps of the same workload (l_max={w.l_max}), "
+                        f"scan evaluator, {t1:.1f} s"}
+    nc = host_cores()
+    with mp.get_context("spawn").Pool(nc) as pool:
+        pool.map(_oracle_per_particle_step, [w] * nc)  # start-up and import outside the timing
+        t = time.perf_counter()
+        pool.map(_oracle_timed_run, [(w, ns, w.seed + 1000 * (k + 1), 0, steps) for k in range(nc)])
+        tn = time.perf_counter() - t
+    return {"value": nc * ns * steps / tn, "unit": UNIT, "cores": nc, "kind": "oracle",
+            "sample": f"{nc} independent samples (one per host core, spawned processes) of {ns} particles "
+                      f"x {steps} steps of the same workload (l_max={w.l_max}), scan evaluator, {tn:.1f} s",
+            "single_core": single}
+
+
+def _brute_samples(args):
+    w, N, idx = args
+    import oracle
+    from paper_2111_13072_gb300.inputs import workload_state
+    x, _ = workload_state(w)
+    p = oracle.from_physical(w.R_E_m, w.R_D_m, w.eps_D, w.R_out_m, w.n_e_m3, w.T_e_eV, N, w.l_max, w.dt,
+                             drive_kind=w.drive_kind, V_volts=w.V_volts, width_wpe=w.width_wpe, seed=w.seed)
+    return oracle.field_brute(p, x, u=oracle.drive(p, 0), sample=idx)
+
+
+def oracle_error(w, fields, n_sample=32):
+    """The FP64 oracle's error of each precision's field at the workload itself
+    (step 0, the loaded state): sampled particles (the 3 innermost, the 3
+    outermost and random ones) against the oracle's direct pair sum (the
+    definition), spread over the host cores. fields: {name: E [N,3]}."""
+    import multiprocessing as mp
+    from paper_2111_13072_gb300.inputs import workload_state
+    x, _ = workload_state(w)
+    order = np.argsort(np.linalg.norm(x, axis=1))
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([order[:3], order[-3:], rng.choice(w.N, n_sample - 6, replace=False)]))
+    nc = min(host_cores(), len(idx))
+    parts = [idx[k::nc] for k in range(nc)]
+    with mp.get_context("spawn").Pool(nc) as pool:
+        res = pool.map(_brute_samples, [(w, w.N, part) for part in parts])
+    Eo = np.zeros((len(idx), 3))
+    pos = {int(i): k for k, i in enumerate(idx)}
+    for part, E in zip(parts, res):
+        for i, e in zip(part, E):
+            Eo[pos[int(i)]] = e
+    out = {}
+    mag = np.linalg.norm(Eo, axis=1)
+    for name, E in fields.items():
+        d = np.linalg.norm(E[idx] - Eo, axis=1)
+        out[name] = {"norm": float(np.linalg.norm(E[idx] - Eo) / np.linalg.norm(Eo)),
+                     "max_per_particle": float(np.max(d / mag)),
+                     "median_per_particle": float(np.median(d / mag))}
+    out["sample"] = (f"{len(idx)} particles of the loaded state (3 innermost, 3 outermost, the rest random) "
+                     f"against the oracle's direct pair sum, {nc} host processes")
+    return out
 
 
 def ensemble_measure(steps, warmup, autotune=True, n_instances=64, stream=None):
@@ -193,23 +272,45 @@ def ensemble_measure(steps, warmup, autotune=True, n_instances=64, stream=None):
                         "l_max in {8,12,16}, mixed precision, one captured graph per step pair"}
 
 
+def ensemble_compare(steps, warmup):
+    """The 64-instance ensemble with the launch shapes the library picks at
+    creation and with the autotuner's choices (imrp_autotune), each timed."""
+    plain = ensemble_measure(steps, warmup, autotune=False)
+    tuned = ensemble_measure(steps, warmup, autotune=True)
+    tuned["default_shapes"] = {"value": plain["value"], "ms_per_step": plain["ms_per_step"]}
+    tuned["speedup_over_default"] = tuned["value"] / plain["value"]
+    return tuned
+
+
 def serving_measure(n_requests, steps, rate=20.0):
     """Continuous-batching service: Poisson arrivals at `rate` of spectrum
     requests (N log-uniform in [1e5, 4e6], T_e in [0.5, 5] eV, n_e log-uniform
-    in [1e14, 1e17] m^-3, l_max in {8, 16}); latency = completion - arrival."""
+    in [1e14, 1e17] m^-3, l_max in {8, 16}, `steps` steps each) over a bounded
+    horizon of n_requests; latency = completion (spectrum ready) - arrival.
+    The offered load is rate x the mean particle-steps of a request; the
+    sustained throughput is all particle-steps over the span from the first
+    arrival to the last completion; the highest arrival rate the device
+    sustains (at which the queue, and so p99, stays bounded) is the
+    sustained throughput over the mean request."""
     from paper_2111_13072_gb300.serve import SpectrumServer, serving_requests
     reqs = serving_requests(n_requests, rate=rate, steps=steps)
-    srv = SpectrumServer(chunk=max(10, steps // 10))
+    srv = SpectrumServer(chunk=250)
     t0 = time.perf_counter()
     res = srv.serve(reqs, realtime=True)
     span = time.perf_counter() - t0
     lat = np.array([r.latency for r in res])
-    ps = sum(r.workload.N * r.steps for r in reqs)
+    work = np.array([r.workload.N * r.steps for r in reqs], dtype=np.float64)
+    sustained = float(work.sum() / span)
     return {"requests": n_requests, "steps_per_request": steps, "rate_req_per_s": rate,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "spectra_per_s": n_requests / span, "particle_steps_per_s": ps / span,
+            "spectra_per_s": n_requests / span, "particle_steps_per_s": sustained,
+            "offered_particle_steps_per_s": float(rate * work.mean()),
+            "max_sustainable_rate_req_per_s": float(sustained / work.mean()),
+            "errors": int(sum(r.error is not None for r in res)),
             "max_active": srv.stats["max_active"], "peak_bytes": srv.stats["peak_bytes"],
-            "workload": "Poisson arrivals, N log-uniform [1e5,4e6], T_e U[0.5,5] eV, n_e log-U[1e14,1e17], "
+            "span_s": span,
+            "workload": f"Poisson arrivals at {rate:g} req/s, {n_requests} requests of {steps} steps, "
+                        "N log-uniform [1e5,4e6], T_e U[0.5,5] eV, n_e log-U[1e14,1e17], "
                         "l_max in {8,16}, mixed precision"}
 
 
@@ -309,36 +410,69 @@ def drude_measure(temps=(2.0, 3.0, 5.0), N=500000, steps=3000, seeds=4, t_win=30
 
 
 def run_reference(args, w):
-    """--impl reference: the FP64 CPU oracle as the reference arm."""
-    import oracle
-    from paper_2111_13072_gb300.inputs import workload_state
-    p1 = oracle.from_physical(w.R_E_m, w.R_D_m, w.eps_D, w.R_out_m, w.n_e_m3, w.T_e_eV, 1000,
-                              w.l_max, w.dt, drive_kind=w.drive_kind, V_volts=w.V_volts,
-                              width_wpe=w.width_wpe, seed=w.seed)
-    x, v = workload_state(w, N=1000)
-    t = time.perf_counter()
-    oracle.run(p1, x, v, 1)
-    per = (time.perf_counter() - t) / 1000.0
+    """--impl reference: the FP64 CPU oracle as the reference arm, on all host
+    cores (one independent sample of the workload per core, spawned processes;
+    the timed steps of the slowest worker set the time)."""
+    import multiprocessing as mp
+    per = _oracle_per_particle_step(w)
     total_budget = 90.0
     ns = int(max(200, min(20000, total_budget / (args.steps + args.warmup) / per)))
-    p = oracle.from_physical(w.R_E_m, w.R_D_m, w.eps_D, w.R_out_m, w.n_e_m3, w.T_e_eV, ns, w.l_max,
-                             w.dt, drive_kind=w.drive_kind, V_volts=w.V_volts, width_wpe=w.width_wpe,
-                             seed=w.seed)
-    x, v = workload_state(w, N=ns)
-    x, v, _, _, _ = oracle.run(p, x, v, args.warmup)
-    t = time.perf_counter()
-    oracle.run(p, x, v, args.steps, step0=args.warmup, first_half_kick=False)
-    dt = time.perf_counter() - t
-    val = ns * args.steps / dt
-    sample = f"{ns} particles per step (same workload, l_max={w.l_max}), scan evaluator, FP64"
+    nc = host_cores()
+    with mp.get_context("spawn").Pool(nc) as pool:
+        pool.map(_oracle_per_particle_step, [w] * nc)
+        times = pool.map(_oracle_timed_run,
+                         [(w, ns, w.seed + 1000 * k, args.warmup, args.steps) for k in range(nc)])
+    dt = max(times)
+    val = nc * ns * args.steps / dt
+    sample = (f"{nc} independent samples (one per host core) of {ns} particles per step "
+              f"(same workload, l_max={w.l_max}), scan evaluator, FP64")
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload_desc(w), "sample_particles": ns, "parallelism": "host, 1 core"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": workload_desc(w), "sample_particles": ns,
+                       "parallelism": f"host, {nc} cores (independent samples)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": nc, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def sub_config(name, steps, warmup, nprof, peak_tflops, stream):
+    """Another single-instance workload, timed like the main one (graph-replayed
+    steps, CUDA events on the context's stream) with its per-stage device time
+    and the field kernel's roofline fraction."""
+    import torch
+    from paper_2111_13072_gb300 import imrp
+    from paper_2111_13072_gb300.inputs import WORKLOADS, workload_state
+    w = WORKLOADS[name]
+    x, v = workload_state(w)
+    with imrp.Sim(imrp.params_from_workload(w)) as sim:
+        sim.set_stream(stream.cuda_stream)
+        sim.load(x, v)
+        sim.step_async(warmup)
+        sim.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step_async(steps)
+        e1.record(stream)
+        sim.sync()
+        ms = e0.elapsed_time(e1)
+        stages = sim.profile_steps(nprof)
+    field_ms = stages["field"] / nprof
+    K = (w.l_max + 1) ** 2
+    out = {"workload": workload_desc(w), "value": w.N * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms / steps, "dtype": "f32" if w.precision else "f64",
+           "stage_ms_per_step": {k: v / nprof for k, v in stages.items()},
+           "gpu_launches": LAUNCHES_PER_STEP * steps}
+    if w.precision:
+        ach = field_flops_per_particle(w.l_max) * w.N / (field_ms / 1e3) / 1e12
+        ach24 = 24.0 * K * w.N / (field_ms / 1e3) / 1e12
+        out["roofline"] = {"bound": "alu", "kernel": "k_field (gather+push)", "achieved": ach,
+                           "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops,
+                           "frac_24K_model": ach24 / peak_tflops,
+                           "flops_per_particle": field_flops_per_particle(w.l_max)}
+    return out
 
 
 def main():
@@ -352,6 +486,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-sub-configs", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="bounded horizon of the serving measurement (requests of 5000 steps)")
+    ap.add_argument("--no-oracle-err", action="store_true")
     ap.add_argument("--drude", action="store_true",
                     help="also run the T_e sweep of the temperature diagnostic on the paper's case")
     ap.add_argument("--drude-n", type=int, default=500000)
@@ -444,7 +582,10 @@ def main():
     # coarse per-particle model: 24 K flops (harmonics, scans, three contractions), K = (L+1)^2
     achieved_24k = 24.0 * K * N / (field_ms / 1e3) / 1e12
     sm_mhz = clocks["sm_mhz"] or 2070.0
-    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+    # measured FP32 FMA throughput of this device (imrp_fp32_peak: independent
+    # FMA chains on every SM, the SM count read from the device)
+    peak, n_sm = imrp.fp32_peak()
+    peak_derived = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
     traffic = None
     tf = os.path.join(ROOT, "profiles", "field_traffic.json")
     if os.path.exists(tf):
@@ -459,7 +600,9 @@ def main():
                 "frac": achieved / peak, "traffic": traffic, "kernel": "k_field (gather+push)",
                 "flops_per_particle": field_flops_per_particle(w.l_max),
                 "achieved_24K_model": achieved_24k, "frac_24K_model": achieved_24k / peak,
-                "peak_basis": f"152 SMs x 128 FP32 FMA/clk x 2 x median SM clock {sm_mhz:.0f} MHz",
+                "peak_basis": "measured (imrp_fp32_peak: FFMA chains on all SMs)",
+                "peak_derived": peak_derived,
+                "peak_derived_basis": f"{n_sm} SMs x 128 FP32 FMA/clk x 2 x median SM clock {sm_mhz:.0f} MHz",
                 "stage_ms_per_step": {k: v / nprof for k, v in stages.items()}}
 
     # end to end through the public API with host buffers (pinned): every step
@@ -502,12 +645,16 @@ def main():
            "d2h_bytes_per_step": 8, "steps": ne, "mode": "streamed (H2D of step k+1 overlaps step k)",
            "blocking_value": throughput(N, ne, world, tb)}
 
+    # the field of each precision at the loaded state, for the oracle's error
+    sim.load(x, v)
+    fields = {"mixed": sim.field()}
     fp64 = None
     if not args.no_fp64:
         p64 = imrp.params_from_workload(w, precision=0, seed=rank_seed(w.seed, rank))
         with imrp.Sim(p64) as s64:
             s64.set_stream(stream.cuda_stream)
             s64.load(x, v)
+            fields["fp64"] = s64.field()
             s64.step_async(3)
             s64.sync()
             k64 = 6
@@ -521,14 +668,22 @@ def main():
                     "note": "plain FP64 GPU path, same workload"}
     sim.close()
 
-    serving = None if args.no_serving else serving_measure(12, 500)
-    ensemble = None if args.no_ensemble else ensemble_measure(200, 4, autotune=False)
+    subs = {}
+    if not args.no_sub_configs:
+        subs["mixed_n1.6e7_l24"] = sub_config("mixed_n1.6e7_l24", 10, 3, 3, peak, stream)
+        subs["fp64_n2e4_l8"] = sub_config("fp64_n2e4_l8", 400, 10, 20, peak, stream)
+
+    serving = None if (args.no_serving or rank != 0) else serving_measure(args.serve_requests, 5000)
+    ensemble = None if args.no_ensemble else ensemble_compare(200, 4)
     drude = (drude_measure(N=args.drude_n, seeds=args.drude_seeds, sheath=args.drude_sheath)
              if (args.drude and rank == 0) else None)
 
     cpu = None
+    oerr = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
+    if rank == 0 and not args.no_oracle_err:
+        oerr = oracle_error(w, fields)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -540,7 +695,8 @@ def main():
                            "l2": "inputs larger than L2 (per-step working set > 300 MB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks, "fp64_gpu": fp64,
-                "serving": serving, "ensemble": ensemble, "drude": drude}
+                "oracle_err": oerr, "configs": subs, "serving": serving, "ensemble": ensemble,
+                "drude": drude}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

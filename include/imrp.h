@@ -164,6 +164,12 @@ int imrp_step_async(imrp_ctx* ctx, int64_t n_steps);
 /* Waits for queued work and checks the device error flags. */
 int imrp_sync(imrp_ctx* ctx);
 
+/* Without waiting: *ready = 1 when all work queued on the context's stream has
+ * finished, 0 while some is still running (for a host loop that serves many
+ * contexts). It does not check the device error flags; imrp_sync does.
+ * Errors: IMRP_E_INVAL, IMRP_E_CUDA (an earlier asynchronous failure). */
+int imrp_ready(imrp_ctx* ctx, int* ready);
+
 /* Copies Q_diff(t_n) and u_asy(t_n) for steps first .. first+count-1 since the
  * last load to host arrays (either may be NULL). */
 int imrp_get_qdiff(imrp_ctx* ctx, int64_t first, int64_t count, double* qdiff, double* uasy);

@@ -625,6 +625,18 @@ int imrp_step_async(imrp_ctx* ctx, int64_t n_steps) {
   return launch_steps(ctx, n_steps);
 }
 
+int imrp_ready(imrp_ctx* ctx, int* ready) {
+  if (!ctx || !ready) return IMRP_E_INVAL;
+  const cudaError_t e = cudaStreamQuery(ctx->stream);
+  if (e == cudaErrorNotReady) {
+    *ready = 0;
+    return IMRP_OK;
+  }
+  CK(e);
+  *ready = 1;
+  return IMRP_OK;
+}
+
 int imrp_sync(imrp_ctx* ctx) {
   if (!ctx) return IMRP_E_INVAL;
   CK(cudaGetLastError());

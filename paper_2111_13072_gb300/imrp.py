@@ -25,7 +25,7 @@ EXPORTS = [
     "imrp_load_particles_async", "imrp_copy_qdiff_async", "imrp_drude_fit", "imrp_drude_k",
     "imrp_drude_te", "imrp_admittance", "imrp_fit_damped_sine", "imrp_sheath_solve",
     "imrp_set_ion_profile", "imrp_checkpoint", "imrp_restore", "imrp_batch_failed",
-    "imrp_get_surface_charge", "imrp_fp32_peak",
+    "imrp_get_surface_charge", "imrp_fp32_peak", "imrp_ready",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -116,6 +116,7 @@ def load_library(path: str = LIB_PATH):
     L.imrp_restore.argtypes = [c_void_p, pd, pd, pu32, ctypes.c_int64, ctypes.c_int64]
     L.imrp_get_surface_charge.argtypes = [c_void_p, pd, P(ctypes.c_int64)]
     L.imrp_fp32_peak.argtypes = [pd, P(ctypes.c_int)]
+    L.imrp_ready.argtypes = [c_void_p, P(ctypes.c_int)]
     for name in EXPORTS:
         if name not in ("imrp_default_params", "imrp_last_error", "imrp_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -411,6 +412,12 @@ class Sim:
         x, v = np.zeros((n, 3)), np.zeros((n, 3))
         self._check(self._lib.imrp_get_particles(self._h, _ptr(x), _ptr(v)))
         return x, v
+
+    def ready(self) -> bool:
+        """imrp_ready: True when the context's queued work has finished (no wait)."""
+        r = ctypes.c_int()
+        self._check(self._lib.imrp_ready(self._h, ctypes.byref(r)))
+        return bool(r.value)
 
     def surface_charge(self):
         """imrp_get_surface_charge: (Q_S in super-particle charges, probe absorptions)."""

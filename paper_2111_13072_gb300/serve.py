@@ -7,23 +7,31 @@ steps. The server
 * admits waiting requests (first come, first served) as soon as a slot and
   enough device memory are free -- the footprint of each request comes from the
   library (imrp_footprint), checked against an HBM budget;
-* keeps every admitted request's particle state resident on the device;
-* advances all admitted requests together, chunk by chunk, with one captured
-  CUDA graph per step pair over all of them (imrp_batch_*), so requests that
-  arrive while others run join at the next chunk and their work overlaps on the
-  GPU;
-* finishes a request when its steps are done: the spectrum is computed on the
-  GPU (imrp_spectrum), the context is freed and its memory returns to the pool;
+* prepares an admitted request off the loop's critical path: a worker thread
+  draws its initial state, creates its context and loads the particles, while
+  the loop keeps the running requests going;
+* keeps every admitted request's particle state resident on the device and
+  advances each in chunks of steps on its own stream, replaying the context's
+  own captured step graphs (a fixed graph per slot, captured once: admissions
+  and completions never re-capture anything), so that the steps of all
+  admitted requests overlap on the GPU and a request that arrives while
+  others run starts as soon as it is prepared;
+* polls the contexts without blocking (imrp_ready) and starts the next chunk
+  of whichever request is done with its last one;
+* finishes a request when its steps are done on another worker thread: the
+  spectrum is computed (imrp_spectrum: the transform on the GPU, the fit on
+  the host), the context is freed and its memory returns to the pool;
 * evicts a request whose context reports an error (a non-finite state, a
   particle outside the domain): its result carries the error, its memory
   returns to the pool, and the others keep running.
 
-A request's result does not depend on what else is in the mix: batched steps
-compute bit for bit what the request's steps compute alone.
+A request's result does not depend on what else is in the mix: its context
+computes bit for bit what it computes alone.
 """
 from __future__ import annotations
 
 import collections
+import concurrent.futures as cf
 import math
 import time
 from dataclasses import dataclass
@@ -66,130 +74,165 @@ class SpectrumResult:
 @dataclass
 class _Slot:
     req: SpectrumRequest
-    sim: imrp.Sim
+    sim: object
     remaining: int
     footprint: int
     admitted: float
+    inflight: int = 0
+
+
+def _failed(req, admitted, now, msg):
+    nan = float("nan")
+    return SpectrumResult(req.rid, nan, nan, np.full(4, nan), np.zeros(0), np.zeros(0), np.zeros(0),
+                          req.arrival, admitted, now, error=msg)
 
 
 class SpectrumServer:
     def __init__(self, hbm_budget: int | None = None, chunk: int = 200, max_slots: int = 64,
-                 autotune: bool = False, backend=None, state_fn=None):
-        """backend: the module with Sim, Batch, footprint, params_from_workload
-        and IMRPError (the library binding by default; tests pass a fake);
-        state_fn: workload -> (x, v) initial state."""
+                 autotune: bool = False, backend=None, state_fn=None, prep_workers: int = 2,
+                 poll_s: float = 2e-4):
+        """backend: the module with Sim, footprint, params_from_workload and
+        IMRPError (the library binding by default; tests pass a fake);
+        state_fn: workload -> (x, v) initial state; prep_workers: threads that
+        draw initial states and create and load contexts."""
         self.lib = imrp if backend is None else backend
         self.state_fn = workload_state if state_fn is None else state_fn
-        if hbm_budget is None:
+        self.device = None
+        if backend is None:
             import torch
-            free, _ = torch.cuda.mem_get_info()
-            hbm_budget = int(0.8 * free)
+            self.device = torch.cuda.current_device()
+            if hbm_budget is None:
+                free, _ = torch.cuda.mem_get_info()
+                hbm_budget = int(0.8 * free)
         self.budget = hbm_budget
         self.chunk = chunk
         self.max_slots = max_slots
         self.autotune = autotune
+        self.prep_workers = prep_workers
+        self.poll_s = poll_s
         self.stats = {"chunks": 0, "max_active": 0, "peak_bytes": 0, "evicted": 0}
 
-    def _admit(self, req: SpectrumRequest, now: float) -> _Slot:
-        p = self.lib.params_from_workload(req.workload)
-        sim = self.lib.Sim(p)
-        x, v = self.state_fn(req.workload)
-        sim.load(x, v)
-        if self.autotune:
-            sim.autotune()
-        return _Slot(req, sim, req.steps, self.lib.footprint(p, req.steps), now)
+    def _on_device(self):
+        if self.device is not None:
+            import torch
+            torch.cuda.set_device(self.device)
 
-    def _failed_slots(self, batch, ids, err) -> list[tuple[int, str]]:
-        """The requests whose contexts failed in the last chunk: the one the
-        batch reported (its flags are cleared by the report) and any other
-        whose own check still fails."""
-        k = batch.failed_index()
-        if k < 0:
-            raise err  # an error of the batch itself: not one request's
-        out = [(ids[k], str(err))]
-        for i, rid in enumerate(ids):
-            if i == k:
-                continue
-            try:
-                self._active[rid].sim.sync()
-            except self.lib.IMRPError as e:
-                out.append((rid, str(e)))
-        return out
+    def _prepare(self, req: SpectrumRequest):
+        """Worker thread: initial state, context, load (and autotuning)."""
+        self._on_device()
+        x, v = self.state_fn(req.workload)
+        sim = self.lib.Sim(self.lib.params_from_workload(req.workload))
+        try:
+            sim.load(x, v)
+            if self.autotune:
+                sim.autotune()
+        except Exception:
+            sim.close()
+            raise
+        return sim
+
+    def _finish(self, slot: _Slot, clock):
+        """Worker thread: spectrum, Q_diff read-back, free the context."""
+        self._on_device()
+        try:
+            sp = slot.sim.spectrum(slot.req.n_freq, slot.req.w_max)
+            q, _ = slot.sim.qdiff()
+        except self.lib.IMRPError as e:
+            slot.sim.close()
+            return _failed(slot.req, slot.admitted, clock(), str(e))
+        slot.sim.close()
+        return SpectrumResult(slot.req.rid, sp["w_res"], sp["dw"], sp["fit"], sp["omega"], sp["reY"], q,
+                              slot.req.arrival, slot.admitted, clock())
+
+    def _launch(self, slot: _Slot):
+        n = min(self.chunk, slot.remaining)
+        slot.sim.step_async(n)  # a launch error is not one request's: it propagates
+        slot.inflight = n
+        self.stats["chunks"] += 1
 
     def serve(self, requests: list[SpectrumRequest], realtime: bool = True) -> list[SpectrumResult]:
+        """realtime: requests arrive at their arrival times (else all at once,
+        in arrival order). Latencies are measured from the arrival."""
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         waiting: collections.deque[SpectrumRequest] = collections.deque()
+        preparing: dict[int, tuple] = {}
         active: dict[int, _Slot] = {}
-        self._active = active
+        finishing: dict[int, tuple] = {}
         results: list[SpectrumResult] = []
         used = 0
-        batch, batch_ids = None, None
         t0 = time.perf_counter()
-        clock = (lambda: time.perf_counter() - t0) if realtime else None
-        vtime = 0.0
-        while pending or waiting or active:
-            now = clock() if realtime else vtime
-            while pending and pending[0].arrival <= now:
-                waiting.append(pending.popleft())
-            # admission: FIFO, as long as a slot and the memory budget allow
-            while waiting and len(active) < self.max_slots:
-                req = waiting[0]
-                need = self.lib.footprint(self.lib.params_from_workload(req.workload), req.steps)
-                if used + need > self.budget and active:
-                    break
-                waiting.popleft()
-                slot = self._admit(req, now)
-                active[req.rid] = slot
-                used += slot.footprint
-            self.stats["max_active"] = max(self.stats["max_active"], len(active))
-            self.stats["peak_bytes"] = max(self.stats["peak_bytes"], used)
-            if not active:
-                nxt = pending[0].arrival if pending else now
-                if realtime:
-                    time.sleep(max(0.0, nxt - now))
-                else:
-                    vtime = max(vtime, nxt)
-                continue
-            ids = tuple(sorted(active))
-            if ids != batch_ids:
-                if batch is not None:
-                    batch.close()
-                batch = self.lib.Batch([active[i].sim for i in ids])
-                batch_ids = ids
-            n = min(self.chunk, min(s.remaining for s in active.values()))
-            tc = time.perf_counter()
-            batch.step(n)  # a launch error is not one request's: it propagates
-            try:
-                batch.sync()
-                failed = []
-            except self.lib.IMRPError as e:
-                failed = self._failed_slots(batch, ids, e)
-            self.stats["chunks"] += 1
-            if not realtime:
-                vtime += time.perf_counter() - tc
-            now = clock() if realtime else vtime
-            for rid, msg in failed:
-                s = active.pop(rid)
-                nan = float("nan")
-                results.append(SpectrumResult(rid, nan, nan, np.full(4, nan), np.zeros(0), np.zeros(0),
-                                              np.zeros(0), s.req.arrival, s.admitted, now, error=msg))
-                s.sim.close()
-                used -= s.footprint
-                self.stats["evicted"] += 1
-            for rid in [r for r in ids if r in active]:
-                s = active[rid]
-                s.remaining -= n
-                if s.remaining == 0:
-                    sp = s.sim.spectrum(s.req.n_freq, s.req.w_max)
-                    q, _ = s.sim.qdiff()
-                    done = clock() if realtime else vtime
-                    results.append(SpectrumResult(rid, sp["w_res"], sp["dw"], sp["fit"], sp["omega"],
-                                                  sp["reY"], q, s.req.arrival, s.admitted, done))
-                    s.sim.close()
-                    used -= s.footprint
-                    del active[rid]
-        if batch is not None:
-            batch.close()
+
+        def clock():
+            return time.perf_counter() - t0
+
+        prep = cf.ThreadPoolExecutor(max_workers=self.prep_workers)
+        fin = cf.ThreadPoolExecutor(max_workers=1)
+        try:
+            while pending or waiting or preparing or active or finishing:
+                now = clock()
+                while pending and (pending[0].arrival <= now or not realtime):
+                    waiting.append(pending.popleft())
+                # admission: FIFO, as long as a slot and the memory budget allow
+                while waiting and len(active) + len(preparing) < self.max_slots:
+                    req = waiting[0]
+                    need = self.lib.footprint(self.lib.params_from_workload(req.workload), req.steps)
+                    if used + need > self.budget and (active or preparing or finishing):
+                        break
+                    waiting.popleft()
+                    used += need
+                    preparing[req.rid] = (prep.submit(self._prepare, req), req, need, now)
+                self.stats["peak_bytes"] = max(self.stats["peak_bytes"], used)
+                progressed = False
+                for rid, (fut, req, need, adm) in list(preparing.items()):
+                    if not fut.done():
+                        continue
+                    del preparing[rid]
+                    progressed = True
+                    try:
+                        sim = fut.result()
+                    except self.lib.IMRPError as e:
+                        results.append(_failed(req, adm, clock(), str(e)))
+                        used -= need
+                        self.stats["evicted"] += 1
+                        continue
+                    slot = _Slot(req, sim, req.steps, need, adm)
+                    active[rid] = slot
+                    self._launch(slot)
+                self.stats["max_active"] = max(self.stats["max_active"], len(active))
+                for rid, slot in list(active.items()):
+                    if not slot.sim.ready():
+                        continue
+                    progressed = True
+                    try:
+                        slot.sim.sync()  # this context's device error flags
+                    except self.lib.IMRPError as e:
+                        del active[rid]
+                        results.append(_failed(slot.req, slot.admitted, clock(), str(e)))
+                        slot.sim.close()
+                        used -= slot.footprint
+                        self.stats["evicted"] += 1
+                        continue
+                    slot.remaining -= slot.inflight
+                    slot.inflight = 0
+                    if slot.remaining > 0:
+                        self._launch(slot)
+                    else:
+                        del active[rid]
+                        finishing[rid] = (fin.submit(self._finish, slot, clock), slot.footprint)
+                for rid, (fut, fp) in list(finishing.items()):
+                    if fut.done():
+                        del finishing[rid]
+                        used -= fp
+                        results.append(fut.result())
+                        progressed = True
+                if not progressed:
+                    if not (active or preparing or finishing) and pending and realtime:
+                        time.sleep(max(0.0, min(pending[0].arrival - clock(), 0.05)))
+                    else:
+                        time.sleep(self.poll_s)
+        finally:
+            prep.shutdown(wait=True)
+            fin.shutdown(wait=True)
         return sorted(results, key=lambda r: r.rid)
 
 

@@ -156,8 +156,9 @@ def test_absorbing_walls_match_oracle(imrp, prec):
     Six steps: positions, velocities, Q_diff, the surface charge and the
     absorption count against the oracle's run."""
     n = 3000
-    w = Workload("absorb", N=n, l_max=8, T_e_eV=20.0, n_e_m3=1e15, drive_kind=1, V_volts=50.0,
-                 wall_rule=2)
+    # a narrow shell (1 < r < 1.6) of hot electrons, so that many reach each wall
+    w = Workload("absorb", N=n, l_max=8, T_e_eV=20.0, n_e_m3=1e15, outer_R=1.6, drive_kind=1,
+                 V_volts=50.0, wall_rule=2)
     x, v = workload_state(w, N=n)
     p, op = _pair(imrp, w, n, precision=prec)
     assert op.wall_rule == 2 and op.sigma_v > 0

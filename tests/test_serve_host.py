@@ -1,4 +1,6 @@
-"""Host-side request and ensemble generators (no GPU)."""
+"""Host side of the serving and ensemble workloads (no GPU): the request and
+ensemble generators, and the serving loop driven by a fake backend (failure
+detection, independent progress, memory admission, error propagation)."""
 import numpy as np
 
 from paper_2111_13072_gb300.serve import ensemble_workloads, serving_requests
@@ -32,17 +34,36 @@ class _FakeError(RuntimeError):
 
 class _FakeSim:
     """Stands in for a GPU context: counts steps, fails (a device error flag
-    that the batch check reports) once it passes fail_at."""
+    that its sync reports) once it passes fail_at; its queued chunk is done
+    after `delay` polls."""
 
     def __init__(self, params):
         self.n_steps = params["steps"]
         self.fail_at = params["fail_at"]
+        self.broken = params["broken"]
         self.step = 0
         self.flag = False
         self.closed = False
+        self.busy = 0
+        self.delay = params["delay"]
 
     def load(self, x, v):
         pass
+
+    def step_async(self, n):
+        assert not self.closed
+        if self.broken:
+            raise _FakeError("IMRP_E_CUDA: launch")
+        self.step += n
+        self.busy = self.delay
+        if self.fail_at is not None and self.step > self.fail_at:
+            self.flag = True
+
+    def ready(self):
+        if self.busy:
+            self.busy -= 1
+            return False
+        return True
 
     def sync(self):
         if self.flag:
@@ -59,63 +80,43 @@ class _FakeSim:
         self.closed = True
 
 
-class _FakeBatch:
-    def __init__(self, sims):
-        self.sims = sims
-        self.failed = -1
-
-    def step(self, n):
-        for s in self.sims:
-            assert not s.closed
-            s.step += n
-            if s.fail_at is not None and s.step > s.fail_at:
-                s.flag = True
-
-    def sync(self):
-        self.failed = -1
-        for i, s in enumerate(self.sims):
-            if s.flag:
-                s.flag = False  # the report clears the first failing context's flags
-                self.failed = i
-                raise _FakeError("IMRP_E_NAN: non-finite value in the particle state")
-
-    def failed_index(self):
-        return self.failed
-
-    def close(self):
-        pass
-
-
 class _FakeBackend:
     IMRPError = _FakeError
     Sim = _FakeSim
-    Batch = _FakeBatch
 
-    def __init__(self, fail):
+    def __init__(self, fail, broken=(), delays=None):
         self.fail = fail
-        self.sims = {}
+        self.broken = set(broken)
+        self.delays = delays or {}
 
     def params_from_workload(self, w):
-        return {"steps": w.steps, "fail_at": self.fail.get(w.name)}
+        return {"steps": w.steps, "fail_at": self.fail.get(w.name), "broken": w.name in self.broken,
+                "delay": self.delays.get(w.name, 1)}
 
     def footprint(self, params, steps):
         return 1000
 
 
+def _server(backend, **kw):
+    from paper_2111_13072_gb300.serve import SpectrumServer
+    return SpectrumServer(hbm_budget=kw.pop("budget", 10 ** 6), chunk=100, backend=backend, poll_s=0.0,
+                          state_fn=lambda w: (np.zeros((w.N, 3)), np.zeros((w.N, 3))), **kw)
+
+
+def _reqs(n, steps=1000):
+    from paper_2111_13072_gb300.inputs import Workload
+    from paper_2111_13072_gb300.serve import SpectrumRequest
+    return [SpectrumRequest(i, Workload(f"r{i}", N=10, l_max=1, T_e_eV=1.0, n_e_m3=1e15, steps=steps),
+                            steps=steps, arrival=0.0) for i in range(n)]
+
+
 def test_server_evicts_failing_requests_and_serves_the_rest():
     """Failure detection on the host: two of five requests' contexts report a
-    device error mid-run (both in the same chunk); they are evicted with the
-    error, their memory returns, and the other three finish their steps."""
-    from paper_2111_13072_gb300.inputs import Workload
-    from paper_2111_13072_gb300.serve import SpectrumRequest, SpectrumServer
-
-    fail = {"r1": 250, "r3": 260}
-    reqs = [SpectrumRequest(i, Workload(f"r{i}", N=10, l_max=1, T_e_eV=1.0, n_e_m3=1e15, steps=1000),
-                            steps=1000, arrival=0.0) for i in range(5)]
-    backend = _FakeBackend(fail)
-    srv = SpectrumServer(hbm_budget=10 ** 6, chunk=100, backend=backend,
-                         state_fn=lambda w: (np.zeros((w.N, 3)), np.zeros((w.N, 3))))
-    res = srv.serve(reqs, realtime=False)
+    device error mid-run (in the same chunk); they are evicted with the error,
+    their memory returns, and the other three finish their steps."""
+    backend = _FakeBackend({"r1": 250, "r3": 260})
+    srv = _server(backend)
+    res = srv.serve(_reqs(5), realtime=False)
     assert [r.rid for r in res] == [0, 1, 2, 3, 4]
     errs = {r.rid: r.error for r in res}
     assert errs[1] and "IMRP_E_NAN" in errs[1]
@@ -128,23 +129,33 @@ def test_server_evicts_failing_requests_and_serves_the_rest():
             assert r.w_res == 0.5
 
 
-def test_server_reraises_errors_of_the_batch_itself():
-    from paper_2111_13072_gb300.inputs import Workload
-    from paper_2111_13072_gb300.serve import SpectrumRequest, SpectrumServer
+def test_requests_progress_independently():
+    """A slow request (its chunks take many polls) does not hold back a fast
+    one: the fast request finishes first although both were admitted together,
+    and both run every step exactly once."""
+    backend = _FakeBackend({}, delays={"r0": 50, "r1": 0})
+    res = _server(backend).serve(_reqs(2), realtime=False)
+    assert res[1].finished < res[0].finished
+    assert [len(r.qdiff) for r in res] == [1000, 1000]
 
-    class Broken(_FakeBatch):
-        def sync(self):
-            self.failed = -1
-            raise _FakeError("IMRP_E_CUDA: sync")
 
+def test_admission_waits_for_memory():
+    """With room for two requests at a time, the third is admitted only once
+    one of the first two has finished and returned its memory."""
     backend = _FakeBackend({})
-    backend.Batch = Broken
-    srv = SpectrumServer(hbm_budget=10 ** 6, chunk=100, backend=backend,
-                         state_fn=lambda w: (np.zeros((w.N, 3)), np.zeros((w.N, 3))))
-    req = SpectrumRequest(0, Workload("r0", N=10, l_max=1, T_e_eV=1.0, n_e_m3=1e15, steps=200), steps=200)
+    srv = _server(backend, budget=2000)
+    res = srv.serve(_reqs(3, steps=300), realtime=False)
+    assert srv.stats["peak_bytes"] <= 2000
+    assert srv.stats["max_active"] == 2
+    assert res[2].admitted >= min(res[0].finished, res[1].finished)
+
+
+def test_server_reraises_errors_that_are_not_one_requests():
+    backend = _FakeBackend({}, broken={"r0"})
+    srv = _server(backend)
     try:
-        srv.serve([req], realtime=False)
+        srv.serve(_reqs(1, steps=200), realtime=False)
     except _FakeError as e:
-        assert "sync" in str(e)
+        assert "launch" in str(e)
     else:
-        raise AssertionError("a batch error must propagate")
+        raise AssertionError("a launch error must propagate")
