@@ -36,7 +36,8 @@ extern "C" {
 #define IMRP_E_INVAL (-1)   /* invalid argument or parameter                     */
 #define IMRP_E_NOMEM (-2)   /* device or host allocation failed                  */
 #define IMRP_E_CUDA (-3)    /* a CUDA call failed (message has the CUDA error)   */
-#define IMRP_E_TIMEOUT (-4) /* a bounded device-side wait gave up                */
+#define IMRP_E_TIMEOUT (-4) /* reserved: no entry point returns it (no kernel of the
+                               path waits on another, so no wait can give up) */
 #define IMRP_E_NAN (-5)     /* a non-finite value appeared in the state          */
 #define IMRP_E_STATE (-6)   /* call out of order (e.g. step before load)         */
 
@@ -153,7 +154,7 @@ int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, i
  * Q_diff(t_n) = -(1/n~) sum_i q_i Psi_anti,L(x_i) (Sec. 4) at the positions
  * x_n used by the step. qdiff_out and uasy_out (host, n_steps doubles each,
  * either may be NULL) receive Q_diff(t_n) and u_asy(t_n).
- * Errors: IMRP_E_STATE (nothing loaded), IMRP_E_TIMEOUT, IMRP_E_NAN, IMRP_E_CUDA. */
+ * Errors: IMRP_E_STATE (nothing loaded), IMRP_E_NAN, IMRP_E_CUDA. */
 int imrp_step(imrp_ctx* ctx, int64_t n_steps, double* qdiff_out, double* uasy_out);
 
 /* As imrp_step without host outputs and without waiting for the GPU: the work
@@ -338,8 +339,10 @@ int imrp_profile_steps(imrp_ctx* ctx, int64_t n_steps, double* ms);
  * denominator of the field kernel, which is FP32 arithmetic rather than a
  * tensor-core contraction; the paper has no counterpart): independent FMA
  * chains on every SM (the SM count is read from the device, *sm_count if not
- * NULL), best of ten timed launches after a warm-up, at whatever clock the
- * device runs. Allocates a few bytes and a stream; takes some tens of ms.
+ * NULL), issued once as scalar FMAs and once as packed pairs (two FMAs per
+ * instruction), best of ten timed launches of each after a warm-up, the larger
+ * of the two, at whatever clock the device runs. Allocates a few bytes and a
+ * stream; takes some tens of ms.
  * Errors: IMRP_E_INVAL (tflops NULL), IMRP_E_NOMEM, IMRP_E_CUDA. */
 int imrp_fp32_peak(double* tflops, int* sm_count);
 

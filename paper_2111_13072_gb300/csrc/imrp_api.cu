@@ -184,7 +184,6 @@ int check_err(imrp_ctx* ctx) {
   if (h) {
     CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
     if (h & kErrNaN) return ctx->fail(IMRP_E_NAN, "non-finite value in the particle state");
-    if (h & kErrTimeout) return ctx->fail(IMRP_E_TIMEOUT, "a device-side wait gave up");
     if (h & kErrRange) return ctx->fail(IMRP_E_INVAL, "a particle lies outside 1 < r < r_out");
   }
   return IMRP_OK;

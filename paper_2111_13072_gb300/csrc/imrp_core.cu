@@ -357,10 +357,39 @@ void launch_state_out(const Part<T>* st, double* x, double* v, int64_t n, cudaSt
 // ============================================================================
 constexpr int kTsTasks = 4;
 
+// Compensated partial sums of the in-group scans. In FP32 every partial sum is
+// the unevaluated pair hi + lo: Knuth's TwoSum gives the rounding error of each
+// addition exactly, which is carried in lo, so a sum over the 1024 particles of
+// a scan group keeps about twice the working precision (the radius-ordered
+// scans are where cancellation sets the accuracy). The results are rounded to
+// FP32 once, the group totals to FP64. In FP64 the sums are plain.
+template <class T> struct CSum { T hi, lo; };
+template <class T> __device__ __forceinline__ CSum<T> cs_add(CSum<T> a, CSum<T> b) {
+  if constexpr (sizeof(T) == 4) {
+    const T s = a.hi + b.hi;
+    const T bb = s - a.hi;
+    const T e = (a.hi - (s - bb)) + (b.hi - bb);  // a.hi + b.hi = s + e exactly
+    const T lo = e + (a.lo + b.lo);
+    const T h = s + lo;
+    return {h, lo - (h - s)};
+  } else {
+    return {a.hi + b.hi, T(0)};
+  }
+}
+template <class T> __device__ __forceinline__ CSum<T> cs_of(T v) { return {v, T(0)}; }
+template <class T> __device__ __forceinline__ CSum<T> cs_shfl_down(CSum<T> v, int d) {
+  return {__shfl_down_sync(0xffffffffu, v.hi, d, 8), __shfl_down_sync(0xffffffffu, v.lo, d, 8)};
+}
+template <class T> __device__ __forceinline__ CSum<T> cs_shfl_up(CSum<T> v, int d) {
+  return {__shfl_up_sync(0xffffffffu, v.hi, d, 8), __shfl_up_sync(0xffffffffu, v.lo, d, 8)};
+}
+template <class T> __device__ __forceinline__ double cs_double(CSum<T> v) { return double(v.hi) + double(v.lo); }
+
 template <class T>
 __global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T* __restrict__ pfx,
                                                    double* __restrict__ gagg, int64_t tw, int64_t ts, int nc) {
   using V4 = typename Vec4<T>::type;
+  using C = CSum<T>;
   const int lane = threadIdx.x & 31, r = lane & 7;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nseg = (tw + 127) / 128;  // 128-tile segments per row
@@ -390,27 +419,29 @@ __global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T*
     const int64_t g = tile / 32;
     V4 o;
     if (u & 1) {  // Is: exclusive suffix
-      const T f2 = v[k].w, f1 = f2 + v[k].z, f0 = f1 + v[k].y, sum = f0 + v[k].x;
-      T x = __shfl_down_sync(0xffffffffu, sum, 1, 8);
-      if (r == 7) x = T(0);
+      const C f2 = cs_of(v[k].w), f1 = cs_add(f2, cs_of(v[k].z)), f0 = cs_add(f1, cs_of(v[k].y)),
+              sum = cs_add(f0, cs_of(v[k].x));
+      C x = cs_shfl_down(sum, 1);
+      if (r == 7) x = cs_of(T(0));
 #pragma unroll
       for (int d = 1; d < 8; d <<= 1) {
-        const T y = __shfl_down_sync(0xffffffffu, x, d, 8);
-        if (r + d < 8) x += y;
+        const C y = cs_shfl_down(x, d);
+        if (r + d < 8) x = cs_add(x, y);
       }
-      o.x = x + f0; o.y = x + f1; o.z = x + f2; o.w = x;
-      if (r == 0 && tile < tw) gagg[g * nc + u] = double(x + sum);
+      o.x = cs_add(x, f0).hi; o.y = cs_add(x, f1).hi; o.z = cs_add(x, f2).hi; o.w = x.hi;
+      if (r == 0 && tile < tw) gagg[g * nc + u] = cs_double(cs_add(x, sum));
     } else {      // Rs: exclusive prefix
-      const T e1 = v[k].x, e2 = e1 + v[k].y, e3 = e2 + v[k].z, sum = e3 + v[k].w;
-      T x = __shfl_up_sync(0xffffffffu, sum, 1, 8);
-      if (r == 0) x = T(0);
+      const C e1 = cs_of(v[k].x), e2 = cs_add(e1, cs_of(v[k].y)), e3 = cs_add(e2, cs_of(v[k].z)),
+              sum = cs_add(e3, cs_of(v[k].w));
+      C x = cs_shfl_up(sum, 1);
+      if (r == 0) x = cs_of(T(0));
 #pragma unroll
       for (int d = 1; d < 8; d <<= 1) {
-        const T y = __shfl_up_sync(0xffffffffu, x, d, 8);
-        if (r >= d) x += y;
+        const C y = cs_shfl_up(x, d);
+        if (r >= d) x = cs_add(x, y);
       }
-      o.x = x; o.y = x + e1; o.z = x + e2; o.w = x + e3;
-      if (r == 7 && tile < tw) gagg[g * nc + u] = double(x + sum);
+      o.x = x.hi; o.y = cs_add(x, e1).hi; o.z = cs_add(x, e2).hi; o.w = cs_add(x, e3).hi;
+      if (r == 7 && tile < tw) gagg[g * nc + u] = cs_double(cs_add(x, sum));
     }
     if (tile < tw) *reinterpret_cast<V4*>(pfx + u * ts + tile) = o;
     if (++sg == nseg) { sg = 0; ++u; }

@@ -61,7 +61,7 @@ struct StepState {
 };
 
 // Device error flags (bitwise or).
-enum : int { kErrNaN = 1, kErrTimeout = 2, kErrRange = 4 };
+enum : int { kErrNaN = 1, kErrRange = 4 };
 
 template <class T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
