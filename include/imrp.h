@@ -306,6 +306,25 @@ int imrp_drude_te(double nu_eff_wpe, double K, double R_m, double n_e_m3, double
 int imrp_sheath_solve(double lambda, double mass_ratio, double r_out, int64_t n_grid, double* psi,
                       double* dpsi, double* q_ion, double* q_elec, double* out);
 
+/* Mobile ions. The paper moves its ions as super-particles, like the
+ * electrons (Sec. 4: 1e6 super-particles including ions). After this call the
+ * particles whose id (their index in the loaded arrays) is at least n_electrons
+ * are ions of charge ion_charge (in e, > 0) and mass ion_mass (in m_e, > 0);
+ * the others are electrons (q = -1, m = 1). They enter the moments and the
+ * pair sums with their charge, the l = 0 term takes the charge inside each
+ * particle's radius from a scan of the charges, the push scales by q/m, the
+ * walls treat both alike, and collisions act on electrons only. n~ counts the
+ * electrons (n_electrons per shell volume, or per the profile's electron
+ * charge), and the immobile uniform background keeps background_ions ion
+ * super-particles (0 when every ion moves; a profile of imrp_set_ion_profile
+ * still applies as given). ion_charge = 0 restores all electrons and the
+ * default background (as many ions as particles). Takes effect for the next
+ * steps and loads; allocates a few FP64 arrays of the tile count on the first
+ * call. Errors: IMRP_E_INVAL (n_electrons outside [1, N], non-positive or
+ * non-finite charge or mass, negative background, wall_rule 2), IMRP_E_CUDA. */
+int imrp_set_species(imrp_ctx* ctx, int64_t n_electrons, double ion_charge, double ion_mass,
+                     double background_ions);
+
 /* Replaces the context's uniform immobile ion background by a radial ion
  * profile, e.g. the equilibrium of imrp_sheath_solve (App. D: the simulation
  * starts from that equilibrium). q_ion[k] (host array of n_tab >= 2, copied)

@@ -103,6 +103,13 @@ struct imrp_ctx {
   int64_t ion_cap = 0;
   double ion_qe = 0.0;        // electron charge the loaded particles represent
   double ion_qs = 0.0;        // surface charge, units e n_inf R^3
+  // mobile ions (imrp_set_species): ids >= sp_ne are ions of charge sp_q (e) and mass sp_m (m_e)
+  int species = 0;
+  int64_t sp_ne = 0;
+  double sp_q = 0.0, sp_m = 0.0, sp_bg = 0.0;  // sp_bg: ions of the immobile uniform background
+  double *qtile = nullptr, *qpfx = nullptr, *qgagg = nullptr, *qgbase = nullptr, *qtot = nullptr,
+         *qtotd = nullptr, *qwork = nullptr;
+  unsigned* qticket = nullptr;
 
   int fail(int code, const char* fmt, ...) {
     char b[512];
@@ -140,9 +147,12 @@ void drop_graphs(imrp_ctx* c) {
 // Super-particles per unit cube at density n_inf: N over the shell volume
 // for the uniform start, N over the electron charge of the given profile.
 double n_tilde_of(const imrp_ctx* c, int64_t n) {
-  if (c->ion_n) return double(n) / c->ion_qe;
-  return double(n) / (4.0 * kPi / 3.0 * (c->r_out * c->r_out * c->r_out - 1.0));
+  const int64_t ne = c->species ? std::min<int64_t>(c->sp_ne, n) : n;  // electron super-particles
+  if (c->ion_n) return double(ne) / c->ion_qe;
+  return double(ne) / (4.0 * kPi / 3.0 * (c->r_out * c->r_out * c->r_out - 1.0));
 }
+// Ion super-particles of the immobile uniform background after a load of n.
+double n_ion_of(const imrp_ctx* c, int64_t n) { return c->species ? c->sp_bg : double(n); }
 
 void free_all(imrp_ctx* c) {
   drop_graphs(c);
@@ -157,6 +167,12 @@ void free_all(imrp_ctx* c) {
   for (void* p : ps) cudaFree(p);
   cudaFree(c->ion_q);
   c->ion_q = nullptr;
+  {
+    void* qs[] = {c->qtile, c->qpfx, c->qgagg, c->qgbase, c->qtot, c->qtotd, c->qwork, c->qticket};
+    for (void* q : qs) cudaFree(q);
+    c->qtile = c->qpfx = c->qgagg = c->qgbase = c->qtot = c->qtotd = c->qwork = nullptr;
+    c->qticket = nullptr;
+  }
   c->ion_n = c->ion_cap = 0;
   c->key0 = c->idx0 = c->key1 = c->idx1 = c->hist = nullptr;
   c->agg = c->pfx = c->gbase = c->tot = c->eout = nullptr;
@@ -231,9 +247,20 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   ma.rho = T(ctx->r_out);
   ma.rho_inv = T(1.0 / ctx->r_out);
   ma.agg = static_cast<T*>(ctx->agg);
+  ma.species = ctx->species;
+  ma.n_e = uint32_t(std::min<int64_t>(ctx->sp_ne, int64_t(UINT32_MAX)));
+  ma.q_ion = T(ctx->sp_q);
+  ma.id = ctx->srt_id;
+  ma.qtile = ctx->qtile;
   if (ev) cudaEventRecord(ev[2], s);
   ks->moments(ma, s);
   if (ev) cudaEventRecord(ev[3], s);
+  if (ctx->species) {
+    // the charge inside each particle's radius: a scan of the tiles' charges (FP64)
+    launch_tile_scan<double>(ctx->qtile, ctx->qpfx, ctx->qgagg, ctx->ntiles, 1, s);
+    launch_group_scan<double>(ctx->qgagg, ctx->qwork, ctx->qticket, ctx->qgbase, ctx->qtot, ctx->qtotd,
+                              ctx->ngroups, 1, ctx->gseg, s);
+  }
   launch_tile_scan<T>(static_cast<T*>(ctx->agg), static_cast<T*>(ctx->pfx), ctx->gagg, ctx->ntiles, ctx->nc, s);
   launch_group_scan<T>(ctx->gagg, ctx->gswork, ctx->gsticket, static_cast<T*>(ctx->gbase),
                        static_cast<T*>(ctx->tot), ctx->totd, ctx->ngroups, ctx->nc, ctx->gseg, s);
@@ -290,6 +317,12 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   a.sigma_v = ctx->lambda_D;
   a.self_image = ctx->p.self_image;
   a.m0_only = ctx->p.m0_only;
+  a.species = ctx->species;
+  a.n_e = uint32_t(std::min<int64_t>(ctx->sp_ne, int64_t(UINT32_MAX)));
+  a.q_ion = T(ctx->sp_q);
+  a.qm_ion = T(ctx->species ? ctx->sp_q / ctx->sp_m : 0.0);
+  a.qpfx = ctx->qpfx;
+  a.qgbase = ctx->qgbase;
   a.coll_thr = coll_threshold(ctx->p.nu_coll, ctx->p.dt);
   a.seed = ctx->p.seed;
   double rl = 1.0;
@@ -540,6 +573,46 @@ int imrp_set_stream(imrp_ctx* ctx, void* stream) {
   return IMRP_OK;
 }
 
+int imrp_set_species(imrp_ctx* ctx, int64_t n_electrons, double ion_charge, double ion_mass,
+                     double background_ions) {
+  if (!ctx) return IMRP_E_INVAL;
+  if (ion_charge == 0.0) {  // all electrons again
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->species = 0;
+  } else {
+    if (!(ion_charge > 0.0) || !std::isfinite(ion_charge) || !(ion_mass > 0.0) || !std::isfinite(ion_mass) ||
+        !(background_ions >= 0.0) || !std::isfinite(background_ions) || n_electrons < 1 || n_electrons > ctx->cap)
+      return ctx->fail(IMRP_E_INVAL, "set_species: n_electrons %lld, ion charge %g, mass %g, background %g",
+                       (long long)n_electrons, ion_charge, ion_mass, background_ions);
+    if (ctx->p.wall_rule == 2)
+      return ctx->fail(IMRP_E_INVAL, "set_species: mobile ions with the absorbing wall are not supported");
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->qtile) {
+      const int64_t nt = (ctx->cap + 31) / 32, ng = (nt + kTilesPerGroup - 1) / kTilesPerGroup;
+      CK(cudaMalloc(&ctx->qtile, tile_stride(nt) * sizeof(double)));
+      CK(cudaMalloc(&ctx->qpfx, tile_stride(nt) * sizeof(double)));
+      CK(cudaMalloc(&ctx->qgagg, ng * sizeof(double)));
+      CK(cudaMalloc(&ctx->qgbase, ng * sizeof(double)));
+      CK(cudaMalloc(&ctx->qtot, sizeof(double)));
+      CK(cudaMalloc(&ctx->qtotd, sizeof(double)));
+      CK(cudaMalloc(&ctx->qwork, gs_work_doubles(1) * sizeof(double)));
+      CK(cudaMalloc(&ctx->qticket, gs_col_blocks(1) * sizeof(unsigned)));
+      CK(cudaMemset(ctx->qticket, 0, gs_col_blocks(1) * sizeof(unsigned)));
+    }
+    ctx->species = 1;
+    ctx->sp_ne = n_electrons;
+    ctx->sp_q = ion_charge;
+    ctx->sp_m = ion_mass;
+    ctx->sp_bg = background_ions;
+  }
+  if (ctx->loaded) {
+    ctx->n_tilde = n_tilde_of(ctx, ctx->n);
+    ctx->n_ion = n_ion_of(ctx, ctx->n);
+  }
+  drop_graphs(ctx);  // the captured steps hold the old arguments
+  return IMRP_OK;
+}
+
 int imrp_set_ion_profile(imrp_ctx* ctx, const double* q_ion, int64_t n_tab, double q_elec_total,
                          double q_s) {
   if (!ctx) return IMRP_E_INVAL;
@@ -604,7 +677,7 @@ int imrp_load_particles(imrp_ctx* ctx, const double* x, const double* v, int64_t
   if (rc) { ctx->loaded = false; return rc; }
   ctx->n = n;
   ctx->n_tilde = n_tilde_of(ctx, n);
-  ctx->n_ion = double(n);
+  ctx->n_ion = n_ion_of(ctx, n);
   ctx->ntiles = (n + 31) / 32;
   ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   ctx->host_step = 0;
@@ -689,7 +762,7 @@ int imrp_load_particles_async(imrp_ctx* ctx, const double* x, const double* v, i
   ctx->cur = 0;
   ctx->n = n;
   ctx->n_tilde = n_tilde_of(ctx, n);
-  ctx->n_ion = double(n);
+  ctx->n_ion = n_ion_of(ctx, n);
   ctx->ntiles = (n + 31) / 32;
   ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   ctx->host_step = 0;
@@ -823,7 +896,7 @@ int imrp_restore(imrp_ctx* ctx, const double* x, const double* v, const uint32_t
   if (rc) { ctx->loaded = false; return rc; }
   ctx->n = n;
   ctx->n_tilde = n_tilde_of(ctx, n);
-  ctx->n_ion = double(n);
+  ctx->n_ion = n_ion_of(ctx, n);
   ctx->ntiles = (n + 31) / 32;
   ctx->ngroups = (ctx->ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   ctx->host_step = step;

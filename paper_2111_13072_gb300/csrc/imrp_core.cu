@@ -358,24 +358,24 @@ void launch_state_out(const Part<T>* st, double* x, double* v, int64_t n, cudaSt
 constexpr int kTsTasks = 4;
 
 // Compensated partial sums of the in-group scans. In FP32 every partial sum is
-// the unevaluated pair hi + lo: Knuth's TwoSum gives the rounding error of each
-// addition exactly, which is carried in lo, so a sum over the 1024 particles of
-// a scan group keeps about twice the working precision (the radius-ordered
-// scans are where cancellation sets the accuracy). The results are rounded to
-// FP32 once, the group totals to FP64. In FP64 the sums are plain.
+// the unevaluated pair hi + lo: hi is the plain running sum and lo collects the
+// rounding error of every addition, which Knuth's TwoSum gives exactly, so a
+// sum over the 1024 particles of a scan group keeps about twice the working
+// precision (the radius-ordered scans are where cancellation sets the
+// accuracy). The results are rounded to FP32 once (hi + lo), the group totals
+// to FP64. In FP64 the sums are plain.
 template <class T> struct CSum { T hi, lo; };
 template <class T> __device__ __forceinline__ CSum<T> cs_add(CSum<T> a, CSum<T> b) {
   if constexpr (sizeof(T) == 4) {
     const T s = a.hi + b.hi;
     const T bb = s - a.hi;
     const T e = (a.hi - (s - bb)) + (b.hi - bb);  // a.hi + b.hi = s + e exactly
-    const T lo = e + (a.lo + b.lo);
-    const T h = s + lo;
-    return {h, lo - (h - s)};
+    return {s, (a.lo + b.lo) + e};
   } else {
     return {a.hi + b.hi, T(0)};
   }
 }
+template <class T> __device__ __forceinline__ T cs_round(CSum<T> v) { return v.hi + v.lo; }
 template <class T> __device__ __forceinline__ CSum<T> cs_of(T v) { return {v, T(0)}; }
 template <class T> __device__ __forceinline__ CSum<T> cs_shfl_down(CSum<T> v, int d) {
   return {__shfl_down_sync(0xffffffffu, v.hi, d, 8), __shfl_down_sync(0xffffffffu, v.lo, d, 8)};
@@ -428,7 +428,8 @@ __global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T*
         const C y = cs_shfl_down(x, d);
         if (r + d < 8) x = cs_add(x, y);
       }
-      o.x = cs_add(x, f0).hi; o.y = cs_add(x, f1).hi; o.z = cs_add(x, f2).hi; o.w = x.hi;
+      o.x = cs_round(cs_add(x, f0)); o.y = cs_round(cs_add(x, f1)); o.z = cs_round(cs_add(x, f2));
+      o.w = cs_round(x);
       if (r == 0 && tile < tw) gagg[g * nc + u] = cs_double(cs_add(x, sum));
     } else {      // Rs: exclusive prefix
       const C e1 = cs_of(v[k].x), e2 = cs_add(e1, cs_of(v[k].y)), e3 = cs_add(e2, cs_of(v[k].z)),
@@ -440,7 +441,8 @@ __global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T*
         const C y = cs_shfl_up(x, d);
         if (r >= d) x = cs_add(x, y);
       }
-      o.x = x.hi; o.y = cs_add(x, e1).hi; o.z = cs_add(x, e2).hi; o.w = cs_add(x, e3).hi;
+      o.x = cs_round(x); o.y = cs_round(cs_add(x, e1)); o.z = cs_round(cs_add(x, e2));
+      o.w = cs_round(cs_add(x, e3));
       if (r == 7 && tile < tw) gagg[g * nc + u] = cs_double(cs_add(x, sum));
     }
     if (tile < tw) *reinterpret_cast<V4*>(pfx + u * ts + tile) = o;

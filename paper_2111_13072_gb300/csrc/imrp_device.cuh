@@ -214,6 +214,13 @@ template <class T> struct MomArgs {
   T rho;       // r_out
   T rho_inv;   // 1 / r_out: regular harmonics use x / r_out so |Rs| <= 1
   T* agg;      // [2 ncomp(L)][ntiles] tile sums, u = 2 e + s (s = 0 Rs, s = 1 Is)
+  // mobile ions (species = 1): particles with id >= n_e have charge q_ion,
+  // the others -1; qtile[tile] receives each tile's charge (FP64)
+  int species;
+  uint32_t n_e;
+  T q_ion;
+  const uint32_t* id;
+  double* qtile;
 };
 
 // Entry tables of the gradient coefficients held in shared memory per warp.
@@ -262,6 +269,15 @@ template <class T> struct FieldArgs {
   double sigma_v;     // thermal speed of the injected plasma (lambda_D / R)
   int self_image;
   int m0_only;        // 1: keep only the m = 0 terms of every degree (the paper's truncation)
+  // mobile ions (species = 1): ids >= n_e are ions of charge q_ion and charge
+  // to mass ratio qm_ion; the inner charge of the l = 0 term is then the
+  // scanned charge of the particles inside: qgbase[group] + qpfx[tile] + the
+  // charges of the lower lanes of the tile (FP64)
+  int species;
+  uint32_t n_e;
+  T q_ion, qm_ion;
+  const double* qpfx;
+  const double* qgbase;
   uint32_t coll_thr;  // collision when the top 24 bits of a Philox word are below this (0: none)
   uint64_t seed;
   T f[kTabL];         // f_l of App. A

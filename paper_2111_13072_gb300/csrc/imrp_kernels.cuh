@@ -116,13 +116,23 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
     const T r2 = X * X + Y * Y + Z * Z;
     sx[o] = X * ri; sy[o] = Y * ri; sz[o] = Z * ri;
     sq[o] = a.rho / r2;
-    sRr[o] = valid ? T(-1) : T(0);
+    // the particle's charge seeds its harmonics: -1 for an electron, q_ion
+    // for a mobile ion
+    sRr[o] = valid ? ((a.species && a.id[j] >= a.n_e) ? a.q_ion : T(-1)) : T(0);
     sRi[o] = T(0);
     ssc[o] = rsqrt_t(r2);
   }
   __syncthreads();
   const bool odd = (th & 1) != 0;
   const int64_t tile = int64_t(blockIdx.x) * (kMomThreads / 2) + (th >> 1);
+  if (a.species) {
+    // the tile's charge (FP64): this thread's 16 particles, then its pair
+    double qs = 0.0;
+#pragma unroll
+    for (int p = 0; p < kMomPPT; ++p) qs += double(sRr[p * S + th]);
+    qs += __shfl_xor_sync(0xffffffffu, qs, 1);
+    if (!odd) a.qtile[tile] = qs;
+  }
   // every tile of the whole groups is written (tiles past the particles hold
   // zeros: their particles carry no charge)
   const int64_t ts = tile_stride(ntiles);
@@ -258,6 +268,9 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
   T VX = T(0), VY = T(0), VZ = T(0);
   if (a.mode == 0 && valid) { VX = a.vx[j]; VY = a.vy[j]; VZ = a.vz[j]; }
+  // mobile ions: ids from n_e on are ions; qneg = -q (1 for an electron), 0 on an empty lane
+  const bool is_ion = a.species && valid && a.id[j] >= a.n_e;
+  const T qneg = valid ? (is_ion ? -a.q_ion : T(1)) : T(0);
 
   // ---- phase 1: cI (coefficients of Is, s = 0) and cR (of Rs(x/r_out), s = 1).
   // The loop has a fixed trip count and is unrolled, so that all loads of the
@@ -551,8 +564,11 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   {
     const T rk = r2 * ir;
     const T ex = X * ir, ey = Y * ir, ez = Z * ir;
-    T Nx = T(0), Ny = T(0), Nz = T(0);  // sum of grad phi (phi = sum_l r_<^l/r_>^{l+1} P_l)
-    const T vmask = valid ? T(1) : T(0);
+    T Nx = T(0), Ny = T(0), Nz = T(0);  // sum of grad phi (phi = sum_l r_<^l/r_>^{l+1} P_l), weighted by -q
+    // -q of this particle (1 for an electron), 0 for the empty lanes of a
+    // ragged tile: a partner's contribution to my field is weighted by its
+    // -q (pm), mine to the partner's by vmask
+    const T vmask = qneg;
 #pragma unroll 1
     for (int s = 1; s <= 16 && !a.m0_only; ++s) {
       const int src = (lane + s) & 31;
@@ -585,17 +601,16 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       // (S1 r^_i + S2 (r^_o - u r^_i)) / (r_i r_o), at the outer end
       // (-(S0 + S1) r^_o + S2 (r^_i - u r^_o)) / r_o^2; radial (r) and angular
       // (a) factors of my end and of the partner's, with the validity mask
-      const T w = pm * vmask;
-      const T wab = w * ir * pir;                          // w / (r_i r_o)
-      const T wo2 = w * (me_inner ? pir * pir : ir * ir);  // w / r_o^2
-      const T in_r = S1 * wab, in_a = S2 * wab;
-      const T out_r = -(S0 + S1) * wo2, out_a = S2 * wo2;
-      const T mr = me_inner ? in_r : out_r, ma = me_inner ? in_a : out_a;
+      const T gab = ir * pir;                          // 1 / (r_i r_o)
+      const T go2 = me_inner ? pir * pir : ir * ir;    // 1 / r_o^2
+      const T in_r = S1 * gab, in_a = S2 * gab;
+      const T out_r = -(S0 + S1) * go2, out_a = S2 * go2;
+      const T mr = (me_inner ? in_r : out_r) * pm, ma = (me_inner ? in_a : out_a) * pm;
       Nx += mr * ex + ma * (pex - uu * ex);
       Ny += mr * ey + ma * (pey - uu * ey);
       Nz += mr * ez + ma * (pez - uu * ez);
       if (s < 16) {
-        const T pr = me_inner ? out_r : in_r, pa = me_inner ? out_a : in_a;
+        const T pr = (me_inner ? out_r : in_r) * vmask, pa = (me_inner ? out_a : in_a) * vmask;
         const T tx = pr * pex + pa * (ex - uu * pex), ty = pr * pey + pa * (ey - uu * pey),
                 tz = pr * pez + pa * (ez - uu * pez);
         const int dst = (lane - s) & 31;
@@ -648,11 +663,10 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
               ogz = go * xoz + C1 * iro * (T(1) - uo * xoz);
       const T igx = gi * xix - C2 * iri * ui * xix, igy = gi * xiy - C2 * iri * ui * xiy,
               igz = gi * xiz + C2 * iri * (T(1) - ui * xiz);
-      const T w = pm * vmask;
-      Nx += w * (me_inner ? igx : ogx); Ny += w * (me_inner ? igy : ogy); Nz += w * (me_inner ? igz : ogz);
+      Nx += pm * (me_inner ? igx : ogx); Ny += pm * (me_inner ? igy : ogy); Nz += pm * (me_inner ? igz : ogz);
       if (s < 16) {
-        const T tx = w * (me_inner ? ogx : igx), ty = w * (me_inner ? ogy : igy),
-                tz = w * (me_inner ? ogz : igz);
+        const T tx = vmask * (me_inner ? ogx : igx), ty = vmask * (me_inner ? ogy : igy),
+                tz = vmask * (me_inner ? ogz : igz);
         const int dst = (lane - s) & 31;
         Nx += __shfl_sync(0xffffffffu, tx, dst);
         Ny += __shfl_sync(0xffffffffu, ty, dst);
@@ -696,14 +710,13 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
           hr += T(l + 1) * wgt * P;
           ha += wgt * D;
         }
-        const T w = pm * vmask;
-        Gx += w * (hr * ex - ha * (dx - uu * ex));
-        Gy += w * (hr * ey - ha * (dy - uu * ey));
-        Gz += w * (hr * ez - ha * (dz - uu * ez));
+        Gx += pm * (hr * ex - ha * (dx - uu * ex));
+        Gy += pm * (hr * ey - ha * (dy - uu * ey));
+        Gz += pm * (hr * ez - ha * (dz - uu * ez));
       }
       Nx += ir * Gx; Ny += ir * Gy; Nz += ir * Gz;
     }
-    // E = -pf sum_i q_i grad phi = +pf grad phi (q_i = -1)
+    // E = -pf sum_i q_i grad phi (N holds the sum weighted by -q_i)
     const T pfT = T(a.pf);
     Ex += pfT * Nx; Ey += pfT * Ny; Ez += pfT * Nz;
   }
@@ -738,7 +751,19 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
     } else {
       qion = a.ion_coef * (r2d * rd - 1.0);
     }
-    const double qin = qion + (q_s - double(j));
+    double qmob;  // charge of the mobile particles inside (sorted before this one)
+    if (a.species) {
+      double qc = valid ? -double(qneg) : 0.0, incl = qc;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (int(lane) >= d) incl += t;
+      }
+      qmob = a.qgbase[g] + a.qpfx[tile] + (incl - qc);
+    } else {
+      qmob = -double(j);  // j electrons inside
+    }
+    const double qin = qion + (q_s + qmob);
     const T er = T(qin) * (T(a.pf) * ir2 * ir);  // multiplies x (gives r^ / r^2)
     Ex += er * X; Ey += er * Y; Ez += er * Z;
     const int self_sign = img_in_tile ? (a.self_image ? 1 : 0) : (a.self_image ? 0 : -1);
@@ -758,7 +783,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
         hr += a.f[l] * T(l + 1) * P * P * rp;
         ha += a.f[l] * P * D * rp;
       }
-      const T pfT = T(self_sign * a.pf);
+      const T pfT = T(self_sign * a.pf) * qneg;
       // r^ = x / r, z^ - u r^ = (0, 0, 1) - u x / r
       Ex += pfT * (hr * X * ir + ha * u * X * ir);
       Ey += pfT * (hr * Y * ir + ha * u * Y * ir);
@@ -768,7 +793,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       T h = T(0);
 #pragma unroll
       for (int l = L; l >= 1; --l) h = h * ir2 + a.f[l] * T(l + 1);
-      const T es = T(self_sign * a.pf) * h * ir2 * ir2 * ir2;  // r^{-(2l+3)} r^ = ir2^{l-1} ir2^3 x
+      const T es = T(self_sign * a.pf) * qneg * h * ir2 * ir2 * ir2;  // r^{-(2l+3)} r^ = ir2^{l-1} ir2^3 x
       Ex += es * X; Ey += es * Y; Ez += es * Z;
     }
   }
@@ -783,8 +808,13 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   }
   if (!valid) return;
 
-  // ---- leapfrog: v += kick (q/m) E with q/m = -1; x += dt v
-  VX -= kick * Ex; VY -= kick * Ey; VZ -= kick * Ez;
+  // ---- leapfrog: v += kick (q/m) E (q/m = -1 for an electron); x += dt v
+  if (is_ion) {
+    const T kq = kick * a.qm_ion;
+    VX += kq * Ex; VY += kq * Ey; VZ += kq * Ez;
+  } else {
+    VX -= kick * Ex; VY -= kick * Ey; VZ -= kick * Ez;
+  }
   X += a.dt * VX; Y += a.dt * VY; Z += a.dt * VZ;
 
   // ---- walls (Sec. 4): mirror the radius back, keep the speed
@@ -843,7 +873,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
       }
       rr = double(X) * double(X) + double(Y) * double(Y) + double(Z) * double(Z);
     }
-    if (a.coll_thr != 0u) {
+    if (a.coll_thr != 0u && !is_ion) {
       // electron-neutral collision: isotropic elastic scattering with
       // probability 1 - exp(-nu dt) (Philox counter (step, step >> 32, id,
       // 0x434F4C4C), key = seed; top 24 bits below the threshold)

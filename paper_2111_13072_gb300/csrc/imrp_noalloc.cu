@@ -159,6 +159,7 @@ int run(const imrp_params* p, const double* x, int64_t n, int64_t step, double* 
                     static_cast<uint32_t*>(P(o.hist)), n, sort_first_byte(sizeof(T) == 4 ? 1 : 0), s);
   launch_reorder<T>(st0, st1, id1, perm, n, s);
   MomArgs<T> ma;
+  memset(&ma, 0, sizeof(ma));  // all electrons (species = 0)
   ma.x = st1[0]; ma.y = st1[1]; ma.z = st1[2];
   ma.n = n;
   ma.rho = T(r_out);

@@ -25,7 +25,7 @@ EXPORTS = [
     "imrp_load_particles_async", "imrp_copy_qdiff_async", "imrp_drude_fit", "imrp_drude_k",
     "imrp_drude_te", "imrp_admittance", "imrp_fit_damped_sine", "imrp_sheath_solve",
     "imrp_set_ion_profile", "imrp_checkpoint", "imrp_restore", "imrp_batch_failed",
-    "imrp_get_surface_charge", "imrp_fp32_peak", "imrp_ready",
+    "imrp_get_surface_charge", "imrp_fp32_peak", "imrp_ready", "imrp_set_species",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH):
     L.imrp_get_surface_charge.argtypes = [c_void_p, pd, P(ctypes.c_int64)]
     L.imrp_fp32_peak.argtypes = [pd, P(ctypes.c_int)]
     L.imrp_ready.argtypes = [c_void_p, P(ctypes.c_int)]
+    L.imrp_set_species.argtypes = [c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     for name in EXPORTS:
         if name not in ("imrp_default_params", "imrp_last_error", "imrp_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -412,6 +413,11 @@ class Sim:
         x, v = np.zeros((n, 3)), np.zeros((n, 3))
         self._check(self._lib.imrp_get_particles(self._h, _ptr(x), _ptr(v)))
         return x, v
+
+    def set_species(self, n_electrons: int, ion_charge: float, ion_mass: float, background_ions: float = 0.0):
+        """imrp_set_species: particles with id >= n_electrons are mobile ions."""
+        self._check(self._lib.imrp_set_species(self._h, int(n_electrons), float(ion_charge), float(ion_mass),
+                                               float(background_ions)))
 
     def ready(self) -> bool:
         """imrp_ready: True when the context's queued work has finished (no wait)."""
