@@ -42,8 +42,9 @@
  *       Legendre polynomials; the gradient is taken by forward-mode dual
  *       numbers, so no derivative formula is written by hand.
  *   (b) orc_field_scan: the same sum regrouped by radius order (particles
- *       sorted by (r, id)); prefix and suffix sums of unnormalised complex
- *       solid harmonics r^l P_l^m e^{im phi}/(l+m)! and
+ *       sorted by (r, id)); prefix sums (from the innermost particle out) and
+ *       suffix sums (from the outermost in) of unnormalised complex solid
+ *       harmonics r^l P_l^m e^{im phi}/(l+m)! and
  *       (l-m)! P_l^m e^{im phi}/r^{l+1}; gradients again by dual numbers.
  *       It is pinned against (a).
  */
@@ -513,14 +514,12 @@ void orc_field_scan(const orc_field_params *p, int64_t n, const double *x, const
   qsort(ord, n, sizeof(orc_key), orc_key_cmp);
 
   cplx *A = calloc(nt, sizeof(cplx));    /* prefix of q M over inner particles   */
-  cplx *Pn = calloc(nt, sizeof(cplx));   /* prefix of q N over inner particles   */
-  cplx *Wn = calloc(nt, sizeof(cplx));   /* total of q N                          */
+  cplx *B = calloc(nt, sizeof(cplx));    /* suffix of q N over outer particles   */
   cplx *Wim = calloc(nt, sizeof(cplx));  /* total of q M(x_i)/r_i^{2l+1} (image)  */
-  cplx *B = calloc(nt, sizeof(cplx));
   cplx *Wk = calloc(nt, sizeof(cplx));
   cdual *Mh = malloc(sizeof(cdual) * nt), *Nh = malloc(sizeof(cdual) * nt);
 
-  /* totals */
+  /* totals of the image moments */
   for (int64_t j = 0; j < n; ++j) {
     const double *xi = x + 3 * ord[j].idx;
     dual X, Y, Z;
@@ -532,12 +531,12 @@ void orc_field_scan(const orc_field_params *p, int64_t n, const double *x, const
       double sc = pow(ri, -(2 * l + 1));
       for (int m = 0; m <= l; ++m) {
         int q = l * (l + 1) / 2 + m;
-        Wn[q].re += qj * Nh[q].re.v; Wn[q].im += qj * Nh[q].im.v;
         Wim[q].re += qj * Mh[q].re.v * sc; Wim[q].im += qj * Mh[q].im.v * sc;
       }
     }
   }
-  /* scan in (r, id) order */
+  /* inner particles, the image and l = 0, in (r, id) order; the prefix A is
+   * summed from the innermost outwards */
   for (int64_t j = 0; j < n; ++j) {
     int64_t k = ord[j].idx;
     const double *xk = x + 3 * k;
@@ -546,11 +545,6 @@ void orc_field_scan(const orc_field_params *p, int64_t n, const double *x, const
     orc_point(xk, &X, &Y, &Z);
     orc_solid(L, X, Y, Z, Mh, Nh);
     const double qk = orc_q(p, k);
-    /* suffix over outer particles = total - inclusive prefix */
-    for (int q = 0; q < nt; ++q) {
-      B[q].re = Wn[q].re - Pn[q].re - qk * Nh[q].re.v;
-      B[q].im = Wn[q].im - Pn[q].im - qk * Nh[q].im.v;
-    }
     /* image moments without particle k unless it feels its own image */
     for (int l = 0; l <= L; ++l) {
       double sc = pow(rk, -(2 * l + 1));
@@ -562,7 +556,6 @@ void orc_field_scan(const orc_field_params *p, int64_t n, const double *x, const
     }
     /* 4 pi * potential (without the 1/n~) as a function of the field point */
     dual phi = orc_contract(L, p->m0_only, A, Nh, 1, NULL);
-    phi = dadd(phi, orc_contract(L, p->m0_only, B, Mh, 1, NULL));
     phi = dadd(phi, orc_contract(L, p->m0_only, Wk, Nh, 1, negf));
     /* l = 0: inner charge A_00 times 1/r; outer charges give a constant */
     phi = dadd(phi, dscale(Nh[0].re, A[0].re));
@@ -572,10 +565,25 @@ void orc_field_scan(const orc_field_params *p, int64_t n, const double *x, const
     orc_external_field(p, canti, u, xk, Ek);
     for (int q = 0; q < nt; ++q) {
       A[q].re += qk * Mh[q].re.v; A[q].im += qk * Mh[q].im.v;
-      Pn[q].re += qk * Nh[q].re.v; Pn[q].im += qk * Nh[q].im.v;
     }
   }
-  free(A); free(Pn); free(Wn); free(Wim); free(B); free(Wk); free(Mh); free(Nh); free(ord);
+  /* outer particles, in reverse order: the suffix B is summed from the
+   * outermost inwards (as total minus prefix it would cancel: at high l the
+   * inner particles' r^-(l+1) outweigh the outer ones' by orders of magnitude) */
+  for (int64_t j = n - 1; j >= 0; --j) {
+    int64_t k = ord[j].idx;
+    dual X, Y, Z;
+    orc_point(x + 3 * k, &X, &Y, &Z);
+    orc_solid(L, X, Y, Z, Mh, Nh);
+    const double qk = orc_q(p, k);
+    dual phi = orc_contract(L, p->m0_only, B, Mh, 1, NULL);
+    double *Ek = E + 3 * k;
+    for (int c = 0; c < 3; ++c) Ek[c] -= phi.d[c] / (4.0 * ORC_PI * p->n_tilde);
+    for (int q = 0; q < nt; ++q) {
+      B[q].re += qk * Nh[q].re.v; B[q].im += qk * Nh[q].im.v;
+    }
+  }
+  free(A); free(B); free(Wim); free(Wk); free(Mh); free(Nh); free(ord);
 }
 
 /* ------------------------------------------------------------------ */

@@ -167,6 +167,22 @@ def test_scan_matches_brute_force(n, L, m0, si, qs, u):
     np.testing.assert_array_equal(oracle.field_brute(p, x, u=u, sample=sample), Eb[sample])
 
 
+@pytest.mark.parametrize("L,r_out", [(16, 5.2), (24, 3.5)])
+def test_scan_matches_brute_force_per_particle_wide_shell(L, r_out):
+    """A wide shell at a high degree: the outermost particles' suffix moments
+    are about (1 / r_out)^(l+1) of the totals (5^-17 here), so a suffix formed
+    as total minus prefix would lose five digits; summed from the outside in,
+    the scan matches the pair sum for every particle to 1e-11 (relative to the
+    particle's own field)."""
+    n = 1200
+    x, _ = maxwellian_shell(n, r_out, 0.05, seed=7)
+    p = _shell_params(n, L, r_out=r_out, self_image=1)
+    Eb = oracle.field_brute(p, x)
+    Es = oracle.field_scan(p, x)
+    err = np.linalg.norm(Es - Eb, axis=1) / np.linalg.norm(Eb, axis=1)
+    assert err.max() < 1e-11, err.max()
+
+
 def test_neutral_shell_monopole_cancels():
     """Uniform electrons over the same shell as the uniform ion background:
     the l = 0 fields cancel up to sqrt(N) fluctuations (a wrong sign or scale of
