@@ -378,9 +378,14 @@ int imrp_fp32_peak(double* tflops, int* sm_count);
 int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* gseg_out);
 
 /* A batch steps several loaded contexts of one device together: every step of
- * every context is captured into one CUDA graph (each context on its own
- * stream, forked from and joined to the batch's stream), replayed per pair of
- * steps, so that instances of uneven N overlap on the GPU. The batch does not
+ * every context is captured into one CUDA graph, replayed per pair of steps.
+ * Within a step, each context sorts and reorders on its own stream (forked
+ * from and joined to the batch's stream); then the moments of all contexts of
+ * one degree and precision run as one launch over a work list of (context,
+ * block of 1024 particles); then each context's scans and finalize; then the
+ * field, push and walls of all contexts of one degree and precision as one
+ * launch over a work list of (context, CTA of tiles). Instances of uneven N
+ * share those launches and overlap on the GPU. The batch does not
  * own the contexts; they must stay alive and must not be used through their
  * own entry points between imrp_batch_step and imrp_batch_sync. Each context
  * computes exactly what imrp_step would compute for it alone.
@@ -392,6 +397,13 @@ int imrp_batch_create(imrp_ctx* const* ctxs, int n, imrp_batch** out);
 int imrp_batch_step(imrp_batch* b, int64_t n_steps);
 int imrp_batch_sync(imrp_batch* b);
 int imrp_batch_destroy(imrp_batch* b);
+/* Autotuner of a batch: times the batched field launch of each degree and
+ * precision at 8, 4, 2 and 1 warps per CTA (those that fit), on the contexts'
+ * current particles with field-only passes (the state does not advance), and
+ * keeps the fastest for the batch's later steps. Shapes never change a
+ * particle's arithmetic: results stay bit-identical. Errors: IMRP_E_CUDA,
+ * IMRP_E_NOMEM, a context's device error (see imrp_batch_failed). */
+int imrp_batch_autotune(imrp_batch* b);
 /* Issues the batch's work on a caller-owned cudaStream_t (NULL: its own). */
 int imrp_batch_set_stream(imrp_batch* b, void* cuda_stream);
 const char* imrp_batch_last_error(const imrp_batch* b);

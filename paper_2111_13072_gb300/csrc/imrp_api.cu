@@ -225,25 +225,13 @@ int grow_history(imrp_ctx* ctx, int64_t need) {
   return IMRP_OK;
 }
 
-// Launches one step (record = 1) or the field evaluation without push (record = 0).
-// ev (optional): IMRP_N_STAGES + 1 events recorded at the stage boundaries.
-template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nullptr) {
-  const KernelSet<T>* ks = find_set<T>(ctx->L);
-  cudaStream_t s = ctx->stream;
-  const int64_t n = ctx->n;
-  Part<T>* st = state_of<T>(ctx);
+// Arguments of the moments kernel of a context (its sorted arrays).
+template <class T> MomArgs<T> make_mom_args(imrp_ctx* ctx) {
   T** S = sorted_ptrs<T>(ctx);
-  if (!ctx->keys_valid) {
-    launch_keys<T>(st, ctx->key0, ctx->idx0, n, 4294967296.0 / (ctx->r_out * ctx->r_out - 1.0), s);
-  }
-  if (ev) cudaEventRecord(ev[0], s);
-  const uint32_t* perm = launch_radix_sort(ctx->key0, ctx->idx0, ctx->key1, ctx->idx1, ctx->hist, n,
-                                           sort_first_byte(ctx->prec), s);
-  if (ev) cudaEventRecord(ev[1], s);
-  launch_reorder<T>(st, S, ctx->srt_id, perm, n, s);
   MomArgs<T> ma;
+  memset(&ma, 0, sizeof(ma));
   ma.x = S[0]; ma.y = S[1]; ma.z = S[2];
-  ma.n = n;
+  ma.n = ctx->n;
   ma.rho = T(ctx->r_out);
   ma.rho_inv = T(1.0 / ctx->r_out);
   ma.agg = static_cast<T*>(ctx->agg);
@@ -252,40 +240,18 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
   ma.q_ion = T(ctx->sp_q);
   ma.id = ctx->srt_id;
   ma.qtile = ctx->qtile;
-  if (ev) cudaEventRecord(ev[2], s);
-  ks->moments(ma, s);
-  if (ev) cudaEventRecord(ev[3], s);
-  if (ctx->species) {
-    // the charge inside each particle's radius: a scan of the tiles' charges (FP64)
-    launch_tile_scan<double>(ctx->qtile, ctx->qpfx, ctx->qgagg, ctx->ntiles, 1, s);
-    launch_group_scan<double>(ctx->qgagg, ctx->qwork, ctx->qticket, ctx->qgbase, ctx->qtot, ctx->qtotd,
-                              ctx->ngroups, 1, ctx->gseg, s);
-  }
-  launch_tile_scan<T>(static_cast<T*>(ctx->agg), static_cast<T*>(ctx->pfx), ctx->gagg, ctx->ntiles, ctx->nc, s);
-  launch_group_scan<T>(ctx->gagg, ctx->gswork, ctx->gsticket, static_cast<T*>(ctx->gbase),
-                       static_cast<T*>(ctx->tot), ctx->totd, ctx->ngroups, ctx->nc, ctx->gseg, s);
-  FinalizeArgs fa;
-  fa.st = ctx->st;
-  fa.totd = ctx->totd;
-  fa.qhist = ctx->qhist;
-  fa.uhist = ctx->uhist;
-  fa.cap = ctx->hcap;
-  fa.first = ctx->hist_first;
-  fa.record = record ? 1 : 0;
-  fa.L = ctx->L;
-  fa.drive_kind = ctx->p.drive_kind;
-  fa.inv_ntilde = 1.0 / ctx->n_tilde;
-  fa.v_hat = ctx->v_hat;
-  fa.sigma = ctx->p.width_wpe;
-  fa.t0 = ctx->t0;
-  fa.dt = ctx->p.dt;
-  for (int l = 0; l < kTabL; ++l) fa.canti[l] = ctx->canti[l];
-  launch_finalize(fa, s);
-  if (ev) cudaEventRecord(ev[4], s);
+  return ma;
+}
+
+// Arguments of the field kernel of a context: push (record) or field only.
+template <class T> FieldArgs<T> make_field_args(imrp_ctx* ctx, bool record) {
+  T** S = sorted_ptrs<T>(ctx);
+  const int64_t n = ctx->n;
   FieldArgs<T> a;
+  memset(&a, 0, sizeof(a));
   a.x = S[0]; a.y = S[1]; a.z = S[2]; a.vx = S[3]; a.vy = S[4]; a.vz = S[5];
   a.id = ctx->srt_id;
-  a.out = st;
+  a.out = state_of<T>(ctx);
   a.key = ctx->key0;
   a.kidx = ctx->idx0;
   a.n = n;
@@ -332,7 +298,69 @@ template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nul
     rl *= ctx->r_out;
     a.cdrive[l] = ctx->canti[l] * 4.0 * kPi * ctx->n_tilde;
   }
-  ks->field(a, ctx->wpb, s);
+  return a;
+}
+
+// The stages of one step (or field evaluation) of a context: radius keys (if
+// stale), sort and reorder; then the moments; then the scans and finalize;
+// then the field. The batch runs the moments and the field of many contexts
+// as one launch each (per degree and precision) between the others.
+template <class T> void enqueue_pre(imrp_ctx* ctx, cudaEvent_t* ev = nullptr) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  Part<T>* st = state_of<T>(ctx);
+  if (!ctx->keys_valid) {
+    launch_keys<T>(st, ctx->key0, ctx->idx0, n, 4294967296.0 / (ctx->r_out * ctx->r_out - 1.0), s);
+  }
+  if (ev) cudaEventRecord(ev[0], s);
+  const uint32_t* perm = launch_radix_sort(ctx->key0, ctx->idx0, ctx->key1, ctx->idx1, ctx->hist, n,
+                                           sort_first_byte(ctx->prec), s);
+  if (ev) cudaEventRecord(ev[1], s);
+  launch_reorder<T>(st, sorted_ptrs<T>(ctx), ctx->srt_id, perm, n, s);
+}
+
+template <class T> void enqueue_mid(imrp_ctx* ctx, bool record) {
+  cudaStream_t s = ctx->stream;
+  if (ctx->species) {
+    // the charge inside each particle's radius: a scan of the tiles' charges (FP64)
+    launch_tile_scan<double>(ctx->qtile, ctx->qpfx, ctx->qgagg, ctx->ntiles, 1, s);
+    launch_group_scan<double>(ctx->qgagg, ctx->qwork, ctx->qticket, ctx->qgbase, ctx->qtot, ctx->qtotd,
+                              ctx->ngroups, 1, ctx->gseg, s);
+  }
+  launch_tile_scan<T>(static_cast<T*>(ctx->agg), static_cast<T*>(ctx->pfx), ctx->gagg, ctx->ntiles, ctx->nc, s);
+  launch_group_scan<T>(ctx->gagg, ctx->gswork, ctx->gsticket, static_cast<T*>(ctx->gbase),
+                       static_cast<T*>(ctx->tot), ctx->totd, ctx->ngroups, ctx->nc, ctx->gseg, s);
+  FinalizeArgs fa;
+  fa.st = ctx->st;
+  fa.totd = ctx->totd;
+  fa.qhist = ctx->qhist;
+  fa.uhist = ctx->uhist;
+  fa.cap = ctx->hcap;
+  fa.first = ctx->hist_first;
+  fa.record = record ? 1 : 0;
+  fa.L = ctx->L;
+  fa.drive_kind = ctx->p.drive_kind;
+  fa.inv_ntilde = 1.0 / ctx->n_tilde;
+  fa.v_hat = ctx->v_hat;
+  fa.sigma = ctx->p.width_wpe;
+  fa.t0 = ctx->t0;
+  fa.dt = ctx->p.dt;
+  for (int l = 0; l < kTabL; ++l) fa.canti[l] = ctx->canti[l];
+  launch_finalize(fa, s);
+}
+
+// Launches one step (record = 1) or the field evaluation without push (record = 0).
+// ev (optional): IMRP_N_STAGES + 1 events recorded at the stage boundaries.
+template <class T> int enqueue(imrp_ctx* ctx, bool record, cudaEvent_t* ev = nullptr) {
+  const KernelSet<T>* ks = find_set<T>(ctx->L);
+  cudaStream_t s = ctx->stream;
+  enqueue_pre<T>(ctx, ev);
+  if (ev) cudaEventRecord(ev[2], s);
+  ks->moments(make_mom_args<T>(ctx), s);
+  if (ev) cudaEventRecord(ev[3], s);
+  enqueue_mid<T>(ctx, record);
+  if (ev) cudaEventRecord(ev[4], s);
+  ks->field(make_field_args<T>(ctx, record), ctx->wpb, s);
   if (ev) cudaEventRecord(ev[5], s);
   // the field kernel wrote fresh keys for the (now sorted) state in push mode
   ctx->keys_valid = record;
@@ -1033,8 +1061,21 @@ extern "C" int imrp_autotune(imrp_ctx* ctx, int* wpb_out, int* gseg_out) {
   return check_err(ctx);
 }
 
+// A degree and precision of a batch: its contexts' moments and field run as
+// one launch each over a work list of (context, block) items.
+struct BatchGroup {
+  int prec = 0, L = 0, wpb = 0;
+  std::vector<int> members;     // indices into the batch's contexts
+  void* dmom = nullptr;         // MomArgs<T>[members]
+  void* dfield = nullptr;       // FieldArgs<T>[members] (push mode)
+  int2* dmom_items = nullptr;   // (member, block of 1024 particles)
+  int2* dfield_items = nullptr; // (member, first tile of a CTA)
+  int nmom = 0, nfield = 0;
+};
+
 struct imrp_batch {
   std::vector<imrp_ctx*> c;
+  std::vector<BatchGroup> groups;
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
   cudaEvent_t fork = nullptr;
@@ -1045,6 +1086,7 @@ struct imrp_batch {
   std::vector<uint64_t> gen_at_capture;
   std::string err;
   int failed = -1;  // index of the context whose error the last call returned
+  std::vector<int3> tuned;  // (precision, degree, warps per CTA) chosen by imrp_batch_autotune
 };
 
 extern "C" int imrp_batch_create(imrp_ctx* const* ctxs, int n, imrp_batch** out) {
@@ -1076,10 +1118,121 @@ extern "C" int imrp_batch_create(imrp_ctx* const* ctxs, int n, imrp_batch** out)
   return IMRP_OK;
 }
 
+namespace {
+void free_groups(imrp_batch* b) {
+  if (!b->groups.empty()) cudaStreamSynchronize(b->stream);  // a replay may still read them
+  for (auto& g : b->groups) {
+    cudaFree(g.dmom);
+    cudaFree(g.dfield);
+    cudaFree(g.dmom_items);
+    cudaFree(g.dfield_items);
+  }
+  b->groups.clear();
+}
+
+// The contexts' arguments and work lists per degree and precision, in device
+// memory, for the batched launches (built before a capture: they hold buffer
+// pointers and scalars that the captured graph keeps using).
+template <class T> int fill_group(imrp_batch* b, BatchGroup& g) {
+  std::vector<MomArgs<T>> ma;
+  std::vector<FieldArgs<T>> fa;
+  std::vector<int2> mi, fi;
+  for (size_t k = 0; k < g.members.size(); ++k) {
+    imrp_ctx* ctx = b->c[g.members[k]];
+    ma.push_back(make_mom_args<T>(ctx));
+    fa.push_back(make_field_args<T>(ctx, true));
+    const int64_t mblocks = (ctx->n + 1023) / 1024;
+    for (int64_t q = 0; q < mblocks; ++q) mi.push_back(make_int2(int(k), int(q)));
+    for (int64_t t = 0; t < ctx->ntiles; t += g.wpb) fi.push_back(make_int2(int(k), int(t)));
+  }
+  g.nmom = int(mi.size());
+  g.nfield = int(fi.size());
+  if (cudaMalloc(&g.dmom, ma.size() * sizeof(MomArgs<T>)) != cudaSuccess ||
+      cudaMalloc(&g.dfield, fa.size() * sizeof(FieldArgs<T>)) != cudaSuccess ||
+      cudaMalloc(&g.dmom_items, mi.size() * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&g.dfield_items, fi.size() * sizeof(int2)) != cudaSuccess)
+    return IMRP_E_NOMEM;
+  if (cudaMemcpy(g.dmom, ma.data(), ma.size() * sizeof(MomArgs<T>), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g.dfield, fa.data(), fa.size() * sizeof(FieldArgs<T>), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g.dmom_items, mi.data(), mi.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g.dfield_items, fi.data(), fi.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+    return IMRP_E_CUDA;
+  return IMRP_OK;
+}
+
+int build_groups(imrp_batch* b) {
+  free_groups(b);
+  for (size_t i = 0; i < b->c.size(); ++i) {
+    imrp_ctx* ctx = b->c[i];
+    BatchGroup* g = nullptr;
+    for (auto& h : b->groups)
+      if (h.prec == ctx->prec && h.L == ctx->L) g = &h;
+    if (!g) {
+      b->groups.emplace_back();
+      g = &b->groups.back();
+      g->prec = ctx->prec;
+      g->L = ctx->L;
+      g->wpb = ctx->wpb;  // the launch shape of the group's first context, unless tuned
+      for (const int3& t : b->tuned)
+        if (t.x == g->prec && t.y == g->L) g->wpb = t.z;
+    }
+    g->members.push_back(int(i));
+  }
+  for (auto& g : b->groups) {
+    const int rc = g.prec == 1 ? fill_group<float>(b, g) : fill_group<double>(b, g);
+    if (rc) return rc;
+  }
+  return IMRP_OK;
+}
+
+// One step of every context of the batch: sort and reorder on each context's
+// stream; the moments of all contexts of a degree in one launch; the scans and
+// finalize per context; the field of all contexts of a degree in one launch.
+int enqueue_batch_step(imrp_batch* b) {
+  const int n = int(b->c.size());
+  cudaEventRecord(b->fork, b->stream);
+  for (int i = 0; i < n; ++i) {
+    imrp_ctx* ctx = b->c[i];
+    cudaStreamWaitEvent(ctx->stream, b->fork, 0);
+    if (ctx->prec == 1) enqueue_pre<float>(ctx);
+    else enqueue_pre<double>(ctx);
+    cudaEventRecord(b->join[i], ctx->stream);
+    cudaStreamWaitEvent(b->stream, b->join[i], 0);
+  }
+  for (auto& g : b->groups) {
+    if (g.prec == 1)
+      find_set<float>(g.L)->moments_batch(static_cast<const MomArgs<float>*>(g.dmom), g.dmom_items, g.nmom, b->stream);
+    else
+      find_set<double>(g.L)->moments_batch(static_cast<const MomArgs<double>*>(g.dmom), g.dmom_items, g.nmom,
+                                           b->stream);
+  }
+  cudaEventRecord(b->fork, b->stream);
+  for (int i = 0; i < n; ++i) {
+    imrp_ctx* ctx = b->c[i];
+    cudaStreamWaitEvent(ctx->stream, b->fork, 0);
+    if (ctx->prec == 1) enqueue_mid<float>(ctx, true);
+    else enqueue_mid<double>(ctx, true);
+    cudaEventRecord(b->join[i], ctx->stream);
+    cudaStreamWaitEvent(b->stream, b->join[i], 0);
+  }
+  for (auto& g : b->groups) {
+    if (g.prec == 1)
+      find_set<float>(g.L)->field_batch(static_cast<const FieldArgs<float>*>(g.dfield), g.dfield_items, g.nfield,
+                                        g.wpb, b->stream);
+    else
+      find_set<double>(g.L)->field_batch(static_cast<const FieldArgs<double>*>(g.dfield), g.dfield_items,
+                                         g.nfield, g.wpb, b->stream);
+  }
+  for (imrp_ctx* ctx : b->c) ctx->keys_valid = true;  // the field kernels wrote the next keys
+  return IMRP_OK;
+}
+}  // namespace
+
 extern "C" int imrp_batch_destroy(imrp_batch* b) {
   if (!b) return IMRP_OK;
   cudaStreamSynchronize(b->stream);
   if (b->g) cudaGraphExecDestroy(b->g);
+  free_groups(b);
   cudaStreamDestroy(b->own_stream ? b->own_stream : b->stream);
   cudaEventDestroy(b->fork);
   for (auto e : b->join) cudaEventDestroy(e);
@@ -1132,20 +1285,14 @@ extern "C" int imrp_batch_step(imrp_batch* b, int64_t n_steps) {
               b->gen_at_capture[i] == b->c[i]->gen;
     if (!valid) {
       if (b->g) { cudaGraphExecDestroy(b->g); b->g = nullptr; }
+      // work lists and arguments of the batched launches (outside the capture)
+      int rc = build_groups(b);
+      if (rc) { b->err = "batch work lists"; return rc; }
       cudaGraph_t g = nullptr;
       if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return batch_fail(b, nullptr, IMRP_E_CUDA);
-      cudaEventRecord(b->fork, b->stream);
-      int rc = IMRP_OK;
-      for (int i = 0; i < n && !rc; ++i) {
-        imrp_ctx* ctx = b->c[i];
-        cudaStreamWaitEvent(ctx->stream, b->fork, 0);
-        rc = enqueue_any(ctx, true);
-        if (!rc) rc = enqueue_any(ctx, true);
-        cudaEventRecord(b->join[i], ctx->stream);
-        cudaStreamWaitEvent(b->stream, b->join[i], 0);
-        if (rc) { b->err = ctx->err; }
-      }
+      rc = enqueue_batch_step(b);
+      if (!rc) rc = enqueue_batch_step(b);
       cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
       if (rc) { if (g) cudaGraphDestroy(g); return rc; }
       if (ec != cudaSuccess) { b->err = cudaGetErrorString(ec); return IMRP_E_CUDA; }
@@ -1182,6 +1329,97 @@ extern "C" int imrp_batch_step(imrp_batch* b, int64_t n_steps) {
     cudaStreamWaitEvent(ctx->stream, b->fork, 0);
   }
   if (cudaGetLastError() != cudaSuccess) { b->err = "launch"; return IMRP_E_CUDA; }
+  return IMRP_OK;
+}
+
+namespace {
+// Times the batched field launch of group g in field-only mode (the contexts'
+// sorted arrays and scans must be current) at `wpb` warps per CTA: the best
+// of `reps` launches after one warm-up, in ms.
+template <class T> int time_group_field(imrp_batch* b, const BatchGroup& g, int wpb, int reps, float* ms) {
+  std::vector<FieldArgs<T>> fa;
+  std::vector<int2> fi;
+  for (size_t k = 0; k < g.members.size(); ++k) {
+    imrp_ctx* ctx = b->c[g.members[k]];
+    fa.push_back(make_field_args<T>(ctx, false));
+    for (int64_t t = 0; t < ctx->ntiles; t += wpb) fi.push_back(make_int2(int(k), int(t)));
+  }
+  void* dfa = nullptr;
+  int2* dfi = nullptr;
+  int rc = IMRP_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaMalloc(&dfa, fa.size() * sizeof(FieldArgs<T>)) != cudaSuccess ||
+      cudaMalloc(&dfi, fi.size() * sizeof(int2)) != cudaSuccess ||
+      cudaMemcpy(dfa, fa.data(), fa.size() * sizeof(FieldArgs<T>), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dfi, fi.data(), fi.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    rc = IMRP_E_CUDA;
+  } else {
+    const KernelSet<T>* ks = find_set<T>(g.L);
+    float best = 1e30f;
+    for (int r = 0; r <= reps && rc == IMRP_OK; ++r) {
+      cudaEventRecord(e0, b->stream);
+      ks->field_batch(static_cast<const FieldArgs<T>*>(dfa), dfi, int(fi.size()), wpb, b->stream);
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = IMRP_E_CUDA; break; }
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0 && t < best) best = t;
+    }
+    *ms = best;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(dfa);
+  cudaFree(dfi);
+  return rc;
+}
+}  // namespace
+
+extern "C" int imrp_batch_autotune(imrp_batch* b) {
+  if (!b) return IMRP_E_INVAL;
+  b->failed = -1;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) { b->err = "sync"; return IMRP_E_CUDA; }
+  // the contexts' sorted arrays and scans at their current state (field-only
+  // stages: the state does not advance; the radius keys are recomputed later)
+  for (imrp_ctx* ctx : b->c) {
+    int rc = ensure_keys(ctx);
+    if (rc) return batch_fail(b, ctx, rc);
+    if (ctx->prec == 1) {
+      enqueue_pre<float>(ctx);
+      find_set<float>(ctx->L)->moments(make_mom_args<float>(ctx), ctx->stream);
+      enqueue_mid<float>(ctx, false);
+    } else {
+      enqueue_pre<double>(ctx);
+      find_set<double>(ctx->L)->moments(make_mom_args<double>(ctx), ctx->stream);
+      enqueue_mid<double>(ctx, false);
+    }
+    ctx->keys_valid = false;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return batch_fail(b, ctx, IMRP_E_CUDA);
+  }
+  int rc = build_groups(b);
+  if (rc) { b->err = "batch work lists"; return rc; }
+  b->tuned.clear();
+  for (auto& g : b->groups) {
+    int best_w = g.wpb;
+    float best = 1e30f;
+    for (int w : {8, 4, 2, 1}) {
+      const int nb = g.prec == 1 ? find_set<float>(g.L)->field_blocks_per_sm(w)
+                                 : find_set<double>(g.L)->field_blocks_per_sm(w);
+      if (nb < 1) continue;
+      float ms = 0.f;
+      rc = g.prec == 1 ? time_group_field<float>(b, g, w, 3, &ms) : time_group_field<double>(b, g, w, 3, &ms);
+      if (rc) { b->err = "batch autotune"; return rc; }
+      if (ms < best) { best = ms; best_w = w; }
+    }
+    b->tuned.push_back(make_int3(g.prec, g.L, best_w));
+  }
+  if (b->g) { cudaGraphExecDestroy(b->g); b->g = nullptr; }  // the next step recaptures with these shapes
+  free_groups(b);
+  for (imrp_ctx* ctx : b->c) {
+    rc = check_err(ctx);
+    if (rc) return batch_fail(b, ctx, rc);
+  }
   return IMRP_OK;
 }
 

@@ -107,6 +107,16 @@ template <class T, int L> void field_launch(const FieldArgs<T>& a, int wpb, cuda
   if (blocks > 0) k_field<T, L><<<unsigned(blocks), wpb * 32, smem, s>>>(a);
 }
 
+template <class T, int L> void mom_batch_launch(const MomArgs<T>* args, const int2* items, int nitems, cudaStream_t s) {
+  if (nitems > 0) k_moments_batch<T, L><<<unsigned(nitems), kMomThreads, moments_smem<T, L>(), s>>>(args, items);
+}
+
+template <class T, int L>
+void field_batch_launch(const FieldArgs<T>* args, const int2* items, int nitems, int wpb, cudaStream_t s) {
+  const size_t smem = size_t(wpb) * field_smem_per_warp<T>(L);
+  if (nitems > 0) k_field_batch<T, L><<<unsigned(nitems), wpb * 32, smem, s>>>(args, items);
+}
+
 template <class T, int L> int field_occ(int wpb) {
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_field<T, L>, wpb * 32,
@@ -119,9 +129,16 @@ template <class T, int L> cudaError_t set_attr() {
   cudaError_t e = cudaFuncSetAttribute(k_moments<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(moments_smem<T, L>()));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_field<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(8 * field_smem_per_warp<T>(L) > 227 * 1024 ? 227 * 1024
-                                                                             : 8 * field_smem_per_warp<T>(L)));
+  e = cudaFuncSetAttribute(k_moments_batch<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(moments_smem<T, L>()));
+  if (e != cudaSuccess) return e;
+  const int fmax = int(8 * field_smem_per_warp<T>(L) > 227 * 1024 ? 227 * 1024 : 8 * field_smem_per_warp<T>(L));
+  e = cudaFuncSetAttribute(k_field<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fmax);
+  if (e != cudaSuccess) return e;
+  // the batched kernel also holds one instance's arguments in static shared memory
+  const int bmax = int(227 * 1024 - sizeof(FieldArgs<T>));
+  return cudaFuncSetAttribute(k_field_batch<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              fmax < bmax ? fmax : bmax);
 }
 
 }  // namespace
@@ -155,7 +172,8 @@ template <class T, int L> cudaError_t set_attr() {
   template <int... Ls> void unit_register(std::vector<KernelSet<T>>& v) {                   \
     KernelSet<T> ks[] = {KernelSet<T>{Ls, &mom_launch<T, Ls>, &field_launch<T, Ls>,         \
                                       &unit_init<Ls...>, field_smem_per_warp<T>(Ls),        \
-                                      &field_occ<T, Ls>}...};                               \
+                                      &field_occ<T, Ls>, &mom_batch_launch<T, Ls>,          \
+                                      &field_batch_launch<T, Ls>}...};                      \
     for (auto& k : ks) v.push_back(k);                                                       \
   }                                                                                          \
   }                                                                                          \

@@ -127,6 +127,12 @@ template <class T> struct KernelSet {
   int (*init)(int device);  // tables + attributes, once per device
   size_t smem_per_warp;
   int (*field_blocks_per_sm)(int wpb);  // occupancy of the field kernel at wpb warps per CTA
+  // Batched launches over several instances of this degree and precision:
+  // args[i] in device memory, items[b] = (instance, first block) for the
+  // moments (blocks of 1024 particles) and (instance, first tile) for the
+  // field (CTAs of wpb tiles).
+  void (*moments_batch)(const MomArgs<T>* args, const int2* items, int nitems, cudaStream_t);
+  void (*field_batch)(const FieldArgs<T>* args, const int2* items, int nitems, int wpb, cudaStream_t);
 };
 void register_all(std::vector<KernelSet<float>>& f, std::vector<KernelSet<double>>& d);
 

@@ -88,9 +88,10 @@ __host__ __device__ constexpr size_t moments_smem() {
   return sizeof(T) * 7 * kMomPPT * (kMomThreads + 1);
 }
 
+// Body of the moments kernel for CTA `blk` of the instance whose arguments are
+// `a` (a kernel parameter, or a copy in shared memory for the batched launch).
 template <class T, int L>
-__global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void moments_block(const MomArgs<T>& a, int64_t blk, unsigned char* smem_raw) {
   constexpr int S = kMomThreads + 1;  // padded row
   T* sx = reinterpret_cast<T*>(smem_raw);  // x / r_out
   T* sy = sx + kMomPPT * S;                // y / r_out
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
   const Tables<T>& tb = tab<T>();
   const int th = threadIdx.x;
   const int64_t ntiles = (a.n + 31) >> 5;
-  const int64_t pbase = int64_t(blockIdx.x) * (kMomThreads * kMomPPT);
+  const int64_t pbase = blk * (kMomThreads * kMomPPT);
   const T ri = a.rho_inv;
   constexpr int kMomChains = mom_chains<T, L>();
   // stage 1024 particles: particle k of the CTA goes to row k % 16, column k / 16
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
   }
   __syncthreads();
   const bool odd = (th & 1) != 0;
-  const int64_t tile = int64_t(blockIdx.x) * (kMomThreads / 2) + (th >> 1);
+  const int64_t tile = blk * (kMomThreads / 2) + (th >> 1);
   if (a.species) {
     // the tile's charge (FP64): this thread's 16 particles, then its pair
     double qs = 0.0;
@@ -215,6 +216,31 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
   }
 }
 
+template <class T, int L>
+__global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  moments_block<T, L>(a, blockIdx.x, smem_raw);
+}
+
+// Batched moments: CTA b takes block items[b].y of instance items[b].x, whose
+// arguments args[items[b].x] are first copied to shared memory.
+template <class T> __device__ __forceinline__ void copy_args(const T* src, T* dst) {
+  static_assert(sizeof(T) % 4 == 0, "argument blocks are copied in words");
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int k = threadIdx.x; k < int(sizeof(T) / 4); k += blockDim.x) d[k] = s[k];
+}
+template <class T, int L>
+__global__ void __launch_bounds__(kMomThreads) k_moments_batch(const MomArgs<T>* __restrict__ args,
+                                                               const int2* __restrict__ items) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ MomArgs<T> sa;
+  const int2 it = items[blockIdx.x];
+  copy_args(args + it.x, &sa);
+  __syncthreads();
+  moments_block<T, L>(sa, it.y, smem_raw);
+}
+
 // Constants of the scaled Legendre recurrences of the near field. With
 // c_l = (2l-1)!!/l! (the leading coefficient of P_l), q_l = s^l P_l(u) / c_l
 // follows q_{l+1} = (s u) q_l - g_l s^2 q_{l-1}, g_l = l^2 / (4 l^2 - 1)
@@ -234,19 +260,18 @@ __host__ __device__ constexpr double leg_r(int l) { return leg_eps(l - 1) / leg_
 // their gradients (ladder identities) in shared memory, phase 3 evaluates the
 // far field of all other tiles, the near field of the pairs inside the tile,
 // the l = 0 terms, and then pushes the particle.
+// Body of the field kernel for warp `warp` of a CTA of `wpb` warps, tile
+// `tile` of the instance whose arguments are `a`.
 template <class T, int L>
-__global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
+__device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char* smem_raw, int warp, int wpb,
+                                           int64_t tile) {
   using V4 = typename Vec4<T>::type;
   using V2 = typename Vec2<T>::type;
   constexpr int NC = 2 * ncomp(L);
   constexpr int NI = nI(L), NR = nR(L);
   constexpr int NE = NI + NR;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const Tables<T>& tb = tab<T>();
   const unsigned lane = lane_id();
-  const int warp = threadIdx.x >> 5;
-  const int wpb = blockDim.x >> 5;
-  const int64_t tile = int64_t(blockIdx.x) * wpb + warp;
   const int64_t ntiles = (a.n + 31) >> 5;
   if (tile >= ntiles) return;  // warp-uniform; no block-wide barrier below
   const int64_t ts = tile_stride(ntiles);
@@ -908,6 +933,29 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
   rec.vx = VX; rec.vy = VY; rec.vz = VZ;
   rec.id = a.id[j];
   a.out[j] = rec;
+}
+
+template <class T, int L>
+__global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  field_tile<T, L>(a, smem_raw, warp, wpb, int64_t(blockIdx.x) * wpb + warp);
+}
+
+// Batched field: the instances of one degree and precision in one launch. CTA
+// b takes the tiles items[b].y .. items[b].y + wpb - 1 of instance items[b].x,
+// whose arguments args[items[b].x] are first copied to shared memory (a warp
+// past its instance's last tile returns at once, as in the single launch).
+template <class T, int L>
+__global__ void __launch_bounds__(256) k_field_batch(const FieldArgs<T>* __restrict__ args,
+                                                     const int2* __restrict__ items) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ FieldArgs<T> sa;
+  const int2 it = items[blockIdx.x];
+  copy_args(args + it.x, &sa);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  field_tile<T, L>(sa, smem_raw, warp, wpb, int64_t(it.y) + warp);
 }
 
 }  // namespace imrp

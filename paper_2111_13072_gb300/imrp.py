@@ -25,7 +25,7 @@ EXPORTS = [
     "imrp_load_particles_async", "imrp_copy_qdiff_async", "imrp_drude_fit", "imrp_drude_k",
     "imrp_drude_te", "imrp_admittance", "imrp_fit_damped_sine", "imrp_sheath_solve",
     "imrp_set_ion_profile", "imrp_checkpoint", "imrp_restore", "imrp_batch_failed",
-    "imrp_get_surface_charge", "imrp_fp32_peak", "imrp_ready", "imrp_set_species",
+    "imrp_get_surface_charge", "imrp_fp32_peak", "imrp_ready", "imrp_set_species", "imrp_batch_autotune",
 ]
 STAGES = ["sort", "reorder", "moments", "scans", "field"]
 
@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH):
     L.imrp_get_surface_charge.argtypes = [c_void_p, pd, P(ctypes.c_int64)]
     L.imrp_fp32_peak.argtypes = [pd, P(ctypes.c_int)]
     L.imrp_ready.argtypes = [c_void_p, P(ctypes.c_int)]
+    L.imrp_batch_autotune.argtypes = [c_void_p]
     L.imrp_set_species.argtypes = [c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     for name in EXPORTS:
         if name not in ("imrp_default_params", "imrp_last_error", "imrp_batch_last_error"):
@@ -268,6 +269,10 @@ class Batch:
 
     def sync(self):
         self._check(self._lib.imrp_batch_sync(self._h))
+
+    def autotune(self):
+        """imrp_batch_autotune: the fastest CTA size of each batched field launch."""
+        self._check(self._lib.imrp_batch_autotune(self._h))
 
     def failed_index(self) -> int:
         """imrp_batch_failed: index of the sim whose error the last call raised, or -1."""
