@@ -45,17 +45,18 @@ def workload_desc(w):
 
 def field_flops_per_particle(L):
     """FP32 flops of one particle in the field kernel (FMA = 2), counted from the
-    final recurrence and fixed: gradient expansions of degree 1..L+1 (Is) and
-    0..L-1 (Rs) on the rescaled recurrences, 19 flops per complex entry (one
-    scaling, complex recurrence, six FMAs of the contraction), 10 per real
-    (m = 0) entry, 8 per diagonal step; 16 pair evaluations of the in-tile
-    direct near field, each 13 flops per degree step of the scaled Legendre
-    recurrences (10 for the first) plus 57 for the pair geometry and the
-    gradient at both ends; 50 for the l = 0 term, the push and the walls, and
-    2 L for the removal of the particle's own image."""
-    nI = (L + 1) * (L + 4) // 2
-    nR = L * (L + 1) // 2
-    far = 19 * (nI - (L + 1)) + 10 * (L + 1) + 8 * (L + 1) + 19 * (nR - L) + 10 * L + 8 * (L - 1)
+    code as it executes: gradient expansions of degree 1..L+1 (Is) and 0..L-1
+    (Rs), column by column. A column m >= 1 is the complex diagonal times a
+    real recurrence: 16 flops per entry after the first (the scaled three-term
+    step, six FMAs of the contraction), 12 for the column's product with the
+    diagonal, 8 for the diagonal step; the real column m = 0 takes 10 per entry
+    (6 for the Rs entry l = 0) and 6 at its end. 16 pair evaluations of the
+    in-tile direct near field, each 13 flops per degree step of the scaled
+    Legendre recurrences (10 for the first) plus 57 for the pair geometry and
+    the gradient at both ends; 50 for the l = 0 term, the push and the walls,
+    and 2 L for the removal of the particle's own image."""
+    far = 10 * (L + 1) + 6 + sum(16 * (L + 1 - m) + 12 + 8 for m in range(1, L + 2))
+    far += 6 + 10 * (L - 1) + 6 + sum(16 * (L - m - 1) + 12 + 8 for m in range(1, L))
     near = 16 * (13 * (L - 1) - (3 if L >= 2 else 0) + 57)
     return far + near + 50 + 2 * L
 
@@ -254,6 +255,8 @@ def ensemble_measure(steps, warmup, autotune=True, n_instances=64, stream=None):
     stream = stream or torch.cuda.Stream()
     with imrp.Batch(sims) as b:
         b.set_stream(stream.cuda_stream)
+        if autotune:
+            b.autotune()  # the CTA size of each batched field launch
         b.step(warmup)
         b.sync()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -269,12 +272,14 @@ def ensemble_measure(steps, warmup, autotune=True, n_instances=64, stream=None):
     return {"value": ntot * steps / (ms / 1e3), "unit": UNIT, "instances": n_instances,
             "particles": ntot, "steps": steps, "ms_per_step": ms / steps, "autotuned": autotune,
             "workload": "64 instances, N log-uniform [1e4,1e6], T_e U[0.5,5] eV, n_e log-U[1e14,1e17], "
-                        "l_max in {8,12,16}, mixed precision, one captured graph per step pair"}
+                        "l_max in {8,12,16}, mixed precision, one captured graph per step pair, "
+                        "one moments and one field launch per degree"}
 
 
 def ensemble_compare(steps, warmup):
     """The 64-instance ensemble with the launch shapes the library picks at
-    creation and with the autotuner's choices (imrp_autotune), each timed."""
+    creation and with the autotuners' choices (imrp_autotune per context for
+    its scans, imrp_batch_autotune for the batched field launches), each timed."""
     plain = ensemble_measure(steps, warmup, autotune=False)
     tuned = ensemble_measure(steps, warmup, autotune=True)
     tuned["default_shapes"] = {"value": plain["value"], "ms_per_step": plain["ms_per_step"]}

@@ -404,23 +404,37 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
             dr = nr;
             di = ni;
           }
-          T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+          // the column is (dr + i di) times the real p_l, which obeys the
+          // same recurrence from p_m = 1: sum the contractions with p_l, then
+          // multiply by the diagonal once per column
+          T p1 = T(1), p0 = T(0);
+          T Sx = T(0), Sy = T(0), Sz = T(0), Tx = T(0), Ty = T(0), Tz = T(0);
 #pragma unroll
           for (int l = m; l <= L + 1; ++l) {
             if (l > m) {
-              const T A = tb.an[l * kTabL + m] * Zir2, B = ir2;
-              const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
-              c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+              const T A = tb.an[l * kTabL + m] * Zir2;
+              const T pn = A * p1 - ir2 * p0;
+              p0 = p1; p1 = pn;
             }
             if (l >= 1) {
               const V4 ca = coefA[idxI(L, l, m) - k0];
-              Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
+              if (l == m) {
+                Sx = ca.x; Sy = ca.y; Sz = ca.z;
+              } else {
+                Sx += ca.x * p1; Sy += ca.y * p1; Sz += ca.z * p1;
+              }
               if (m > 0) {
                 const V2 cb = coefB[idxI(L, l, m) - k0];
-                Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+                if (l == m) {
+                  Tx = ca.w; Ty = cb.x; Tz = cb.y;
+                } else {
+                  Tx += ca.w * p1; Ty += cb.x * p1; Tz += cb.y * p1;
+                }
               }
             }
           }
+          Ex += dr * Sx; Ey += dr * Sy; Ez += dr * Sz;
+          if (m > 0) { Fx += di * Tx; Fy += di * Ty; Fz += di * Tz; }
         }
       }
     }
@@ -444,21 +458,32 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
             dr = nr;
             di = ni;
           }
-          T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+          T p1 = T(1), p0 = T(0);
+          T Sx = T(0), Sy = T(0), Sz = T(0), Tx = T(0), Ty = T(0), Tz = T(0);
 #pragma unroll
           for (int l = m; l <= L - 1; ++l) {
             if (l > m) {
-              const T A = tb.an[l * kTabL + m] * Zs, B = rs2;
-              const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
-              c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+              const T A = tb.an[l * kTabL + m] * Zs;
+              const T pn = A * p1 - rs2 * p0;
+              p0 = p1; p1 = pn;
             }
             const V4 ca = coefA[NI + idxR(L, l, m) - k0];
-            Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
+            if (l == m) {
+              Sx = ca.x; Sy = ca.y; Sz = ca.z;
+            } else {
+              Sx += ca.x * p1; Sy += ca.y * p1; Sz += ca.z * p1;
+            }
             if (m > 0) {
               const V2 cb = coefB[NI + idxR(L, l, m) - k0];
-              Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+              if (l == m) {
+                Tx = ca.w; Ty = cb.x; Tz = cb.y;
+              } else {
+                Tx += ca.w * p1; Ty += cb.x * p1; Tz += cb.y * p1;
+              }
             }
           }
+          Ex += dr * Sx; Ey += dr * Sy; Ez += dr * Sz;
+          if (m > 0) { Fx += di * Tx; Fy += di * Ty; Fz += di * Tz; }
         }
       }
     }
@@ -498,25 +523,28 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
           T cA[L + 1];  // the column's recurrence coefficients, loaded before its steps
 #pragma unroll
           for (int j = 1; j <= L; ++j) cA[j] = m + j <= L + 1 ? tb.an[(m + j) * kTabL + m] : T(0);
-          T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+          T p1 = T(1), p0 = T(0);  // the column is (dr + i di) p_l
+          T Sx, Sy, Sz, Tx, Ty, Tz;
           {
             const V4 ca = coefA[eb + m];
             const V2 cb = coefB[eb + m];
-            Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
-            Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+            Sx = ca.x; Sy = ca.y; Sz = ca.z;
+            Tx = ca.w; Ty = cb.x; Tz = cb.y;
           }
 #pragma unroll
           for (int j = 1; j <= L; ++j) {
             const int l = m + j;
             if (l > L + 1) break;
-            const T A = cA[j] * Zir2, B = ir2;
-            const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
-            c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+            const T A = cA[j] * Zir2;
+            const T pn = A * p1 - ir2 * p0;
+            p0 = p1; p1 = pn;
             const V4 ca = coefA[eb + l];
             const V2 cb = coefB[eb + l];
-            Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
-            Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+            Sx += ca.x * p1; Sy += ca.y * p1; Sz += ca.z * p1;
+            Tx += ca.w * p1; Ty += cb.x * p1; Tz += cb.y * p1;
           }
+          Ex += dr * Sx; Ey += dr * Sy; Ez += dr * Sz;
+          Fx += di * Tx; Fy += di * Ty; Fz += di * Tz;
         }
       }
     }
@@ -557,25 +585,28 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
           T cA[L];  // the column's recurrence coefficients, loaded before its steps
 #pragma unroll
           for (int j = 1; j <= L - 1; ++j) cA[j] = m + j <= L - 1 ? tb.an[(m + j) * kTabL + m] : T(0);
-          T c1r = dr, c1i = di, c0r = T(0), c0i = T(0);
+          T p1 = T(1), p0 = T(0);
+          T Sx, Sy, Sz, Tx, Ty, Tz;
           {
             const V4 ca = coefA[eb + m];
             const V2 cb = coefB[eb + m];
-            Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
-            Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+            Sx = ca.x; Sy = ca.y; Sz = ca.z;
+            Tx = ca.w; Ty = cb.x; Tz = cb.y;
           }
 #pragma unroll
           for (int j = 1; j <= L - 1; ++j) {
             const int l = m + j;
             if (l > L - 1) break;
-            const T A = cA[j] * Zs, B = rs2;
-            const T nr = A * c1r - B * c0r, ni = A * c1i - B * c0i;
-            c0r = c1r; c0i = c1i; c1r = nr; c1i = ni;
+            const T A = cA[j] * Zs;
+            const T pn = A * p1 - rs2 * p0;
+            p0 = p1; p1 = pn;
             const V4 ca = coefA[eb + l];
             const V2 cb = coefB[eb + l];
-            Ex += ca.x * c1r; Ey += ca.y * c1r; Ez += ca.z * c1r;
-            Fx += ca.w * c1i; Fy += cb.x * c1i; Fz += cb.y * c1i;
+            Sx += ca.x * p1; Sy += ca.y * p1; Sz += ca.z * p1;
+            Tx += ca.w * p1; Ty += cb.x * p1; Tz += cb.y * p1;
           }
+          Ex += dr * Sx; Ey += dr * Sy; Ez += dr * Sz;
+          Fx += di * Tx; Fy += di * Ty; Fz += di * Tz;
         }
       }
     }
