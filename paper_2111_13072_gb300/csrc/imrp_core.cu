@@ -355,7 +355,6 @@ void launch_state_out(const Part<T>* st, double* x, double* v, int64_t n, cudaSt
 // total (the inclusive sum at the far end) goes to gagg[g][u] in FP64. Each
 // warp takes kTsTasks consecutive tasks and issues their loads first.
 // ============================================================================
-constexpr int kTsTasks = 4;
 
 // Compensated partial sums of the in-group scans. In FP32 every partial sum is
 // the unevaluated pair hi + lo: hi is the plain running sum and lo collects the
@@ -385,37 +384,40 @@ template <class T> __device__ __forceinline__ CSum<T> cs_shfl_up(CSum<T> v, int 
 }
 template <class T> __device__ __forceinline__ double cs_double(CSum<T> v) { return double(v.hi) + double(v.lo); }
 
+// In-group scans of the tile sums. A CTA takes 32 rows (components u) x 128
+// tiles (4 scan groups) of agg[u][tile]: each warp scans 4 rows, one V4 of 4
+// tiles per lane (a 4-element in-lane scan plus an 8-lane shuffle scan per
+// group), and the CTA writes the results transposed, pfx[tile][u], through
+// shared memory, so that the field kernel reads the carries of one tile as
+// contiguous lines. Is rows (u odd) get exclusive suffixes, Rs rows (u even)
+// exclusive prefixes; the group totals go to gagg[g][u] in FP64.
+constexpr int kTsRows = 32;    // components per CTA
+constexpr int kTsTiles = 128;  // tiles per CTA
+
 template <class T>
 __global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T* __restrict__ pfx,
                                                    double* __restrict__ gagg, int64_t tw, int64_t ts, int nc) {
   using V4 = typename Vec4<T>::type;
   using C = CSum<T>;
-  const int lane = threadIdx.x & 31, r = lane & 7;
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nseg = (tw + 127) / 128;  // 128-tile segments per row
-  const int64_t ntask = nseg * nc;
-  const int64_t t0 = warp * kTsTasks;
-  if (t0 >= ntask) return;  // warp-uniform
-  const int64_t u0 = t0 / nseg, s0 = t0 - u0 * nseg;
-  V4 v[kTsTasks];
-  {
-    int64_t u = u0, sg = s0;
+  __shared__ T buf[kTsRows][kTsTiles + 1];  // [row][tile], padded: the transposed reads hit distinct banks
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, r = lane & 7;
+  const int64_t tile0 = int64_t(blockIdx.x) * kTsTiles;
+  const int u0 = int(blockIdx.y) * kTsRows;
+  const int64_t tile = tile0 + 4 * lane;
+  V4 v[4];
 #pragma unroll
-    for (int k = 0; k < kTsTasks; ++k) {
-      const int64_t tile = sg * 128 + 4 * lane;
-      if (t0 + k < ntask && tile < tw) {
-        v[k] = *reinterpret_cast<const V4*>(agg + u * ts + tile);
-      } else {
-        v[k].x = v[k].y = v[k].z = v[k].w = T(0);
-      }
-      if (++sg == nseg) { sg = 0; ++u; }
+  for (int k = 0; k < 4; ++k) {
+    const int u = u0 + 4 * warp + k;
+    if (u < nc && tile < tw) {
+      v[k] = *reinterpret_cast<const V4*>(agg + int64_t(u) * ts + tile);
+    } else {
+      v[k].x = v[k].y = v[k].z = v[k].w = T(0);
     }
   }
-  int64_t u = u0, sg = s0;
 #pragma unroll
-  for (int k = 0; k < kTsTasks; ++k) {
-    if (t0 + k >= ntask) break;  // warp-uniform
-    const int64_t tile = sg * 128 + 4 * lane;
+  for (int k = 0; k < 4; ++k) {
+    const int row = 4 * warp + k, u = u0 + row;
+    if (u >= nc) break;  // warp-uniform
     const int64_t g = tile / 32;
     V4 o;
     if (u & 1) {  // Is: exclusive suffix
@@ -445,17 +447,26 @@ __global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T*
       o.w = cs_round(cs_add(x, e3));
       if (r == 7 && tile < tw) gagg[g * nc + u] = cs_double(cs_add(x, sum));
     }
-    if (tile < tw) *reinterpret_cast<V4*>(pfx + u * ts + tile) = o;
-    if (++sg == nseg) { sg = 0; ++u; }
+    buf[row][4 * lane] = o.x; buf[row][4 * lane + 1] = o.y;
+    buf[row][4 * lane + 2] = o.z; buf[row][4 * lane + 3] = o.w;
+  }
+  __syncthreads();
+  // transposed write: warp w writes tiles w, w + 8, ..., lane = row
+  const int u = u0 + lane;
+  if (u < nc) {
+#pragma unroll 4
+    for (int t = warp; t < kTsTiles; t += 8) {
+      const int64_t tt = tile0 + t;
+      if (tt < tw) pfx[tt * nc + u] = buf[lane][t];
+    }
   }
 }
 
 template <class T>
 void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s) {
   const int64_t tw = tiles_whole(ntiles), ts = tile_stride(ntiles);
-  const int64_t warps = ((tw + 127) / 128 * nc + kTsTasks - 1) / kTsTasks;
-  const int64_t blocks = (warps * 32 + 255) / 256;
-  if (blocks > 0) k_tile_scan<T><<<unsigned(blocks), 256, 0, s>>>(agg, pfx, gagg, tw, ts, nc);
+  const dim3 grid(unsigned((tw + kTsTiles - 1) / kTsTiles), unsigned((nc + kTsRows - 1) / kTsRows));
+  if (tw > 0) k_tile_scan<T><<<grid, 256, 0, s>>>(agg, pfx, gagg, tw, ts, nc);
 }
 
 // ============================================================================

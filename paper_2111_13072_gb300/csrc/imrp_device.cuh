@@ -242,7 +242,7 @@ template <class T> struct FieldArgs {
   uint32_t* key;      // next radius key (push mode)
   uint32_t* kidx;     // identity payload for the next sort (push mode)
   int64_t n;
-  const T* pfx;       // [NC][ntiles] in-group: Rs exclusive prefix, Is exclusive suffix
+  const T* pfx;       // [tile][NC] in-group: Rs exclusive prefix, Is exclusive suffix
   const T* gbase;     // [ngroups][NC] Rs: sum over earlier groups; Is: sum over later groups
   const T* tot;       // [NC] totals (Is components used)
   const T* agg;       // [NC][ntiles] tile sums (read only with img_in_tile)

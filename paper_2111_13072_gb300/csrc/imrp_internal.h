@@ -80,8 +80,9 @@ template <class T>
 void launch_state_out(const Part<T>* st, double* x, double* v, int64_t n, cudaStream_t s);
 
 // ---- scans (imrp_core.cu) ---------------------------------------------------
-// in-group scans of agg[u][tile] into pfx (row stride tile_stride(ntiles)),
-// group totals into gagg[g][u] (FP64)
+// in-group scans of agg[u][tile] (row stride tile_stride(ntiles)) into
+// pfx[tile][u] (tile-major: one tile's nc carries contiguous), group totals
+// into gagg[g][u] (FP64)
 template <class T>
 void launch_tile_scan(const T* agg, T* pfx, double* gagg, int64_t ntiles, int nc, cudaStream_t s);
 // group scan over gagg:

@@ -301,7 +301,7 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
   // The loop has a fixed trip count and is unrolled, so that all loads of the
   // scan carries are in flight at once.
   {
-    const T* pt = a.pfx + tile;   // [u][tile]
+    const V2* pt = reinterpret_cast<const V2*>(a.pfx + tile * NC);  // [tile][u]: (A, B) pairs
     const T* gb = a.gbase + g * NC;
     const T* at = a.agg + tile;   // [u][tile]
     const uint16_t* ctab = g_comp + comp_tab_off(L);
@@ -313,8 +313,9 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
         const uint16_t cr = ctab[e];
         const int l = cr & 0xff;
         const T rl = a.rhol[l];  // r_out^l
-        const T A = gb[2 * e] + pt[(2 * e) * ts];          // sum over inner tiles of q Rs(x_i / r_out)
-        const T B = gb[2 * e + 1] + pt[(2 * e + 1) * ts];  // sum over outer tiles of q Is(x_i)
+        const V2 ab = pt[e];
+        const T A = gb[2 * e] + ab.x;      // sum over inner tiles of q Rs(x_i / r_out)
+        const T B = gb[2 * e + 1] + ab.y;  // sum over outer tiles of q Is(x_i)
         // sum of q Is(x_i) of the image term: over all particles, or over the
         // other tiles when the own tile's image pairs are summed directly
         const T W = img_in_tile ? a.tot[2 * e + 1] - at[(2 * e + 1) * ts] : a.tot[2 * e + 1];
