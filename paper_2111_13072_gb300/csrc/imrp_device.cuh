@@ -352,7 +352,7 @@ __host__ __device__ constexpr int chunk_cap(int L) {
 template <class T>
 __host__ __device__ constexpr size_t field_smem_per_warp(int L) {
   return (sizeof(typename Vec4<T>::type) + sizeof(typename Vec2<T>::type)) * chunk_cap(L) +
-         sizeof(T) * 2 * ncomp(L);
+         sizeof(T) * (2 * ncomp(L) + 2);
 }
 
 }  // namespace imrp

@@ -52,35 +52,41 @@ void fill_prologue_tables() {
       const int s = isI ? 0 : 1;
       const int lq = isI ? Lp - 1 : Lp + 1;
       const int ms[3] = {M - 1, M + 1, M};
-      uint16_t flags = 0;
+      const int16_t zero = int16_t(2 * ncomp(L));  // the scratch's zero slot
+      double sgn_r = 1.0, sgn_i = 1.0;             // sign of source 1 (m = M - 1 < 0 only at M = 0)
       for (int q = 0; q < 3; ++q) {
         const int mq = ms[q], am = mq < 0 ? -mq : mq;
         if (lq < 1 || lq > L || am > lq) {
-          r.src[2 * q] = -1;
-          r.src[2 * q + 1] = -1;
+          r.src[2 * q] = zero;
+          r.src[2 * q + 1] = zero;
           continue;
         }
         r.src[2 * q] = int16_t(2 * comp_idx(L, lq, am, 0) + s);
-        r.src[2 * q + 1] = am > 0 ? int16_t(2 * comp_idx(L, lq, am, 1) + s) : int16_t(-1);
-        if (mq < 0) {  // X^{-m} = (-1)^m conj(X^m)
-          if (am & 1) flags |= uint16_t(1u << (2 * q));
-          else flags |= uint16_t(1u << (2 * q + 1));
+        r.src[2 * q + 1] = am > 0 ? int16_t(2 * comp_idx(L, lq, am, 1) + s) : zero;
+        if (mq < 0) {  // X^{-m} = (-1)^m conj(X^m); only source 1 can have m < 0
+          if (am & 1) sgn_r = -1.0;
+          else sgn_i = -1.0;
         }
       }
-      if (isI) flags |= uint16_t(1u << 8);
-      if (M > 0) flags |= uint16_t(1u << 9);
-      r.flags = flags;
       // ladder factors, times nu of the evaluated (rescaled) harmonic (Lp, M)
       const double nu = rec_nu(Lp, M);
+      double s1, s2, sz;
       if (isI) {
-        r.s1 = float(nu * sqrt(double((Lp + M) * (Lp + M - 1))));
-        r.s2 = float(-nu * sqrt(double((Lp - M) * (Lp - M - 1))));
-        r.sz = float(-nu * sqrt(double((Lp + M) * (Lp - M))));
+        s1 = nu * sqrt(double((Lp + M) * (Lp + M - 1)));
+        s2 = -nu * sqrt(double((Lp - M) * (Lp - M - 1)));
+        sz = -nu * sqrt(double((Lp + M) * (Lp - M)));
       } else {
-        r.s1 = float(nu * sqrt(double((Lp - M + 2) * (Lp - M + 1))));
-        r.s2 = float(-nu * sqrt(double((Lp + M + 2) * (Lp + M + 1))));
-        r.sz = float(nu * sqrt(double((Lp + 1 + M) * (Lp + 1 - M))));
+        s1 = nu * sqrt(double((Lp - M + 2) * (Lp - M + 1)));
+        s2 = -nu * sqrt(double((Lp + M + 2) * (Lp + M + 1)));
+        sz = nu * sqrt(double((Lp + 1 + M) * (Lp + 1 - M)));
       }
+      // d/dx = (s1 c1 + s2 c2) / 2, d/dy = (i / 2)(s1 c1 - s2 c2), d/dz = sz c0;
+      // entries of m > 0 count twice (the -m terms)
+      const double fac = M > 0 ? 2.0 : 1.0;
+      r.s1r = float(0.5 * fac * sgn_r * s1);
+      r.s1i = float(0.5 * fac * sgn_i * s1);
+      r.s2 = float(0.5 * fac * s2);
+      r.sz = float(fac * sz);
       return r;
     };
     for (int M = 0; M <= L + 1; ++M)

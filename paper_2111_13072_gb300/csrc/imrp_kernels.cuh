@@ -19,11 +19,17 @@ template <> __device__ __forceinline__ const Tables<double>& tab<double>() { ret
 // translation unit (filled by fill_prologue_tables at initialisation), for
 // every instantiated degree.
 // EntryRec: one gradient entry k of the shared-memory coefficient arrays.
+// Its six sources are scratch entries (the zero slot 2 ncomp(L) where a ladder
+// step leaves the table); the factors are the ladder factors times nu of the
+// evaluated harmonic, with the 1/2 of d/dx and d/dy, the 2 of the m > 0
+// entries and the sign of a negative-m source (X^{-m} = (-1)^m conj(X^m))
+// folded in, so the entry is
+//   d/dx = s1r c1.re + s2 c2.re + i (s1i c1.im + s2 c2.im)
+//   d/dy = (s2 c2.im - s1i c1.im) + i (s1r c1.re - s2 c2.re),  d/dz = sz c0.
 struct __align__(16) EntryRec {
-  int16_t src[6];   // scratch index of c1.re, c1.im, c2.re, c2.im, c0.re, c0.im (-1: zero)
-  uint16_t flags;   // bit q < 6: negate source q; bit 8: multipole (Is) part; bit 9: M > 0
-  uint16_t pad;
-  float s1, s2, sz, pad2;  // ladder factors times nu of the evaluated harmonic
+  int16_t src[6];   // scratch index of c1.re, c1.im, c2.re, c2.im, c0.re, c0.im
+  uint16_t pad[2];
+  float s1r, s1i, s2, sz;
 };
 constexpr int kNumDegrees = 7;  // the instantiated degrees: 1, 2, 4, 8, 12, 16, 24
 __host__ __device__ constexpr int degree_at(int i) {
@@ -279,7 +285,7 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
   V4* coefA = reinterpret_cast<V4*>(smem_raw) + size_t(warp) * CH;
   V2* coefB = reinterpret_cast<V2*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * CH) + size_t(warp) * CH;
   T* sc = reinterpret_cast<T*>(reinterpret_cast<V2*>(reinterpret_cast<V4*>(smem_raw) + size_t(wpb) * CH) +
-                               size_t(wpb) * CH) + size_t(warp) * NC;
+                               size_t(wpb) * CH) + size_t(warp) * (NC + 2);
   const int64_t g = tile / kTilesPerGroup;
   const double u_drive = a.st->u;
   const T kick = T(a.st->kick);
@@ -297,9 +303,12 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
   const bool is_ion = a.species && valid && a.id[j] >= a.n_e;
   const T qneg = valid ? (is_ion ? -a.q_ion : T(1)) : T(0);
 
-  // ---- phase 1: cI (coefficients of Is, s = 0) and cR (of Rs(x/r_out), s = 1).
+  // ---- phase 1: cI (coefficients of Is, s = 0) and cR (of Rs(x/r_out), s = 1),
+  // with the gradient's scale -pf (and 1/r_out for Rs) applied, and the zero slot.
   // The loop has a fixed trip count and is unrolled, so that all loads of the
   // scan carries are in flight at once.
+  const T mpf = T(-a.pf), mpfr = T(-a.pf) * a.rho_inv;
+  if (lane == 0) { sc[NC] = T(0); sc[NC + 1] = T(0); }
   {
     const V2* pt = reinterpret_cast<const V2*>(a.pfx + tile * NC);  // [tile][u]: (A, B) pairs
     const T* gb = a.gbase + g * NC;
@@ -323,8 +332,8 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
         if ((cr >> 8) & 1) cI += T(u_drive * a.cdrive[l]);
         T cR = rl * B;
         if (a.m0_only && ((cr >> 9) & 1)) { cI = T(0); cR = T(0); }
-        sc[2 * e] = cI;
-        sc[2 * e + 1] = cR;
+        sc[2 * e] = cI * mpf;
+        sc[2 * e + 1] = cR * mpfr;
       }
     }
   }
@@ -337,10 +346,9 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
   T Fx = T(0), Fy = T(0), Fz = T(0);  // second accumulator chain (Im parts)
 
   // ---- far field, in column chunks of at most kChunk gradient entries: the
-  // entries of a chunk are formed in shared memory (phase 2, scaled by -pf,
-  // x2 for m > 0) and evaluated at once; the recurrence's diagonal term is
-  // carried from chunk to chunk in registers.
-  const T mpf = T(-a.pf);
+  // entries of a chunk are formed in shared memory (phase 2) and evaluated at
+  // once; the recurrence's diagonal term is carried from chunk to chunk in
+  // registers.
   const EntryRec* etab = g_ent + ent_off(L);
   auto build = [&](int k0, int k1) {
     __syncwarp();
@@ -350,28 +358,17 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
       const int k = k0 + int(lane) + 32 * it;
       if (k < k1) {
         const EntryRec er = etab[k];
-        T c[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-          const int si = er.src[q];
-          const T val = si >= 0 ? sc[si] : T(0);
-          c[q] = ((er.flags >> q) & 1) ? -val : val;
-        }
-        const T c1r = c[0], c1i = c[1], c2r = c[2], c2i = c[3], c0r = c[4], c0i = c[5];
-        const T s1 = T(er.s1), s2 = T(er.s2), sz = T(er.sz);
-        const bool isI = (er.flags >> 8) & 1;
-        const int M = (er.flags >> 9) & 1;
-        // dx = (s1 c1 + s2 c2)/2 ; dy = (i/2)(s1 c1 - s2 c2) ; dz = sz c0
-        const T dxr = T(0.5) * (s1 * c1r + s2 * c2r), dxi = T(0.5) * (s1 * c1i + s2 * c2i);
-        const T tr = s1 * c1r - s2 * c2r, ti = s1 * c1i - s2 * c2i;
-        const T dyr = T(-0.5) * ti, dyi = T(0.5) * tr;
-        const T dzr = sz * c0r, dzi = sz * c0i;
-        T w = (M > 0 ? T(2) : T(1)) * mpf;
-        if (!isI) w *= a.rho_inv;
+        const T c1r = sc[er.src[0]], c1i = sc[er.src[1]], c2r = sc[er.src[2]], c2i = sc[er.src[3]],
+                c0r = sc[er.src[4]], c0i = sc[er.src[5]];
+        const T s1r = T(er.s1r), s1i = T(er.s1i), s2 = T(er.s2), sz = T(er.sz);
         V4 ca;
         V2 cb;
-        ca.x = w * dxr; ca.y = w * dyr; ca.z = w * dzr; ca.w = w * dxi;
-        cb.x = w * dyi; cb.y = w * dzi;
+        ca.x = s1r * c1r + s2 * c2r;  // d/dx, d/dy, d/dz (Re), d/dx (Im)
+        ca.y = s2 * c2i - s1i * c1i;
+        ca.z = sz * c0r;
+        ca.w = s1i * c1i + s2 * c2i;
+        cb.x = s1r * c1r - s2 * c2r;  // d/dy, d/dz (Im)
+        cb.y = sz * c0i;
         coefA[k - k0] = ca;
         coefB[k - k0] = cb;
       }
@@ -967,8 +964,14 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
   a.out[j] = rec;
 }
 
+// Register budget: in FP32, at least 3 CTAs of 256 threads per SM (80
+// registers): ptxas otherwise settles at 64 with spills in the far-field
+// loops; FP64 keeps its ~124.
+template <class T>
+__host__ __device__ constexpr int field_min_blocks() { return sizeof(T) == 4 ? 3 : 1; }
+
 template <class T, int L>
-__global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
+__global__ void __launch_bounds__(256, field_min_blocks<T>()) k_field(FieldArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   field_tile<T, L>(a, smem_raw, warp, wpb, int64_t(blockIdx.x) * wpb + warp);
@@ -979,7 +982,7 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs<T> a) {
 // whose arguments args[items[b].x] are first copied to shared memory (a warp
 // past its instance's last tile returns at once, as in the single launch).
 template <class T, int L>
-__global__ void __launch_bounds__(256) k_field_batch(const FieldArgs<T>* __restrict__ args,
+__global__ void __launch_bounds__(256, field_min_blocks<T>()) k_field_batch(const FieldArgs<T>* __restrict__ args,
                                                      const int2* __restrict__ items) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FieldArgs<T> sa;
