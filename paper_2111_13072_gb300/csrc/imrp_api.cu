@@ -1068,9 +1068,9 @@ struct BatchGroup {
   std::vector<int> members;     // indices into the batch's contexts
   void* dmom = nullptr;         // MomArgs<T>[members]
   void* dfield = nullptr;       // FieldArgs<T>[members] (push mode)
-  int2* dmom_items = nullptr;   // (member, block of 1024 particles)
+  int2* dmom_items = nullptr;   // (member, block): first the members of mom_ppt 16, then of 4
   int2* dfield_items = nullptr; // (member, first tile of a CTA)
-  int nmom = 0, nfield = 0;
+  int nmom = 0, nmom_small = 0, nfield = 0;
 };
 
 struct imrp_batch {
@@ -1136,15 +1136,19 @@ void free_groups(imrp_batch* b) {
 template <class T> int fill_group(imrp_batch* b, BatchGroup& g) {
   std::vector<MomArgs<T>> ma;
   std::vector<FieldArgs<T>> fa;
-  std::vector<int2> mi, fi;
+  std::vector<int2> mi, ms, fi;
   for (size_t k = 0; k < g.members.size(); ++k) {
     imrp_ctx* ctx = b->c[g.members[k]];
     ma.push_back(make_mom_args<T>(ctx));
     fa.push_back(make_field_args<T>(ctx, true));
-    const int64_t mblocks = (ctx->n + 1023) / 1024;
-    for (int64_t q = 0; q < mblocks; ++q) mi.push_back(make_int2(int(k), int(q)));
+    // the moments' blocks as the context's own launch takes them (bit-identical sums)
+    const int ppt = mom_ppt(sizeof(T), ctx->n);
+    const int64_t mblocks = mom_blocks(ctx->n, ppt);
+    for (int64_t q = 0; q < mblocks; ++q) (ppt == 16 ? mi : ms).push_back(make_int2(int(k), int(q)));
     for (int64_t t = 0; t < ctx->ntiles; t += g.wpb) fi.push_back(make_int2(int(k), int(t)));
   }
+  g.nmom_small = int(ms.size());
+  mi.insert(mi.end(), ms.begin(), ms.end());
   g.nmom = int(mi.size());
   g.nfield = int(fi.size());
   if (cudaMalloc(&g.dmom, ma.size() * sizeof(MomArgs<T>)) != cudaSuccess ||
@@ -1200,11 +1204,18 @@ int enqueue_batch_step(imrp_batch* b) {
     cudaStreamWaitEvent(b->stream, b->join[i], 0);
   }
   for (auto& g : b->groups) {
-    if (g.prec == 1)
-      find_set<float>(g.L)->moments_batch(static_cast<const MomArgs<float>*>(g.dmom), g.dmom_items, g.nmom, b->stream);
-    else
-      find_set<double>(g.L)->moments_batch(static_cast<const MomArgs<double>*>(g.dmom), g.dmom_items, g.nmom,
-                                           b->stream);
+    const int nbig = g.nmom - g.nmom_small;
+    if (g.prec == 1) {
+      const KernelSet<float>* ks = find_set<float>(g.L);
+      const MomArgs<float>* ma = static_cast<const MomArgs<float>*>(g.dmom);
+      ks->moments_batch(ma, g.dmom_items, nbig, 16, b->stream);
+      ks->moments_batch(ma, g.dmom_items + nbig, g.nmom_small, 4, b->stream);
+    } else {
+      const KernelSet<double>* ks = find_set<double>(g.L);
+      const MomArgs<double>* ma = static_cast<const MomArgs<double>*>(g.dmom);
+      ks->moments_batch(ma, g.dmom_items, nbig, 16, b->stream);
+      ks->moments_batch(ma, g.dmom_items + nbig, g.nmom_small, 4, b->stream);
+    }
   }
   cudaEventRecord(b->fork, b->stream);
   for (int i = 0; i < n; ++i) {

@@ -100,10 +100,17 @@ struct PrologueInit {
 };
 const PrologueInit g_prologue_init;
 
+// CTAs of 64 threads, mom_ppt particles per thread, covering whole scan groups
+// of 1024 particles (every tile the scans read is written; past the particles
+// the sums are zero)
 template <class T, int L> void mom_launch(const MomArgs<T>& a, cudaStream_t s) {
-  const int64_t per = kMomThreads * kMomPPT;
-  const int64_t blocks = (a.n + per - 1) / per;
-  if (blocks > 0) k_moments<T, L><<<unsigned(blocks), kMomThreads, moments_smem<T, L>(), s>>>(a);
+  if (a.n <= 0) return;
+  const int ppt = mom_ppt(sizeof(T), a.n);
+  const unsigned blocks = unsigned(mom_blocks(a.n, ppt));
+  if (ppt == kMomPPT)
+    k_moments<T, L, kMomPPT><<<blocks, kMomThreads, moments_smem<T, L, kMomPPT>(), s>>>(a);
+  else
+    k_moments<T, L, kMomPPTSmall><<<blocks, kMomThreads, moments_smem<T, L, kMomPPTSmall>(), s>>>(a);
 }
 
 template <class T, int L> void field_launch(const FieldArgs<T>& a, int wpb, cudaStream_t s) {
@@ -113,8 +120,14 @@ template <class T, int L> void field_launch(const FieldArgs<T>& a, int wpb, cuda
   if (blocks > 0) k_field<T, L><<<unsigned(blocks), wpb * 32, smem, s>>>(a);
 }
 
-template <class T, int L> void mom_batch_launch(const MomArgs<T>* args, const int2* items, int nitems, cudaStream_t s) {
-  if (nitems > 0) k_moments_batch<T, L><<<unsigned(nitems), kMomThreads, moments_smem<T, L>(), s>>>(args, items);
+template <class T, int L>
+void mom_batch_launch(const MomArgs<T>* args, const int2* items, int nitems, int ppt, cudaStream_t s) {
+  if (nitems <= 0) return;
+  if (ppt == kMomPPT)
+    k_moments_batch<T, L, kMomPPT><<<unsigned(nitems), kMomThreads, moments_smem<T, L, kMomPPT>(), s>>>(args, items);
+  else
+    k_moments_batch<T, L, kMomPPTSmall>
+        <<<unsigned(nitems), kMomThreads, moments_smem<T, L, kMomPPTSmall>(), s>>>(args, items);
 }
 
 template <class T, int L>
@@ -132,11 +145,17 @@ template <class T, int L> int field_occ(int wpb) {
 }
 
 template <class T, int L> cudaError_t set_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_moments<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(moments_smem<T, L>()));
+  cudaError_t e = cudaFuncSetAttribute(k_moments<T, L, kMomPPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(moments_smem<T, L, kMomPPT>()));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_moments_batch<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(moments_smem<T, L>()));
+  e = cudaFuncSetAttribute(k_moments<T, L, kMomPPTSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(moments_smem<T, L, kMomPPTSmall>()));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_moments_batch<T, L, kMomPPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(moments_smem<T, L, kMomPPT>()));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_moments_batch<T, L, kMomPPTSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(moments_smem<T, L, kMomPPTSmall>()));
   if (e != cudaSuccess) return e;
   const int fmax = int(8 * field_smem_per_warp<T>(L) > 227 * 1024 ? 227 * 1024 : 8 * field_smem_per_warp<T>(L));
   e = cudaFuncSetAttribute(k_field<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, fmax);

@@ -121,6 +121,31 @@ void launch_dft(const double* q, const double* u, int64_t ns, double dt, double 
                 int64_t nf, double w_max, double* out, cudaStream_t s);
 
 // ---- per-degree kernels (imrp_inst_*.cu) ------------------------------------
+// SMs of the current device (cached per device)
+inline int sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cache[dev] == 0) {
+    int v = 0;
+    cache[dev] = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0 ? v : 152;
+  }
+  return cache[dev];
+}
+// Particles per thread of the moments kernel for an instance of n particles:
+// 16 (1024 per CTA of 64 threads), or 4 (256 per CTA) for an FP64 instance
+// that would give fewer than two CTAs per SM. FP64 runs at a small fraction
+// of the FP32 rate here, so a small FP64 instance gains from four times the
+// SMs (N = 2e4, l_max = 8: 0.292 -> 0.103 ms); in FP32 the wider reduction
+// over each tile's threads costs more than the SMs bring (N = 1e5, l_max =
+// 16: 0.045 -> 0.068 ms), so FP32 keeps 16.
+inline int mom_ppt(int elem_size, int64_t n) {
+  return (elem_size == 8 && (n + 1023) / 1024 < 2 * sm_count()) ? 4 : 16;
+}
+// CTAs of the moments kernel (64 threads of ppt particles): whole scan groups
+// of 1024 particles, so that every tile the scans read is written
+inline int64_t mom_blocks(int64_t n, int ppt) { return (n + 1023) / 1024 * (16 / ppt); }
+
 template <class T> struct KernelSet {
   int L;
   void (*moments)(const MomArgs<T>&, cudaStream_t);
@@ -129,10 +154,10 @@ template <class T> struct KernelSet {
   size_t smem_per_warp;
   int (*field_blocks_per_sm)(int wpb);  // occupancy of the field kernel at wpb warps per CTA
   // Batched launches over several instances of this degree and precision:
-  // args[i] in device memory, items[b] = (instance, first block) for the
-  // moments (blocks of 1024 particles) and (instance, first tile) for the
-  // field (CTAs of wpb tiles).
-  void (*moments_batch)(const MomArgs<T>* args, const int2* items, int nitems, cudaStream_t);
+  // args[i] in device memory, items[b] = (instance, block) for the moments
+  // (blocks of 64 ppt particles, ppt = mom_ppt of every listed instance) and
+  // (instance, first tile) for the field (CTAs of wpb tiles).
+  void (*moments_batch)(const MomArgs<T>* args, const int2* items, int nitems, int ppt, cudaStream_t);
   void (*field_batch)(const FieldArgs<T>* args, const int2* items, int nitems, int wpb, cudaStream_t);
 };
 void register_all(std::vector<KernelSet<float>>& f, std::vector<KernelSet<double>>& d);

@@ -75,13 +75,17 @@ template <> __device__ __forceinline__ double fma_t<double>(double x, double y, 
 // shared memory in a [particle][thread] layout (conflict-free). The multipole
 // harmonics follow from the regular ones by the Kelvin relation
 //   Is_l^m(x) = Rs_l^m(x / r_out) * r_out^l / r^(2l+1),
-// the scale advancing by one factor r_out / r^2 per degree. At the end of a
-// column the two halves of each tile are combined with one shuffle per Rs/Is
-// pair (the even lane keeps the Rs sum, the odd lane the Is sum) and written:
-// agg[u][tile], u = 2 e + s (s = 0 Rs, s = 1 Is).
-constexpr int kMomThreads = 64;  // 32 tiles per CTA
-constexpr int kMomPPT = 16;      // particles per thread
-constexpr int kMomBreak = 2;     // steps between the column-end tests
+// the scale advancing by one factor r_out / r^2 per degree. A CTA of 64
+// threads takes 64 PPT particles (2 PPT tiles), PPT particles per thread,
+// 32 / PPT threads per tile.
+// At the end of a column the threads of each tile are combined: with two
+// (PPT = 16), one shuffle per Rs/Is pair (the even lane keeps the Rs sum, the
+// odd lane the Is sum); with more, a butterfly over the tile's threads, each
+// then writing its share. Written: agg[u][tile], u = 2 e + s (s = 0 Rs, s = 1 Is).
+constexpr int kMomThreads = 64;
+constexpr int kMomPPT = 16;       // particles per thread (1024 per CTA) when that fills the GPU
+constexpr int kMomPPTSmall = 4;   // particles per thread (256 per CTA) when it would leave SMs idle
+constexpr int kMomBreak = 2;      // steps between the column-end tests
 // particles advanced together (independent recurrence chains): four in FP32
 // (N = 2e6, l_max = 16: 0.174 -> 0.168 ms against two; l_max = 24, N = 4e6:
 // 0.676 -> 0.652 ms, though 150 registers lower the occupancy there), two in
@@ -89,37 +93,39 @@ constexpr int kMomBreak = 2;     // steps between the column-end tests
 template <class T, int L>
 __host__ __device__ constexpr int mom_chains() { return sizeof(T) == 4 ? 4 : 2; }
 
-template <class T, int L>
+template <class T, int L, int PPT = kMomPPT>
 __host__ __device__ constexpr size_t moments_smem() {
-  return sizeof(T) * 7 * kMomPPT * (kMomThreads + 1);
+  return sizeof(T) * 7 * PPT * (kMomThreads + 1);
 }
 
 // Body of the moments kernel for CTA `blk` of the instance whose arguments are
 // `a` (a kernel parameter, or a copy in shared memory for the batched launch).
-template <class T, int L>
+template <class T, int L, int PPT>
 __device__ __forceinline__ void moments_block(const MomArgs<T>& a, int64_t blk, unsigned char* smem_raw) {
-  constexpr int S = kMomThreads + 1;  // padded row
+  constexpr int NT = kMomThreads;  // threads of the CTA
+  constexpr int TPT = 32 / PPT;    // threads per tile
+  constexpr int S = NT + 1;       // padded row
   T* sx = reinterpret_cast<T*>(smem_raw);  // x / r_out
-  T* sy = sx + kMomPPT * S;                // y / r_out
-  T* sz = sy + kMomPPT * S;                // z / r_out
-  T* sq = sz + kMomPPT * S;                // r_out / r^2
-  T* sRr = sq + kMomPPT * S;               // q Rs_m^m(x / r_out), real and imaginary
-  T* sRi = sRr + kMomPPT * S;
-  T* ssc = sRi + kMomPPT * S;              // r_out^m / r^(2m+1)
+  T* sy = sx + PPT * S;                    // y / r_out
+  T* sz = sy + PPT * S;                    // z / r_out
+  T* sq = sz + PPT * S;                    // r_out / r^2
+  T* sRr = sq + PPT * S;                   // q Rs_m^m(x / r_out), real and imaginary
+  T* sRi = sRr + PPT * S;
+  T* ssc = sRi + PPT * S;                  // r_out^m / r^(2m+1)
   const Tables<T>& tb = tab<T>();
   const int th = threadIdx.x;
   const int64_t ntiles = (a.n + 31) >> 5;
-  const int64_t pbase = blk * (kMomThreads * kMomPPT);
+  const int64_t pbase = blk * (NT * PPT);
   const T ri = a.rho_inv;
-  constexpr int kMomChains = mom_chains<T, L>();
-  // stage 1024 particles: particle k of the CTA goes to row k % 16, column k / 16
+  constexpr int kMomChains = mom_chains<T, L>() < PPT ? mom_chains<T, L>() : PPT;
+  // stage 1024 particles: particle k of the CTA goes to row k % PPT, column k / PPT
 #pragma unroll 4
-  for (int i = 0; i < kMomPPT; ++i) {
-    const int k = i * kMomThreads + th;
+  for (int i = 0; i < PPT; ++i) {
+    const int k = i * NT + th;
     const int64_t j = pbase + k;
     const bool valid = j < a.n;
     const T X = valid ? a.x[j] : T(1), Y = valid ? a.y[j] : T(0), Z = valid ? a.z[j] : T(0);
-    const int o = (k % kMomPPT) * S + k / kMomPPT;
+    const int o = (k % PPT) * S + k / PPT;
     const T r2 = X * X + Y * Y + Z * Z;
     sx[o] = X * ri; sy[o] = Y * ri; sz[o] = Z * ri;
     sq[o] = a.rho / r2;
@@ -130,15 +136,17 @@ __device__ __forceinline__ void moments_block(const MomArgs<T>& a, int64_t blk, 
     ssc[o] = rsqrt_t(r2);
   }
   __syncthreads();
+  const int sub = th % TPT;  // this thread's part of its tile
   const bool odd = (th & 1) != 0;
-  const int64_t tile = blk * (kMomThreads / 2) + (th >> 1);
+  const int64_t tile = blk * (NT * PPT / 32) + th / TPT;
   if (a.species) {
-    // the tile's charge (FP64): this thread's 16 particles, then its pair
+    // the tile's charge (FP64): this thread's particles, then the tile's threads
     double qs = 0.0;
 #pragma unroll
-    for (int p = 0; p < kMomPPT; ++p) qs += double(sRr[p * S + th]);
-    qs += __shfl_xor_sync(0xffffffffu, qs, 1);
-    if (!odd) a.qtile[tile] = qs;
+    for (int p = 0; p < PPT; ++p) qs += double(sRr[p * S + th]);
+#pragma unroll
+    for (int d = 1; d < TPT; d <<= 1) qs += __shfl_xor_sync(0xffffffffu, qs, d);
+    if (sub == 0) a.qtile[tile] = qs;
   }
   // every tile of the whole groups is written (tiles past the particles hold
   // zeros: their particles carry no charge)
@@ -155,29 +163,31 @@ __device__ __forceinline__ void moments_block(const MomArgs<T>& a, int64_t blk, 
     for (int j = 1; j <= L; ++j) cA[j] = m + j <= L ? tb.an[(m + j) * kTabL + m] : T(0);
     const T dg = tb.dg[m];
 #pragma unroll 1
-    for (int p = 0; p < kMomPPT; p += kMomChains) {
-      T Zs[kMomChains], rs2[kMomChains], q[kMomChains], R1r[kMomChains], R1i[kMomChains], R0r[kMomChains],
-          R0i[kMomChains], sc[kMomChains];
+    for (int p = 0; p < PPT; p += kMomChains) {
+      // a column's harmonics are the diagonal Rs_m^m = (Dr + i Di) times a real
+      // p_l that obeys the column's three-term recurrence from p_m = 1
+      T Zs[kMomChains], rs2[kMomChains], q[kMomChains], Dr[kMomChains], Di[kMomChains], P1[kMomChains],
+          P0[kMomChains], sc[kMomChains];
 #pragma unroll
       for (int u = 0; u < kMomChains; ++u) {
         const int o = (p + u) * S + th;
         const T Xs = sx[o], Ys = sy[o];
         Zs[u] = sz[o]; q[u] = sq[o];
-        R1r[u] = sRr[o]; R1i[u] = sRi[o]; sc[u] = ssc[o];
+        Dr[u] = sRr[o]; Di[u] = sRi[o]; sc[u] = ssc[o];
         if (m > 0) {  // diagonal step: Rs_m^m = dg_m (x + i y) / r_out * Rs_{m-1}^{m-1}
           const T cx = dg * Xs, cy = dg * Ys;
-          const T nr = cx * R1r[u] - cy * R1i[u], ni = cx * R1i[u] + cy * R1r[u];
-          R1r[u] = nr; R1i[u] = ni; sc[u] *= q[u];
+          const T nr = cx * Dr[u] - cy * Di[u], ni = cx * Di[u] + cy * Dr[u];
+          Dr[u] = nr; Di[u] = ni; sc[u] *= q[u];
           sRr[o] = nr; sRi[o] = ni; ssc[o] = sc[u];
         }
         rs2[u] = Xs * Xs + Ys * Ys + Zs[u] * Zs[u];
-        R0r[u] = T(0); R0i[u] = T(0);
+        P1[u] = T(1); P0[u] = T(0);
       }
       if (m > 0) {
 #pragma unroll
         for (int u = 0; u < kMomChains; ++u) {
-          acc[0] += R1r[u]; acc[1] = fma_t(R1r[u], sc[u], acc[1]);
-          acc[2] += R1i[u]; acc[3] = fma_t(R1i[u], sc[u], acc[3]);
+          acc[0] += Dr[u]; acc[1] = fma_t(Dr[u], sc[u], acc[1]);
+          acc[2] += Di[u]; acc[3] = fma_t(Di[u], sc[u], acc[3]);
         }
       }
 #pragma unroll
@@ -189,54 +199,88 @@ __device__ __forceinline__ void moments_block(const MomArgs<T>& a, int64_t blk, 
 #pragma unroll
         for (int u = 0; u < kMomChains; ++u) {
           const T az = cA[j] * Zs[u];
-          const T nr = az * R1r[u] - rs2[u] * R0r[u], ni = az * R1i[u] - rs2[u] * R0i[u];
-          R0r[u] = R1r[u]; R0i[u] = R1i[u]; R1r[u] = nr; R1i[u] = ni;
+          const T pn = az * P1[u] - rs2[u] * P0[u];
+          P0[u] = P1[u]; P1[u] = pn;
           sc[u] *= q[u];
-          acc[4 * j + 0] += nr; acc[4 * j + 1] = fma_t(nr, sc[u], acc[4 * j + 1]);
-          acc[4 * j + 2] += ni; acc[4 * j + 3] = fma_t(ni, sc[u], acc[4 * j + 3]);
+          const T ps = pn * sc[u];
+          acc[4 * j + 0] = fma_t(Dr[u], pn, acc[4 * j + 0]); acc[4 * j + 1] = fma_t(Dr[u], ps, acc[4 * j + 1]);
+          acc[4 * j + 2] = fma_t(Di[u], pn, acc[4 * j + 2]); acc[4 * j + 3] = fma_t(Di[u], ps, acc[4 * j + 3]);
         }
       }
     }
     // ---- tile sums of the column, pair p = packed component e0 + p
     // (m = 0: p = l - 1, acc[4 l + s]; m > 0: p = 2 j + part, acc[2 p + s])
     const int64_t e0 = col_off(L, m);
-    if (m == 0) {
+    if constexpr (TPT == 2) {
+      if (m == 0) {
 #pragma unroll
-      for (int p = 0; p < L; ++p) {
-        const T send = odd ? acc[4 * (p + 1)] : acc[4 * (p + 1) + 1];
-        const T recv = __shfl_xor_sync(0xffffffffu, send, 1);
-        const T v = (odd ? acc[4 * (p + 1) + 1] : acc[4 * (p + 1)]) + recv;
-        agg_t[(2 * (e0 + p)) * ts] = v * tb.nu[(p + 1) * kTabL];
+        for (int p = 0; p < L; ++p) {
+          const T send = odd ? acc[4 * (p + 1)] : acc[4 * (p + 1) + 1];
+          const T recv = __shfl_xor_sync(0xffffffffu, send, 1);
+          const T v = (odd ? acc[4 * (p + 1) + 1] : acc[4 * (p + 1)]) + recv;
+          agg_t[(2 * (e0 + p)) * ts] = v * tb.nu[(p + 1) * kTabL];
+        }
+      } else {
+        const int np = 2 * (L - m + 1);
+#pragma unroll
+        for (int p = 0; p < 2 * L; ++p) {
+          if (p >= np) break;
+          const T send = odd ? acc[2 * p] : acc[2 * p + 1];
+          const T recv = __shfl_xor_sync(0xffffffffu, send, 1);
+          const T v = (odd ? acc[2 * p + 1] : acc[2 * p]) + recv;
+          agg_t[(2 * (e0 + p)) * ts] = v * tb.nu[(m + (p >> 1)) * kTabL + m];
+        }
       }
     } else {
-      const int np = 2 * (L - m + 1);
+      // sums over the tile's threads (butterfly), then value 2 p + s of the
+      // column goes out from the thread with sub = (2 p + s) % TPT
+      T* const agg_c = a.agg + tile;
+      if (m == 0) {
 #pragma unroll
-      for (int p = 0; p < 2 * L; ++p) {
-        if (p >= np) break;
-        const T send = odd ? acc[2 * p] : acc[2 * p + 1];
-        const T recv = __shfl_xor_sync(0xffffffffu, send, 1);
-        const T v = (odd ? acc[2 * p + 1] : acc[2 * p]) + recv;
-        agg_t[(2 * (e0 + p)) * ts] = v * tb.nu[(m + (p >> 1)) * kTabL + m];
+        for (int p = 0; p < L; ++p) {
+#pragma unroll
+          for (int sp = 0; sp < 2; ++sp) {
+            T v = acc[4 * (p + 1) + sp];
+#pragma unroll
+            for (int d = 1; d < TPT; d <<= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if ((2 * p + sp) % TPT == sub) agg_c[(2 * (e0 + p) + sp) * ts] = v * tb.nu[(p + 1) * kTabL];
+          }
+        }
+      } else {
+        const int np = 2 * (L - m + 1);
+#pragma unroll
+        for (int p = 0; p < 2 * L; ++p) {
+          if (p >= np) break;
+#pragma unroll
+          for (int sp = 0; sp < 2; ++sp) {
+            T v = acc[2 * p + sp];
+#pragma unroll
+            for (int d = 1; d < TPT; d <<= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if ((2 * p + sp) % TPT == sub)
+              agg_c[(2 * (e0 + p) + sp) * ts] = v * tb.nu[(m + (p >> 1)) * kTabL + m];
+          }
+        }
       }
     }
   }
 }
 
-template <class T, int L>
+template <class T, int L, int PPT>
 __global__ void __launch_bounds__(kMomThreads) k_moments(MomArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  moments_block<T, L>(a, blockIdx.x, smem_raw);
+  moments_block<T, L, PPT>(a, blockIdx.x, smem_raw);
 }
 
-// Batched moments: CTA b takes block items[b].y of instance items[b].x, whose
-// arguments args[items[b].x] are first copied to shared memory.
+// Batched moments: CTA b takes block items[b].y (of 64 PPT particles) of
+// instance items[b].x, whose arguments args[items[b].x] are first copied to
+// shared memory.
 template <class T> __device__ __forceinline__ void copy_args(const T* src, T* dst) {
   static_assert(sizeof(T) % 4 == 0, "argument blocks are copied in words");
   const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
   uint32_t* d = reinterpret_cast<uint32_t*>(dst);
   for (int k = threadIdx.x; k < int(sizeof(T) / 4); k += blockDim.x) d[k] = s[k];
 }
-template <class T, int L>
+template <class T, int L, int PPT>
 __global__ void __launch_bounds__(kMomThreads) k_moments_batch(const MomArgs<T>* __restrict__ args,
                                                                const int2* __restrict__ items) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -244,7 +288,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments_batch(const MomArgs<T>*
   const int2 it = items[blockIdx.x];
   copy_args(args + it.x, &sa);
   __syncthreads();
-  moments_block<T, L>(sa, it.y, smem_raw);
+  moments_block<T, L, PPT>(sa, it.y, smem_raw);
 }
 
 // Constants of the scaled Legendre recurrences of the near field. With

@@ -315,6 +315,50 @@ def test_large_sampled_parity(imrp):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_field_on_reused_device_memory(imrp, prec):
+    """A context created where an earlier one's buffers were freed (the device
+    allocator hands the same memory back, so the tile-sum arrays start with
+    the earlier instance's values): every tile the scans read must be written,
+    including the empty tiles of a ragged last scan group (n = 2500 fills 79
+    of the group's 96 tiles)."""
+    big = WORKLOADS["fp64_n2e4_l8"]
+    for n_prev in (20000, 9001):
+        x0, v0 = workload_state(big, N=n_prev)
+        with imrp.Sim(imrp.params_from_workload(big, N=n_prev, precision=prec)) as s0:
+            s0.load(x0, v0)
+            s0.step(2)
+        n = 2500
+        x, v = workload_state(big, N=n)
+        p, op = _pair(imrp, big, n, precision=prec)
+        with imrp.Sim(p) as sim:
+            sim.load(x, v)
+            E = sim.field()
+        Eo = oracle.field_scan(op, x, u=oracle.drive(op, 0))
+        check_field(E, Eo, prec, f"reused memory after n={n_prev}")
+
+
+def test_large_sampled_parity_fp64(imrp):
+    """FP64 at N = 2e6, l_max = 8: the moments kernel's 1024-particle blocks
+    (an FP64 instance this large fills the GPU with them; smaller FP64
+    instances use 256-particle blocks, covered by the full comparisons above),
+    sampled particles against the oracle's direct pair sum."""
+    w = WORKLOADS["mixed_n2e6_l16"]
+    x, _ = workload_state(w)
+    p, op = _pair(imrp, w, w.N, precision=0, l_max=8)
+    with imrp.Sim(p) as sim:
+        sim.load(x, np.zeros_like(x))
+        E = sim.field()
+    rng = np.random.default_rng(1)
+    order = np.argsort(np.linalg.norm(x, axis=1))
+    sample = np.unique(np.concatenate([order[:2], order[-2:], rng.choice(w.N, 8, replace=False)]))
+    Eo = oracle.field_brute(op, x, u=oracle.drive(op, 0), sample=sample)
+    err = np.linalg.norm(E[sample] - Eo, axis=1) / np.linalg.norm(Eo, axis=1)
+    print(f"N=2e6 FP64 sampled: largest per particle {err.max():.3e}")
+    assert _rel(E[sample], Eo) < TOL[0]
+    assert err.max() < P999[0]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("L,si,drive", [(1, 0, 1), (1, 1, 1), (4, 0, 2), (8, 1, 1), (16, 0, 1)])
 def test_m0_only_truncation_matches_oracle(imrp, prec, L, si, drive):
     """The paper's truncation (Sec. 3: m = 0 terms only; with l_max = 1 the printed
