@@ -74,6 +74,22 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
+def field_traffic(workload_name):
+    """DRAM bytes per field launch of this workload from profiles/field_traffic.json
+    (an ncu capture), or None unless it was taken of the current kernel sources."""
+    tf = os.path.join(ROOT, "profiles", "field_traffic.json")
+    if not os.path.exists(tf):
+        return None
+    try:
+        recs = json.load(open(tf))
+        for rec in recs if isinstance(recs, list) else [recs]:
+            if rec.get("kernel_hash") == kernel_hash() and rec.get("workload") == workload_name:
+                return rec.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -476,7 +492,8 @@ def sub_config(name, steps, warmup, nprof, peak_tflops, stream):
         out["roofline"] = {"bound": "alu", "kernel": "k_field (gather+push)", "achieved": ach,
                            "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops,
                            "frac_24K_model": ach24 / peak_tflops,
-                           "flops_per_particle": field_flops_per_particle(w.l_max)}
+                           "flops_per_particle": field_flops_per_particle(w.l_max),
+                           "traffic": field_traffic(w.name)}
     return out
 
 
@@ -591,16 +608,7 @@ def main():
     # FMA chains on every SM, the SM count read from the device)
     peak, n_sm = imrp.fp32_peak()
     peak_derived = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "field_traffic.json")
-    if os.path.exists(tf):
-        try:
-            recs = json.load(open(tf))
-            for rec in recs if isinstance(recs, list) else [recs]:
-                if rec.get("kernel_hash") == kernel_hash() and rec.get("workload") == w.name:
-                    traffic = rec.get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = field_traffic(w.name)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "k_field (gather+push)",
                 "flops_per_particle": field_flops_per_particle(w.l_max),
