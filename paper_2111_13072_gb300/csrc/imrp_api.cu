@@ -275,7 +275,7 @@ template <class T> FieldArgs<T> make_field_args(imrp_ctx* ctx, bool record) {
   a.ion_scale = ctx->n_tilde;
   a.q_s = ctx->ion_n ? ctx->ion_qs * ctx->n_tilde : ctx->p.q_s;
   a.r_out2 = ctx->r_out * ctx->r_out;
-  a.kscale = 4294967296.0 / (ctx->r_out * ctx->r_out - 1.0);
+  a.rk = make_radius_key(ctx->r_out);
   a.dt = T(ctx->p.dt);
   a.r_out = T(ctx->r_out);
   a.wall_rule = ctx->p.wall_rule;
@@ -310,7 +310,7 @@ template <class T> void enqueue_pre(imrp_ctx* ctx, cudaEvent_t* ev = nullptr) {
   const int64_t n = ctx->n;
   Part<T>* st = state_of<T>(ctx);
   if (!ctx->keys_valid) {
-    launch_keys<T>(st, ctx->key0, ctx->idx0, n, 4294967296.0 / (ctx->r_out * ctx->r_out - 1.0), s);
+    launch_keys<T>(st, ctx->key0, ctx->idx0, n, ctx->r_out, s);
   }
   if (ev) cudaEventRecord(ev[0], s);
   const uint32_t* perm = launch_radix_sort(ctx->key0, ctx->idx0, ctx->key1, ctx->idx1, ctx->hist, n,
@@ -992,9 +992,8 @@ namespace {
 // Radius keys for the current storage order (no step is taken).
 int ensure_keys(imrp_ctx* ctx) {
   if (ctx->keys_valid) return IMRP_OK;
-  const double ks = 4294967296.0 / (ctx->r_out * ctx->r_out - 1.0);
-  if (ctx->prec == 1) launch_keys<float>(state_of<float>(ctx), ctx->key0, ctx->idx0, ctx->n, ks, ctx->stream);
-  else launch_keys<double>(state_of<double>(ctx), ctx->key0, ctx->idx0, ctx->n, ks, ctx->stream);
+  if (ctx->prec == 1) launch_keys<float>(state_of<float>(ctx), ctx->key0, ctx->idx0, ctx->n, ctx->r_out, ctx->stream);
+  else launch_keys<double>(state_of<double>(ctx), ctx->key0, ctx->idx0, ctx->n, ctx->r_out, ctx->stream);
   CK(cudaGetLastError());
   ctx->keys_valid = true;
   return IMRP_OK;

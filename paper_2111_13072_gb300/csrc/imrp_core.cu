@@ -230,29 +230,84 @@ void launch_reorder(const Part<T>* src, T* const* dst, uint32_t* id_dst, const u
 // evaluation; a step's field kernel writes the next keys itself).
 template <class T>
 __global__ void k_keys(const Part<T>* __restrict__ st, uint32_t* __restrict__ key, uint32_t* __restrict__ kidx,
-                       int64_t n, double kscale) {
+                       int64_t n, RadiusKey rk) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const Part<T> p = st[j];
-  const double xd = p.x, yd = p.y, zd = p.z;
-  double kf = (xd * xd + yd * yd + zd * zd - 1.0) * kscale;
-  kf = kf < 0.0 ? 0.0 : (kf > 4294967295.0 ? 4294967295.0 : kf);
-  key[j] = uint32_t(kf);
+  key[j] = radius_key<T>(p.x, p.y, p.z, rk);
   kidx[j] = uint32_t(j);
 }
 
 template <class T>
-void launch_keys(const Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, double kscale, cudaStream_t s) {
-  k_keys<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(st, key, kidx, n, kscale);
+void launch_keys(const Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, double r_out, cudaStream_t s) {
+  k_keys<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(st, key, kidx, n, make_radius_key(r_out));
 }
 
+// FP64 -> FP32 rounding to nearest, ties to even (IEEE 754 binary64 ->
+// binary32), in integer operations: FP64 arithmetic, conversions included,
+// runs at a small fraction of the FP32 rate on this part and bound the load
+// kernel. Normal results keep the top 23 of the 52 mantissa bits and round on
+// the other 29 (a carry steps the exponent, up to infinity at the top of the
+// range); subnormal results shift the full 53-bit significand into the
+// subnormal units and round on the shifted-out bits; overflow gives infinity,
+// NaN stays a (quiet) NaN.
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+  const uint64_t b = uint64_t(__double_as_longlong(d));
+  const uint32_t sign = uint32_t(b >> 32) & 0x80000000u;
+  const int e = int(b >> 52) & 0x7ff;
+  const uint64_t m = b & 0xfffffffffffffull;
+  uint32_t bits;
+  if (e >= 897 && e <= 1150) {  // normal FP32 result
+    const uint32_t top = uint32_t(m >> 29), rest = uint32_t(m) & 0x1fffffffu;
+    bits = (uint32_t(e - 896) << 23) | top;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (top & 1u))) bits += 1u;
+  } else if (e == 0x7ff) {  // infinity, NaN
+    bits = 0x7f800000u | (m ? (0x400000u | uint32_t(m >> 29)) : 0u);
+  } else if (e > 1150) {    // overflow
+    bits = 0x7f800000u;
+  } else if (e >= 873) {    // subnormal result: M 2^(e - 926) units of 2^-149
+    const uint64_t M = m | (1ull << 52);
+    const int sh = 926 - e;  // 30 .. 53
+    const uint64_t q = M >> sh, r = M & ((1ull << sh) - 1), h = 1ull << (sh - 1);
+    bits = uint32_t(q) + ((r > h || (r == h && (q & 1u))) ? 1u : 0u);
+  } else {                  // below half the smallest subnormal
+    bits = 0u;
+  }
+  return __uint_as_float(sign | bits);
+}
+// FP32 -> FP64, exact, in integer operations: the exponent rebiased and the
+// mantissa widened; a subnormal is normalised from its leading bit.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = uint64_t(u & 0x80000000u) << 32;
+  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  uint64_t bits;
+  if (e == 255u) {
+    bits = 0x7ff0000000000000ull | (uint64_t(m) << 29);
+  } else if (e != 0u) {
+    bits = (uint64_t(e + 896u) << 52) | (uint64_t(m) << 29);
+  } else if (m == 0u) {
+    bits = 0;
+  } else {  // m 2^-149, leading bit at p
+    const int p = 31 - __clz(m);
+    bits = (uint64_t(p - 149 + 1023) << 52) | ((uint64_t(m) << (52 - p)) & 0xfffffffffffffull);
+  }
+  return __longlong_as_double(int64_t(sign | bits));
+}
+template <class T> __device__ __forceinline__ T narrow(double d);
+template <> __device__ __forceinline__ float narrow<float>(double d) { return f64_to_f32_rn(d); }
+template <> __device__ __forceinline__ double narrow<double>(double d) { return d; }
+template <class T> __device__ __forceinline__ double widen(T v);
+template <> __device__ __forceinline__ double widen<float>(float v) { return f32_to_f64(v); }
+template <> __device__ __forceinline__ double widen<double>(double v) { return v; }
+
 // Host FP64 [n][3] positions and velocities into the state, ids 0..n-1, with
-// the radius keys of that order (the same expression as k_keys), so that the
-// first step after a load needs no separate key pass.
+// the radius keys of that order, so that the first step after a load needs no
+// separate key pass.
 template <class T>
 __global__ void k_load(const double* __restrict__ xs, const double* __restrict__ vs,
                        const uint32_t* __restrict__ ids, Part<T>* __restrict__ st, uint32_t* __restrict__ key,
-                       uint32_t* __restrict__ kidx, int64_t n, double r_out, double kscale, int* err) {
+                       uint32_t* __restrict__ kidx, int64_t n, double r_out2, RadiusKey rk, int* err) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double v[6];
@@ -268,25 +323,36 @@ __global__ void k_load(const double* __restrict__ xs, const double* __restrict__
   for (int c = 0; c < 6; ++c)
     fin = fin && ((uint32_t(__double_as_longlong(v[c]) >> 32) & 0x7ff00000u) != 0x7ff00000u);
   Part<T> p;
-  p.x = T(v[0]); p.y = T(v[1]); p.z = T(v[2]);
-  p.vx = T(v[3]); p.vy = T(v[4]); p.vz = T(v[5]);
+  p.x = narrow<T>(v[0]); p.y = narrow<T>(v[1]); p.z = narrow<T>(v[2]);
+  p.vx = narrow<T>(v[3]); p.vy = narrow<T>(v[4]); p.vz = narrow<T>(v[5]);
   p.id = ids ? ids[j] : uint32_t(j);
-  const double xd = p.x, yd = p.y, zd = p.z;
-  const double r2 = xd * xd + yd * yd + zd * zd;
-  if (!fin) atomicOr(err, kErrNaN);
-  else if (!(r2 > 1.0 && r2 < r_out * r_out)) atomicOr(err, kErrRange);
   st[j] = p;
-  double kf = (r2 - 1.0) * kscale;
-  kf = kf < 0.0 ? 0.0 : (kf > 4294967295.0 ? 4294967295.0 : kf);
-  key[j] = uint32_t(kf);
+  // range test and radius key (radius_key's two forms, with r^2 shared)
+  bool inside;
+  uint32_t k;
+  bool fx = false;
+  if constexpr (sizeof(T) == 4) fx = key_fx_applies(p.x, p.y, p.z, rk);
+  if (fx) {
+    const uint64_t R2 = r2_fx(float(p.x), float(p.y), float(p.z));
+    inside = R2 > kFxOne && R2 < rk.rout2_fx;
+    k = key_of_fx(R2, rk);
+  } else {
+    const double xd = widen<T>(p.x), yd = widen<T>(p.y), zd = widen<T>(p.z);
+    const double r2 = xd * xd + yd * yd + zd * zd;
+    inside = r2 > 1.0 && r2 < r_out2;
+    k = key_of_r2(r2, rk);
+  }
+  if (!fin) atomicOr(err, kErrNaN);
+  else if (!inside) atomicOr(err, kErrRange);
+  key[j] = k;
   kidx[j] = uint32_t(j);
 }
 
 template <class T>
 void launch_load(const double* x, const double* v, const uint32_t* ids, Part<T>* st, uint32_t* key,
                  uint32_t* kidx, int64_t n, double r_out, int* err, cudaStream_t s) {
-  const double kscale = 4294967296.0 / (r_out * r_out - 1.0);
-  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, v, ids, st, key, kidx, n, r_out, kscale, err);
+  k_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, v, ids, st, key, kidx, n, r_out * r_out,
+                                                      make_radius_key(r_out), err);
 }
 
 template <class T>
@@ -454,11 +520,11 @@ __global__ void __launch_bounds__(256) k_tile_scan(const T* __restrict__ agg, T*
   // transposed write: warp w writes tiles w, w + 8, ..., lane = row
   const int u = u0 + lane;
   if (u < nc) {
+    const int tend = tw - tile0 < kTsTiles ? int(tw - tile0) : kTsTiles;
+    T* dst = pfx + (tile0 + warp) * nc + u;
+    const int64_t step = 8 * int64_t(nc);
 #pragma unroll 4
-    for (int t = warp; t < kTsTiles; t += 8) {
-      const int64_t tt = tile0 + t;
-      if (tt < tw) pfx[tt * nc + u] = buf[lane][t];
-    }
+    for (int t = warp; t < tend; t += 8, dst += step) *dst = buf[lane][t];
   }
 }
 

@@ -28,6 +28,8 @@
 // with X^{-m} = (-1)^m conj(X^m).
 #pragma once
 
+#include <math.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -59,6 +61,71 @@ struct StepState {
                       // folded in by the finalize kernel before each field evaluation
   int64_t nabs_total; // electrons absorbed at the probe since the load, as folded
 };
+
+// ---- radius key -------------------------------------------------------------
+// The sort key of a particle: r^2 quantised to 32 bits,
+// floor((r^2 - 1) 2^32 / (r_out^2 - 1)) clamped to [0, 2^32 - 1]. FP32
+// positions take a fixed-point form in 64-bit integer arithmetic (FP64 runs at
+// a small fraction of the FP32 rate on this part): r^2 with 56 fraction bits,
+// each square S^2 2^(2e - 244) of the 24-bit significand S truncated (an error
+// below 3 2^-56), times ks = round(2^40 / (r_out^2 - 1)), of which the high
+// 64 bits of the 128-bit product are the key. It is monotone in r^2 and within
+// one unit of the FP64 formula, which FP64 positions keep (and FP32 positions
+// with a coordinate of 8 or more, or r_out^2 of 48 or more, where the
+// fixed-point sum could overflow). Every kernel that writes keys for one
+// context uses radius_key, so keys compare alike across them.
+struct RadiusKey {
+  double kscale;      // 2^32 / (r_out^2 - 1)
+  uint64_t rout2_fx;  // r_out^2 2^56
+  uint64_t ks_fx;     // round(2^40 / (r_out^2 - 1))
+  int use_fx;         // the fixed-point form applies to FP32 positions
+};
+inline RadiusKey make_radius_key(double r_out) {
+  RadiusKey rk{};
+  const double r2 = r_out * r_out;
+  rk.kscale = 4294967296.0 / (r2 - 1.0);
+  const double ks = ldexp(1.0, 40) / (r2 - 1.0);
+  if (r2 < 48.0 && ks < ldexp(1.0, 62)) {
+    rk.use_fx = 1;
+    rk.rout2_fx = uint64_t(ldexp(r2, 56));
+    rk.ks_fx = uint64_t(llround(ks));
+  }
+  return rk;
+}
+constexpr uint64_t kFxOne = 1ull << 56;
+// floor(v^2 2^56) for |v| < 8
+__device__ __forceinline__ uint64_t sq_fx56(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const int e8 = int((u >> 23) & 0xffu);
+  if (e8 == 0) return 0;  // zero or subnormal: v^2 < 2^-252
+  const uint64_t S = uint64_t((u & 0x7fffffu) | 0x800000u);
+  const uint64_t S2 = S * S;  // < 2^48
+  const int t = 2 * e8 - 244;  // <= 14 for |v| < 8
+  if (t >= 0) return S2 << t;
+  return t <= -64 ? 0 : (S2 >> (-t));
+}
+__device__ __forceinline__ bool key_fx_applies(float x, float y, float z, const RadiusKey& rk) {
+  return rk.use_fx && fabsf(x) < 8.f && fabsf(y) < 8.f && fabsf(z) < 8.f;
+}
+__device__ __forceinline__ uint64_t r2_fx(float x, float y, float z) { return sq_fx56(x) + sq_fx56(y) + sq_fx56(z); }
+__device__ __forceinline__ uint32_t key_of_fx(uint64_t R2, const RadiusKey& rk) {
+  if (R2 <= kFxOne) return 0u;
+  if (R2 >= rk.rout2_fx) return 4294967295u;
+  const uint64_t hi = __umul64hi(R2 - kFxOne, rk.ks_fx);
+  return hi < 4294967295ull ? uint32_t(hi) : 4294967295u;
+}
+__device__ __forceinline__ uint32_t key_of_r2(double r2, const RadiusKey& rk) {
+  double kf = (r2 - 1.0) * rk.kscale;
+  kf = kf < 0.0 ? 0.0 : (kf > 4294967295.0 ? 4294967295.0 : kf);
+  return uint32_t(kf);
+}
+template <class T> __device__ __forceinline__ uint32_t radius_key(T x, T y, T z, const RadiusKey& rk) {
+  if constexpr (sizeof(T) == 4) {
+    if (key_fx_applies(x, y, z, rk)) return key_of_fx(r2_fx(x, y, z), rk);
+  }
+  const double xd = x, yd = y, zd = z;
+  return key_of_r2(xd * xd + yd * yd + zd * zd, rk);
+}
 
 // Device error flags (bitwise or).
 enum : int { kErrNaN = 1, kErrRange = 4 };
@@ -261,7 +328,7 @@ template <class T> struct FieldArgs {
   int ion_n;          // nodes of ion_q (>= 2 when ion_q is set)
   double q_s;         // surface charge of the parameters (the absorbed charge st->qs_acc adds to it)
   double r_out2;      // r_out^2
-  double kscale;      // 2^32 / (r_out^2 - 1)
+  RadiusKey rk;       // the radius key of the next step's sort
   T dt;
   T r_out;
   int wall_rule;      // 0 diffuse, 1 specular, 2 absorb (probe charge to Q_S) and re-inject

@@ -64,7 +64,7 @@ template <class T>
 void launch_reorder(const Part<T>* src, T* const* dst, uint32_t* id_dst, const uint32_t* perm, int64_t n,
                     cudaStream_t s);
 template <class T>
-void launch_keys(const Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, double kscale, cudaStream_t s);
+void launch_keys(const Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, double r_out, cudaStream_t s);
 template <class T>
 void launch_load(const double* x /* [n][3] */, const double* v /* [n][3] */, const uint32_t* ids /* or null */,
                  Part<T>* st, uint32_t* key, uint32_t* kidx, int64_t n, double r_out, int* err, cudaStream_t s);

@@ -917,14 +917,16 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
 
   // ---- walls (Sec. 4): mirror the radius back, keep the speed
   {
-    double rr;
-    bool hit;
+    double rr = 0.0;
+    bool hit = false;
     {
       const T rt = X * X + Y * Y + Z * Z;
       const bool near_wall = rt < T(1.0 + 1e-5) || rt > T(a.r_out2 * (1.0 - 1e-5));
-      const double xd = double(X), yd = double(Y), zd = double(Z);
-      rr = xd * xd + yd * yd + zd * zd;  // exact for FP32 positions; also the next key
-      hit = near_wall && (rr < 1.0 || rr > a.r_out2);
+      if (near_wall) {  // the exact test in FP64 only near a wall
+        const double xd = double(X), yd = double(Y), zd = double(Z);
+        rr = xd * xd + yd * yd + zd * zd;  // exact for FP32 positions
+        hit = rr < 1.0 || rr > a.r_out2;
+      }
     }
     if (hit && a.wall_rule == 2) {
       // absorbed (at the probe its charge joins Q_S) and replaced from the outer wall
@@ -933,7 +935,6 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
       inject_particle(a.id[j], uint64_t(a.st->step), a.seed, double(a.r_out), double(a.dt), a.sigma_v, xn, vn);
       X = T(xn[0]); Y = T(xn[1]); Z = T(xn[2]);
       VX = T(vn[0]); VY = T(vn[1]); VZ = T(vn[2]);
-      rr = double(X) * double(X) + double(Y) * double(Y) + double(Z) * double(Z);
     } else if (hit) {
       const double xd = double(X), yd = double(Y), zd = double(Z);
       const double rd = sqrt(rr);
@@ -969,7 +970,6 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
         VY = speed * (ca * n1 + sa * (cp * t11 + sp * t21));
         VZ = speed * (ca * n2 + sa * (cp * t12 + sp * t22));
       }
-      rr = double(X) * double(X) + double(Y) * double(Y) + double(Z) * double(Z);
     }
     if (a.coll_thr != 0u && !is_ion) {
       // electron-neutral collision: isotropic elastic scattering with
@@ -992,13 +992,9 @@ __device__ __forceinline__ void field_tile(const FieldArgs<T>& a, unsigned char*
         VZ = speed * ct;
       }
     }
-    if (!(isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(VX) && isfinite(VY) && isfinite(VZ))) {
-      atomicOr(a.err, kErrNaN);
-      rr = 1.0;
-    }
-    double kf = (rr - 1.0) * a.kscale;
-    kf = kf < 0.0 ? 0.0 : (kf > 4294967295.0 ? 4294967295.0 : kf);
-    a.key[j] = uint32_t(kf);
+    const bool fin = isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(VX) && isfinite(VY) && isfinite(VZ);
+    if (!fin) atomicOr(a.err, kErrNaN);
+    a.key[j] = fin ? radius_key<T>(X, Y, Z, a.rk) : 0u;
     a.kidx[j] = uint32_t(j);
   }
   Part<T> rec;

@@ -154,7 +154,7 @@ int run(const imrp_params* p, const double* x, int64_t n, int64_t step, double* 
   int* err = static_cast<int*>(P(o.err));
   k_na_init<<<1, 1, 0, s>>>(st, step, err, static_cast<unsigned*>(P(o.gsticket)), gs_col_blocks(nc));
   k_na_load<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, st0, n, r_out, err);
-  launch_keys<T>(st0, key0, idx0, n, 4294967296.0 / (r_out * r_out - 1.0), s);
+  launch_keys<T>(st0, key0, idx0, n, r_out, s);
   const uint32_t* perm = launch_radix_sort(key0, idx0, static_cast<uint32_t*>(P(o.key1)), static_cast<uint32_t*>(P(o.idx1)),
                     static_cast<uint32_t*>(P(o.hist)), n, sort_first_byte(sizeof(T) == 4 ? 1 : 0), s);
   launch_reorder<T>(st0, st1, id1, perm, n, s);
@@ -213,7 +213,7 @@ int run(const imrp_params* p, const double* x, int64_t n, int64_t step, double* 
   a.ion_coef = double(n) / (r_out * r_out * r_out - 1.0);
   a.q_s = p->q_s;
   a.r_out2 = r_out * r_out;
-  a.kscale = 4294967296.0 / (r_out * r_out - 1.0);
+  a.rk = make_radius_key(r_out);
   a.dt = T(p->dt);
   a.r_out = T(r_out);
   a.wall_rule = p->wall_rule;

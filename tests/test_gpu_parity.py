@@ -337,6 +337,43 @@ def test_field_on_reused_device_memory(imrp, prec):
         check_field(E, Eo, prec, f"reused memory after n={n_prev}")
 
 
+def test_fp32_load_rounds_to_nearest_even(imrp):
+    """The load converts FP64 host data to the FP32 state by round to nearest,
+    ties to even (its own integer rounding in the normal range, the hardware
+    conversion elsewhere): bit for bit what numpy's float32 conversion gives,
+    on exact ties both ways, carries into the exponent, values near the top of
+    the FP32 range and past it (infinity), subnormal results and the ties
+    between them and zero, signed zeros."""
+    rng = np.random.default_rng(4)
+    n = 4096
+    w = WORKLOADS["fp64_n2e4_l8"]
+    x, v = workload_state(w, N=n)
+    x = x.copy()
+    v = v.copy()
+    # ties: a float32 value plus or minus half its spacing (even and odd mantissas)
+    f = x[:1024].astype(np.float32)
+    half = np.spacing(f).astype(np.float64) / 2
+    x[:512] = f[:512].astype(np.float64) + half[:512]
+    x[512:1024] = f[512:1024].astype(np.float64) - half[512:1024]
+    # velocities: random bits of the mantissa, carries, extremes
+    vv = v.reshape(-1)
+    vv[:3000] = rng.standard_normal(3000) * np.exp(rng.uniform(-20, 20, 3000))
+    edge = np.array([np.nextafter(2.0, 0.0), np.nextafter(1.0, 2.0), -np.nextafter(4.0, 0.0), 3.3e38,
+                     -3.4e38, float(np.float32(3.4028235e38)) * (1 - 2 ** -25), 1e-40, -3e-45, 1e-46,
+                     0.0, -0.0, 1.1754942e-38, 1.1754944e-38, 5.877472e-39, 3.5e38, -1e39,
+                     1.401298464324817e-45 * 0.5, 1.401298464324817e-45 * 0.75, 1.401298464324817e-45 * 1.5])
+    vv[3000:3000 + edge.size] = edge
+    p = imrp.params_from_workload(w, N=n, precision=1)
+    with imrp.Sim(p) as sim:
+        sim.load(x, v)
+        xg, vg = sim.particles()
+    with np.errstate(over="ignore"):
+        xf, vf = x.astype(np.float32), v.astype(np.float32)
+    np.testing.assert_array_equal(xg, xf.astype(np.float64))
+    np.testing.assert_array_equal(vg, vf.astype(np.float64))
+    assert np.array_equal(np.signbit(vg), np.signbit(vf))
+
+
 def test_large_sampled_parity_fp64(imrp):
     """FP64 at N = 2e6, l_max = 8: the moments kernel's 1024-particle blocks
     (an FP64 instance this large fills the GPU with them; smaller FP64
