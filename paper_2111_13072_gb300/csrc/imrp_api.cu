@@ -552,6 +552,7 @@ int imrp_create(const imrp_params* p, imrp_ctx** out) {
   ctx->stream = ctx->own_stream;
   int rc = ctx->prec == 1 ? find_set<float>(ctx->L)->init(ctx->device)
                           : find_set<double>(ctx->L)->init(ctx->device);
+  if (rc == 0 && set_sort_attributes() != cudaSuccess) rc = 1;
   if (rc != 0) { free_all(ctx); delete ctx; return IMRP_E_CUDA; }
   // warps per CTA of the field kernel: the largest of 8, 4, 2, 1 whose
   // resident warps per SM reach 85% of the best. Larger CTAs keep their warps

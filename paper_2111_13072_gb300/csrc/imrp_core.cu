@@ -180,11 +180,192 @@ __global__ void __launch_bounds__(kSortThreads, 7) k_sort_scatter(
   }
 }
 
+// Sort of one top-byte bucket by the three low key bytes, in one CTA. The
+// first pass of the sort (on the top byte, over the whole array) leaves the
+// keys of bucket b contiguous and in their input order; this CTA then runs
+// three stable LSD passes over its bucket, bytes 0, 1, 2, which need no
+// global synchronisation: in shared memory when the bucket fits (loaded once,
+// written once), else between the two global key/value buffers (in L2; the
+// CTA alone touches that range). A pass: the scan of the byte's digit counts,
+// then the bucket in chunks of 4096 keys in order; each warp ranks its 256
+// keys (item i of lane l is chunk slot 256 w + 32 i + l) against its running
+// digit counts, the warps' counts are scanned per digit, and each key goes to
+// (digit start) + (keys of that digit in earlier chunks and warps) + (its rank
+// in its warp): stable. The next byte's counts are gathered as keys are placed.
+// The result is the permutation of a stable LSD sort on all four bytes.
+constexpr int kBsThreads = 512;
+constexpr int kBsWarps = kBsThreads / 32;
+constexpr int kBsItems = 8;
+constexpr int kBsChunk = kBsThreads * kBsItems;
+
+struct BsShared {
+  uint32_t cnt[2][256];              // digit counts of this pass's byte and of the next
+  uint32_t dst[256];                 // output place of the next key of digit d
+  uint16_t whist[kBsWarps][256];     // per-warp counts, then the counts of earlier warps
+  uint32_t wsum[8];
+};
+
+// One pass over len keys (slots 0 .. len-1 of ki/vi into ko/vo), digit =
+// byte at `shift`; cnt: this byte's counts; cnx (or null): zeroed here, then
+// the counts of the byte at shift + 8.
+template <class K>
+__device__ __forceinline__ void bucket_pass(const K* ki, const K* vi, K* ko, K* vo, int64_t len, int shift,
+                                            const uint32_t* cnt, uint32_t* cnx, BsShared& sh) {
+  const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t c = 0, s1 = 0;
+  if (t < 256) {
+    c = cnt[t];
+    s1 = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, s1, o);
+      if (lane >= unsigned(o)) s1 += x;
+    }
+    if (lane == 31) sh.wsum[warp] = s1;
+    if (cnx) cnx[t] = 0u;
+  }
+  __syncthreads();
+  if (t < 256) {
+    uint32_t off = 0;
+    for (unsigned w = 0; w < warp; ++w) off += sh.wsum[w];
+    sh.dst[t] = off + s1 - c;
+  }
+  for (int64_t c0 = 0; c0 < len; c0 += kBsChunk) {
+    for (int k = t; k < kBsWarps * 256; k += kBsThreads) (&sh.whist[0][0])[k] = 0;
+    __syncthreads();
+    const int64_t wb = c0 + int64_t(warp) * (32 * kBsItems);
+    uint32_t key[kBsItems], val[kBsItems];
+    uint32_t wrank[kBsItems / 2] = {};
+#pragma unroll
+    for (int i = 0; i < kBsItems; ++i) {
+      const int64_t idx = wb + 32 * i + lane;
+      key[i] = idx < len ? ki[idx] : 0u;
+      val[i] = idx < len ? vi[idx] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kBsItems; ++i) {
+      const bool ok = wb + 32 * i + lane < len;
+      const unsigned d = ok ? ((key[i] >> shift) & 255u) : 256u;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const unsigned before = ok ? unsigned(sh.whist[warp][d]) : 0u;
+      wrank[i / 2] |= (before + __popc(peers & lt)) << (16 * (i % 2));
+      __syncwarp();
+      if (ok && lane == unsigned(__ffs(peers) - 1)) sh.whist[warp][d] = uint16_t(before + __popc(peers));
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t total = 0;
+    if (t < 256) {
+#pragma unroll
+      for (int w = 0; w < kBsWarps; ++w) {
+        const uint32_t x = sh.whist[w][t];
+        sh.whist[w][t] = uint16_t(total);
+        total += x;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kBsItems; ++i) {
+      if (wb + 32 * i + lane < len) {
+        const unsigned d = (key[i] >> shift) & 255u;
+        const uint32_t g = sh.dst[d] + sh.whist[warp][d] + ((wrank[i / 2] >> (16 * (i % 2))) & 0xffffu);
+        ko[g] = key[i];
+        vo[g] = val[i];
+        if (cnx) atomicAdd(&cnx[(key[i] >> (shift + 8)) & 255u], 1u);
+      }
+    }
+    __syncthreads();
+    if (t < 256) sh.dst[t] += total;
+  }
+  __syncthreads();  // this pass's writes are visible to the CTA's next pass
+}
+
+// cap: the largest bucket sorted in shared memory (dynamic shared memory of
+// 16 cap bytes: two key and two value buffers)
+__global__ void __launch_bounds__(kBsThreads, 2) k_bucket_sort(uint32_t* k1, uint32_t* v1, uint32_t* k0, uint32_t* v0,
+                                                           const uint32_t* __restrict__ rowtot, int cap) {
+  extern __shared__ __align__(16) uint32_t sbuf[];
+  __shared__ BsShared sh;
+  __shared__ int64_t s_start;
+  const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const unsigned b = blockIdx.x;
+  // bucket start: the sizes of the buckets before b
+  if (t < 256) {
+    uint32_t v = t < b ? rowtot[t] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh.wsum[warp] = v;
+    sh.cnt[0][t] = 0u;
+  }
+  __syncthreads();
+  if (t == 0) {
+    int64_t a = 0;
+    for (int w = 0; w < 8; ++w) a += sh.wsum[w];
+    s_start = a;
+  }
+  __syncthreads();
+  const int64_t start = s_start;
+  const int64_t len = rowtot[b];
+  if (len == 0) return;  // uniform over the CTA
+  uint32_t *gk1 = k1 + start, *gv1 = v1 + start, *gk0 = k0 + start, *gv0 = v0 + start;
+  if (len <= cap) {
+    uint32_t *ka = sbuf, *va = sbuf + cap, *kb = sbuf + 2 * cap, *vb = sbuf + 3 * cap;
+    for (int64_t i = t; i < len; i += kBsThreads) {
+      const uint32_t k = gk1[i];
+      ka[i] = k;
+      va[i] = gv1[i];
+      atomicAdd(&sh.cnt[0][k & 255u], 1u);
+    }
+    __syncthreads();
+    bucket_pass(ka, va, kb, vb, len, 0, sh.cnt[0], sh.cnt[1], sh);
+    bucket_pass(kb, vb, ka, va, len, 8, sh.cnt[1], sh.cnt[0], sh);
+    bucket_pass(ka, va, kb, vb, len, 16, sh.cnt[0], nullptr, sh);
+    for (int64_t i = t; i < len; i += kBsThreads) {
+      gk0[i] = kb[i];
+      gv0[i] = vb[i];
+    }
+  } else {
+    for (int64_t i = t; i < len; i += kBsThreads) atomicAdd(&sh.cnt[0][gk1[i] & 255u], 1u);
+    __syncthreads();
+    bucket_pass(gk1, gv1, gk0, gv0, len, 0, sh.cnt[0], sh.cnt[1], sh);
+    bucket_pass(gk0, gv0, gk1, gv1, len, 8, sh.cnt[1], sh.cnt[0], sh);
+    bucket_pass(gk1, gv1, gk0, gv0, len, 16, sh.cnt[0], nullptr, sh);
+  }
+}
+
+// Largest N for the bucket sort: the buckets of a uniform shell (density in
+// r^2 up to 1.45 times its mean) must fit the shared-memory capacity; beyond
+// it they take the global path, and one CTA's share of the work outweighs the
+// saved passes (N = 4e6: 0.256 ms against 0.222 for the four global passes;
+// N = 1.6e7: 0.91 against 0.74 ms).
+constexpr int64_t kBucketSortMaxN = 2250000;
+constexpr int kBsCapMax = 13312;  // 208 KB of buckets beside the static shared memory
+inline int bucket_cap(int64_t n) {
+  int64_t c = (3 * (n / 256) + 511) / 512 * 512;
+  if (c < 2048) c = 2048;
+  return int(c < kBsCapMax ? c : kBsCapMax);
+}
+
+cudaError_t set_sort_attributes() {
+  return cudaFuncSetAttribute(k_bucket_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kBsCapMax);
+}
+
 const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
                                   int64_t n, int first_byte, cudaStream_t s) {
   if (n <= 1) return v0;
   const int64_t nblk = sort_blocks(n);
   uint32_t* rowtot = hist + 256 * nblk;
+  if (first_byte == 0 && n <= kBucketSortMaxN) {
+    // the top byte over the whole array into 256 contiguous buckets (k0 -> k1),
+    // then the three low bytes per bucket (into k0)
+    const int cap = bucket_cap(n);
+    k_sort_hist<<<unsigned(nblk), kSortThreads, 0, s>>>(k0, n, 24, nblk, hist);
+    k_sort_rowscan<<<256, 256, 0, s>>>(hist, nblk, rowtot);
+    k_sort_scatter<<<unsigned(nblk), kSortThreads, 0, s>>>(k0, v0, k1, v1, n, 24, nblk, hist, rowtot);
+    k_bucket_sort<<<256, kBsThreads, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, cap);
+    return v0;
+  }
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int pass = first_byte; pass < 4; ++pass) {
     const int shift = 8 * pass;
@@ -754,6 +935,7 @@ template <class T> cudaError_t preload_core_kernels_t() {
 }
 
 cudaError_t preload_core_kernels() {
+  if (set_sort_attributes() != cudaSuccess) return cudaErrorInvalidValue;
   cudaFuncAttributes fa;
   const void* fns[] = {reinterpret_cast<const void*>(&k_sort_hist), reinterpret_cast<const void*>(&k_sort_rowscan),
                        reinterpret_cast<const void*>(&k_sort_scatter), reinterpret_cast<const void*>(&k_finalize),

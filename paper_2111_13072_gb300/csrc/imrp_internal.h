@@ -113,6 +113,9 @@ void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 // load reserves device memory): the allocation-free entry point calls it at
 // its set-up so that later calls load nothing.
 cudaError_t preload_core_kernels();
+// opt-in shared memory of the sort's bucket kernel (once per device, before
+// the first sort)
+cudaError_t set_sort_attributes();
 void launch_init_step(StepState* st, cudaStream_t s);
 
 // Spectrum sums: Qh[j] = dt sum_n (q_n - q_0) e^{-i w_j t_n},
