@@ -33,7 +33,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s at N=2e6,l_max=16 (mixed vs FP64); served spectra p50/p99"
 UNIT = "particle-steps/s"
-LAUNCHES_PER_STEP = 19  # 12 sort + reorder + moments + tile scan + 2 group scan + finalize + field
+BUCKET_SORT_MAX_N = 2250000  # the library sorts up to this many keys in 4 launches, more in 12
+
+
+def sort_launches(n):
+    """Kernel launches of one radius sort of n keys: the top-byte pass (histogram,
+    row scan, scatter) and the per-bucket kernel up to BUCKET_SORT_MAX_N keys, four
+    such passes (12 launches) beyond."""
+    return 0 if n <= 1 else (4 if n <= BUCKET_SORT_MAX_N else 12)
+
+
+def step_launches(n):
+    """Kernel launches of one step of one instance: sort, reorder, moments, tile
+    scan, two group-scan kernels, finalize, field."""
+    return sort_launches(n) + 7
 
 
 def workload_desc(w):
@@ -285,7 +298,11 @@ def ensemble_measure(steps, warmup, autotune=True, n_instances=64, stream=None):
     ntot = sum(w.N for w in ws)
     for s in sims:
         s.close()
+    # per context: sort, reorder, tile scan, two group-scan kernels, finalize;
+    # per degree and precision: one moments and one field launch
+    launches = sum(sort_launches(w.N) + 5 for w in ws) + 2 * len({(w.precision, w.l_max) for w in ws})
     return {"value": ntot * steps / (ms / 1e3), "unit": UNIT, "instances": n_instances,
+            "gpu_launches_per_step": launches,
             "particles": ntot, "steps": steps, "ms_per_step": ms / steps, "autotuned": autotune,
             "workload": "64 instances, N log-uniform [1e4,1e6], T_e U[0.5,5] eV, n_e log-U[1e14,1e17], "
                         "l_max in {8,12,16}, mixed precision, one captured graph per step pair, "
@@ -485,7 +502,7 @@ def sub_config(name, steps, warmup, nprof, peak_tflops, stream):
     out = {"workload": workload_desc(w), "value": w.N * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
            "warmup": warmup, "ms_per_step": ms / steps, "dtype": "f32" if w.precision else "f64",
            "stage_ms_per_step": {k: v / nprof for k, v in stages.items()},
-           "gpu_launches": LAUNCHES_PER_STEP * steps}
+           "gpu_launches": step_launches(w.N) * steps}
     if w.precision:
         ach = field_flops_per_particle(w.l_max) * w.N / (field_ms / 1e3) / 1e12
         ach24 = 24.0 * K * w.N / (field_ms / 1e3) / 1e12
@@ -539,7 +556,7 @@ def main():
                     "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
                     "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                     "config": {"workload": r["workload"], "particles": r["particles"]},
-                    "clocks": clk.summary(), "gpu_launches": LAUNCHES_PER_STEP * 64 * args.steps}
+                    "clocks": clk.summary(), "gpu_launches": r["gpu_launches_per_step"] * args.steps}
         else:
             r = serving_measure(max(4, args.steps // 50), args.steps)
             line = {"metric": "served spectra p50/p99 latency", "value": r["p50_s"], "unit": "s",
@@ -707,7 +724,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (per-step working set > 300 MB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks, "fp64_gpu": fp64,
+                "gpu_launches": step_launches(N) * args.steps, "clocks": clocks, "fp64_gpu": fp64,
                 "oracle_err": oerr, "configs": subs, "serving": serving, "ensemble": ensemble,
                 "drude": drude}
         print(json.dumps(line), flush=True)
