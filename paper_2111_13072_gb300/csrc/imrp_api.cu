@@ -305,7 +305,7 @@ template <class T> FieldArgs<T> make_field_args(imrp_ctx* ctx, bool record) {
 // stale), sort and reorder; then the moments; then the scans and finalize;
 // then the field. The batch runs the moments and the field of many contexts
 // as one launch each (per degree and precision) between the others.
-template <class T> void enqueue_pre(imrp_ctx* ctx, cudaEvent_t* ev = nullptr) {
+template <class T> void enqueue_pre(imrp_ctx* ctx, cudaEvent_t* ev = nullptr, bool shared_gpu = false) {
   cudaStream_t s = ctx->stream;
   const int64_t n = ctx->n;
   Part<T>* st = state_of<T>(ctx);
@@ -314,7 +314,7 @@ template <class T> void enqueue_pre(imrp_ctx* ctx, cudaEvent_t* ev = nullptr) {
   }
   if (ev) cudaEventRecord(ev[0], s);
   const uint32_t* perm = launch_radix_sort(ctx->key0, ctx->idx0, ctx->key1, ctx->idx1, ctx->hist, n,
-                                           sort_first_byte(ctx->prec), s);
+                                           sort_first_byte(ctx->prec), s, shared_gpu);
   if (ev) cudaEventRecord(ev[1], s);
   launch_reorder<T>(st, sorted_ptrs<T>(ctx), ctx->srt_id, perm, n, s);
 }
@@ -1198,8 +1198,8 @@ int enqueue_batch_step(imrp_batch* b) {
   for (int i = 0; i < n; ++i) {
     imrp_ctx* ctx = b->c[i];
     cudaStreamWaitEvent(ctx->stream, b->fork, 0);
-    if (ctx->prec == 1) enqueue_pre<float>(ctx);
-    else enqueue_pre<double>(ctx);
+    if (ctx->prec == 1) enqueue_pre<float>(ctx, nullptr, true);
+    else enqueue_pre<double>(ctx, nullptr, true);
     cudaEventRecord(b->join[i], ctx->stream);
     cudaStreamWaitEvent(b->stream, b->join[i], 0);
   }

@@ -193,24 +193,22 @@ __global__ void __launch_bounds__(kSortThreads, 7) k_sort_scatter(
 // (digit start) + (keys of that digit in earlier chunks and warps) + (its rank
 // in its warp): stable. The next byte's counts are gathered as keys are placed.
 // The result is the permutation of a stable LSD sort on all four bytes.
-constexpr int kBsThreads = 512;
-constexpr int kBsWarps = kBsThreads / 32;
 constexpr int kBsItems = 8;
-constexpr int kBsChunk = kBsThreads * kBsItems;
 
-struct BsShared {
+template <int NT> struct BsShared {
   uint32_t cnt[2][256];              // digit counts of this pass's byte and of the next
   uint32_t dst[256];                 // output place of the next key of digit d
-  uint16_t whist[kBsWarps][256];     // per-warp counts, then the counts of earlier warps
+  uint16_t whist[NT / 32][256];      // per-warp counts, then the counts of earlier warps
   uint32_t wsum[8];
 };
 
 // One pass over len keys (slots 0 .. len-1 of ki/vi into ko/vo), digit =
 // byte at `shift`; cnt: this byte's counts; cnx (or null): zeroed here, then
 // the counts of the byte at shift + 8.
-template <class K>
+template <int NT, class K>
 __device__ __forceinline__ void bucket_pass(const K* ki, const K* vi, K* ko, K* vo, int64_t len, int shift,
-                                            const uint32_t* cnt, uint32_t* cnx, BsShared& sh) {
+                                            const uint32_t* cnt, uint32_t* cnx, BsShared<NT>& sh) {
+  constexpr int kWarps = NT / 32, kChunk = NT * kBsItems;
   const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const unsigned lt = (1u << lane) - 1u;
   uint32_t c = 0, s1 = 0;
@@ -231,8 +229,8 @@ __device__ __forceinline__ void bucket_pass(const K* ki, const K* vi, K* ko, K* 
     for (unsigned w = 0; w < warp; ++w) off += sh.wsum[w];
     sh.dst[t] = off + s1 - c;
   }
-  for (int64_t c0 = 0; c0 < len; c0 += kBsChunk) {
-    for (int k = t; k < kBsWarps * 256; k += kBsThreads) (&sh.whist[0][0])[k] = 0;
+  for (int64_t c0 = 0; c0 < len; c0 += kChunk) {
+    for (int k = t; k < kWarps * 256; k += NT) (&sh.whist[0][0])[k] = 0;
     __syncthreads();
     const int64_t wb = c0 + int64_t(warp) * (32 * kBsItems);
     uint32_t key[kBsItems], val[kBsItems];
@@ -258,7 +256,7 @@ __device__ __forceinline__ void bucket_pass(const K* ki, const K* vi, K* ko, K* 
     uint32_t total = 0;
     if (t < 256) {
 #pragma unroll
-      for (int w = 0; w < kBsWarps; ++w) {
+      for (int w = 0; w < kWarps; ++w) {
         const uint32_t x = sh.whist[w][t];
         sh.whist[w][t] = uint16_t(total);
         total += x;
@@ -281,56 +279,95 @@ __device__ __forceinline__ void bucket_pass(const K* ki, const K* vi, K* ko, K* 
   __syncthreads();  // this pass's writes are visible to the CTA's next pass
 }
 
-// cap: the largest bucket sorted in shared memory (dynamic shared memory of
-// 16 cap bytes: two key and two value buffers)
-__global__ void __launch_bounds__(kBsThreads, 2) k_bucket_sort(uint32_t* k1, uint32_t* v1, uint32_t* k0, uint32_t* v0,
-                                                           const uint32_t* __restrict__ rowtot, int cap) {
+// cap: the largest segment sorted in shared memory (dynamic shared memory of
+// 16 cap bytes: two key and two value buffers). With rowtot, CTA c sorts the
+// top-byte buckets g c .. g c + g - 1 of k1/v1 into k0/v0: by bytes 0..2 when
+// g = 1, by all four bytes when a CTA takes several buckets (small instances:
+// fewer, fuller CTAs). Without rowtot (one CTA, n_single <= cap), the whole
+// array k0/v0 by all four bytes, in place.
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_bucket_sort(uint32_t* k1, uint32_t* v1, uint32_t* k0,
+                                                              uint32_t* v0, const uint32_t* __restrict__ rowtot,
+                                                              int64_t n_single, int cap, int g) {
   extern __shared__ __align__(16) uint32_t sbuf[];
-  __shared__ BsShared sh;
-  __shared__ int64_t s_start;
+  __shared__ BsShared<NT> sh;
+  __shared__ uint32_t s_len[8];
+  __shared__ int64_t s_start, s_n;
   const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const unsigned b = blockIdx.x;
-  // bucket start: the sizes of the buckets before b
+  const unsigned b0 = blockIdx.x * unsigned(g), b1 = b0 + unsigned(g);
+  // segment start and length: the sizes of the buckets before it and in it
   if (t < 256) {
-    uint32_t v = t < b ? rowtot[t] : 0u;
+    uint32_t v = (rowtot && t < b0) ? rowtot[t] : 0u;
+    uint32_t w = (rowtot && t >= b0 && t < b1) ? rowtot[t] : 0u;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh.wsum[warp] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+      v += __shfl_down_sync(0xffffffffu, v, o);
+      w += __shfl_down_sync(0xffffffffu, w, o);
+    }
+    if (lane == 0) {
+      sh.wsum[warp] = v;
+      s_len[warp] = w;
+    }
     sh.cnt[0][t] = 0u;
   }
   __syncthreads();
   if (t == 0) {
-    int64_t a = 0;
-    for (int w = 0; w < 8; ++w) a += sh.wsum[w];
+    int64_t a = 0, m = 0;
+    for (int k = 0; k < 8; ++k) {
+      a += sh.wsum[k];
+      m += s_len[k];
+    }
     s_start = a;
+    s_n = m;
   }
   __syncthreads();
+  const bool single = rowtot == nullptr;
   const int64_t start = s_start;
-  const int64_t len = rowtot[b];
+  const int64_t len = single ? n_single : s_n;
   if (len == 0) return;  // uniform over the CTA
-  uint32_t *gk1 = k1 + start, *gv1 = v1 + start, *gk0 = k0 + start, *gv0 = v0 + start;
+  const bool all4 = single || g > 1;  // the segment spans several top bytes
+  const uint32_t *sk = single ? k0 : k1 + start, *sv = single ? v0 : v1 + start;
+  uint32_t *gk0 = k0 + start, *gv0 = v0 + start, *gk1 = k1 + start, *gv1 = v1 + start;
   if (len <= cap) {
     uint32_t *ka = sbuf, *va = sbuf + cap, *kb = sbuf + 2 * cap, *vb = sbuf + 3 * cap;
-    for (int64_t i = t; i < len; i += kBsThreads) {
-      const uint32_t k = gk1[i];
+    for (int64_t i = t; i < len; i += NT) {
+      const uint32_t k = sk[i];
       ka[i] = k;
-      va[i] = gv1[i];
+      va[i] = sv[i];
       atomicAdd(&sh.cnt[0][k & 255u], 1u);
     }
     __syncthreads();
-    bucket_pass(ka, va, kb, vb, len, 0, sh.cnt[0], sh.cnt[1], sh);
-    bucket_pass(kb, vb, ka, va, len, 8, sh.cnt[1], sh.cnt[0], sh);
-    bucket_pass(ka, va, kb, vb, len, 16, sh.cnt[0], nullptr, sh);
-    for (int64_t i = t; i < len; i += kBsThreads) {
-      gk0[i] = kb[i];
-      gv0[i] = vb[i];
+    bucket_pass<NT>(ka, va, kb, vb, len, 0, sh.cnt[0], sh.cnt[1], sh);
+    bucket_pass<NT>(kb, vb, ka, va, len, 8, sh.cnt[1], sh.cnt[0], sh);
+    if (all4) {
+      bucket_pass<NT>(ka, va, kb, vb, len, 16, sh.cnt[0], sh.cnt[1], sh);
+      bucket_pass<NT>(kb, vb, ka, va, len, 24, sh.cnt[1], nullptr, sh);
+      for (int64_t i = t; i < len; i += NT) {
+        gk0[i] = ka[i];
+        gv0[i] = va[i];
+      }
+    } else {
+      bucket_pass<NT>(ka, va, kb, vb, len, 16, sh.cnt[0], nullptr, sh);
+      for (int64_t i = t; i < len; i += NT) {
+        gk0[i] = kb[i];
+        gv0[i] = vb[i];
+      }
     }
-  } else {
-    for (int64_t i = t; i < len; i += kBsThreads) atomicAdd(&sh.cnt[0][gk1[i] & 255u], 1u);
+  } else {  // a segment (never the single array) larger than cap: through L2
+    for (int64_t i = t; i < len; i += NT) atomicAdd(&sh.cnt[0][gk1[i] & 255u], 1u);
     __syncthreads();
-    bucket_pass(gk1, gv1, gk0, gv0, len, 0, sh.cnt[0], sh.cnt[1], sh);
-    bucket_pass(gk0, gv0, gk1, gv1, len, 8, sh.cnt[1], sh.cnt[0], sh);
-    bucket_pass(gk1, gv1, gk0, gv0, len, 16, sh.cnt[0], nullptr, sh);
+    bucket_pass<NT>(gk1, gv1, gk0, gv0, len, 0, sh.cnt[0], sh.cnt[1], sh);
+    bucket_pass<NT>(gk0, gv0, gk1, gv1, len, 8, sh.cnt[1], sh.cnt[0], sh);
+    if (all4) {
+      bucket_pass<NT>(gk1, gv1, gk0, gv0, len, 16, sh.cnt[0], sh.cnt[1], sh);
+      bucket_pass<NT>(gk0, gv0, gk1, gv1, len, 24, sh.cnt[1], nullptr, sh);
+      for (int64_t i = t; i < len; i += NT) {
+        gk0[i] = gk1[i];
+        gv0[i] = gv1[i];
+      }
+    } else {
+      bucket_pass<NT>(gk1, gv1, gk0, gv0, len, 16, sh.cnt[0], nullptr, sh);
+    }
   }
 }
 
@@ -341,29 +378,49 @@ __global__ void __launch_bounds__(kBsThreads, 2) k_bucket_sort(uint32_t* k1, uin
 // N = 1.6e7: 0.91 against 0.74 ms).
 constexpr int64_t kBucketSortMaxN = 2250000;
 constexpr int kBsCapMax = 13312;  // 208 KB of buckets beside the static shared memory
-inline int bucket_cap(int64_t n) {
-  int64_t c = (3 * (n / 256) + 511) / 512 * 512;
+constexpr int64_t kBsSmallN = 1 << 19;  // up to here, CTAs of 256 threads (buckets of ~2048 keys)
+constexpr int64_t kBsSingleN = 3072;     // up to here, one CTA sorts everything (N = 1000: 13 us)
+// shared-memory capacity: three times the mean segment of g buckets
+inline int bucket_cap(int64_t n, int g) {
+  int64_t c = (3 * (int64_t(g) * n / 256) + 511) / 512 * 512;
   if (c < 2048) c = 2048;
   return int(c < kBsCapMax ? c : kBsCapMax);
 }
 
 cudaError_t set_sort_attributes() {
-  return cudaFuncSetAttribute(k_bucket_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kBsCapMax);
+  const cudaError_t e = cudaFuncSetAttribute(k_bucket_sort<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             16 * kBsCapMax);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_bucket_sort<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kBsCapMax);
 }
 
 const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
-                                  int64_t n, int first_byte, cudaStream_t s) {
+                                  int64_t n, int first_byte, cudaStream_t s, bool shared_gpu) {
   if (n <= 1) return v0;
   const int64_t nblk = sort_blocks(n);
   uint32_t* rowtot = hist + 256 * nblk;
+  if (first_byte == 0 && n <= kBsSingleN) {
+    // one CTA sorts the whole array in shared memory, all four bytes
+    const int cap = int((n + 255) / 256 * 256);
+    k_bucket_sort<256><<<1, 256, size_t(16) * cap, s>>>(k1, v1, k0, v0, nullptr, n, cap, 256);
+    return v0;
+  }
   if (first_byte == 0 && n <= kBucketSortMaxN) {
     // the top byte over the whole array into 256 contiguous buckets (k0 -> k1),
-    // then the three low bytes per bucket (into k0)
-    const int cap = bucket_cap(n);
+    // then the three low bytes per bucket (into k0). Alone on the GPU, one CTA
+    // per bucket (the most parallel); sharing it (a batch), a small instance
+    // takes segments of several buckets, about 2048 keys per CTA (fewer CTAs,
+    // all four bytes each): the same permutation either way
+    int g = 1;
+    while (shared_gpu && g < 256 && int64_t(g) * 2 * n <= int64_t(2048) * 256) g *= 2;
+    const int cap = bucket_cap(n, g);
     k_sort_hist<<<unsigned(nblk), kSortThreads, 0, s>>>(k0, n, 24, nblk, hist);
     k_sort_rowscan<<<256, 256, 0, s>>>(hist, nblk, rowtot);
     k_sort_scatter<<<unsigned(nblk), kSortThreads, 0, s>>>(k0, v0, k1, v1, n, 24, nblk, hist, rowtot);
-    k_bucket_sort<<<256, kBsThreads, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, cap);
+    if (n <= kBsSmallN)
+      k_bucket_sort<256><<<unsigned(256 / g), 256, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, 0, cap, g);
+    else
+      k_bucket_sort<512><<<256, 512, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, 0, cap, 1);
     return v0;
   }
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;

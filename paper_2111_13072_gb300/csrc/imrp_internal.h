@@ -55,7 +55,8 @@ inline int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; 
 // so even radii that FP32 arithmetic cannot tell apart are ordered exactly.
 inline int sort_first_byte(int) { return 0; }
 const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
-                                  int64_t n, int first_byte, cudaStream_t s);
+                                  int64_t n, int first_byte, cudaStream_t s,
+                                  bool shared_gpu = false);
 
 // ---- state movement and keys (imrp_core.cu) ---------------------------------
 // The state is an array of Part<T> records in the order of the last push (or
