@@ -33,14 +33,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s at N=2e6,l_max=16 (mixed vs FP64); served spectra p50/p99"
 UNIT = "particle-steps/s"
-BUCKET_SORT_MAX_N = 2250000  # the library sorts up to this many keys in 4 launches, more in 12
+BUCKET_SORT_SINGLE_N = 3072  # the library sorts up to this many keys in 1 launch,
+BUCKET_SORT_MAX_N = 2250000  # up to this many in 4, more in 12
 
 
 def sort_launches(n):
-    """Kernel launches of one radius sort of n keys: the top-byte pass (histogram,
-    row scan, scatter) and the per-bucket kernel up to BUCKET_SORT_MAX_N keys, four
-    such passes (12 launches) beyond."""
-    return 0 if n <= 1 else (4 if n <= BUCKET_SORT_MAX_N else 12)
+    """Kernel launches of one radius sort of n keys: one CTA for all of a small
+    array; up to BUCKET_SORT_MAX_N keys the top-byte pass (histogram, row scan,
+    scatter) and the per-bucket kernel; four such passes (12 launches) beyond."""
+    if n <= 1:
+        return 0
+    if n <= BUCKET_SORT_SINGLE_N:
+        return 1
+    return 4 if n <= BUCKET_SORT_MAX_N else 12
 
 
 def step_launches(n):

@@ -12,8 +12,12 @@ def test_sort_launch_rule_matches_the_library():
     src = open(os.path.join(ROOT, "paper_2111_13072_gb300", "csrc", "imrp_core.cu")).read()
     m = re.search(r"constexpr int64_t kBucketSortMaxN = (\d+);", src)
     assert m and int(m.group(1)) == bench.BUCKET_SORT_MAX_N
+    m = re.search(r"constexpr int64_t kBsSingleN = (\d+);", src)
+    assert m and int(m.group(1)) == bench.BUCKET_SORT_SINGLE_N
     assert bench.sort_launches(1) == 0
-    assert bench.sort_launches(2) == 4
+    assert bench.sort_launches(2) == 1
+    assert bench.sort_launches(bench.BUCKET_SORT_SINGLE_N) == 1
+    assert bench.sort_launches(bench.BUCKET_SORT_SINGLE_N + 1) == 4
     assert bench.sort_launches(bench.BUCKET_SORT_MAX_N) == 4
     assert bench.sort_launches(bench.BUCKET_SORT_MAX_N + 1) == 12
     assert bench.step_launches(2_000_000) == 11
