@@ -6,6 +6,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "imrp_device.cuh"
@@ -125,16 +126,19 @@ void launch_dft(const double* q, const double* u, int64_t ns, double dt, double 
                 int64_t nf, double w_max, double* out, cudaStream_t s);
 
 // ---- per-degree kernels (imrp_inst_*.cu) ------------------------------------
-// SMs of the current device (cached per device)
+// SMs of the current device (cached per device; contexts may be created from
+// several host threads, hence the atomics)
 inline int sm_count() {
-  static int cache[64] = {0};
+  static std::atomic<int> cache[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-  if (cache[dev] == 0) {
+  int c = cache[dev].load(std::memory_order_relaxed);
+  if (c == 0) {
     int v = 0;
-    cache[dev] = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0 ? v : 152;
+    c = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0 ? v : 152;
+    cache[dev].store(c, std::memory_order_relaxed);
   }
-  return cache[dev];
+  return c;
 }
 // Particles per thread of the moments kernel for an instance of n particles:
 // 16 (1024 per CTA of 64 threads), or 4 (256 per CTA) for an FP64 instance
