@@ -429,7 +429,7 @@ size_t footprint_bytes(int64_t N, int L, int prec) {
   b += N * (es == 4 ? sizeof(Part<float>) : sizeof(Part<double>));  // state records
   b += 6 * N * es + N * 4;                          // radius-ordered copy + ids
   b += 4 * size_t(N) * 4;                           // keys and slots
-  b += size_t(256 * sort_blocks(N) + 256) * 4;      // histogram
+  b += size_t(sort_hist_words(N)) * 4;              // histogram
   b += 2 * size_t(tile_stride(ntiles) * nc) * es;   // tile sums and in-group scans
   b += size_t(ngroups * nc) * (es + 8) + size_t(nc) * (es + 8);
   b += size_t(gs_work_doubles(int(nc))) * 8 + size_t(gs_col_blocks(int(nc))) * 4;
@@ -451,7 +451,7 @@ int alloc_ctx(imrp_ctx* ctx) {
   CK(cudaMalloc(&ctx->idx0, N * sizeof(uint32_t)));
   CK(cudaMalloc(&ctx->key1, N * sizeof(uint32_t)));
   CK(cudaMalloc(&ctx->idx1, N * sizeof(uint32_t)));
-  CK(cudaMalloc(&ctx->hist, (256 * sort_blocks(N) + 256) * sizeof(uint32_t)));
+  CK(cudaMalloc(&ctx->hist, size_t(sort_hist_words(N)) * sizeof(uint32_t)));
   CK(cudaMalloc(&ctx->agg, tile_stride(ntiles) * nc * es));
   CK(cudaMalloc(&ctx->pfx, tile_stride(ntiles) * nc * es));
   CK(cudaMalloc(&ctx->gbase, ngroups * nc * es));

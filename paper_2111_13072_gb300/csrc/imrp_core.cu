@@ -10,25 +10,34 @@
 namespace imrp {
 
 // ============================================================================
-// Radix sort: stable LSD, 4 passes of 8-bit digits. Each CTA owns
+// Radix sort: stable LSD passes of 8-bit digits, and a wide first pass of
+// 10-bit digits for the bucket sort of large arrays. Each CTA owns
 // kSortTile = 2048 consecutive keys in a striped layout (item i of thread t is
 // key base + i*256 + t), which keeps the slot order (item, warp, lane) equal
-// to the key order, so the local ranks below are stable.
+// to the key order, so the local ranks below are stable. ND: digits of the
+// pass (256 or 1024); hist holds ND rows of nblk block counts.
 // ============================================================================
+template <int ND>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys,
                                                            int64_t n, int shift, int64_t nblk,
                                                            uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
+  __shared__ uint32_t h[ND];
+  for (int d = threadIdx.x; d < ND; d += kSortThreads) h[d] = 0;
   __syncthreads();
   const int64_t base = int64_t(blockIdx.x) * kSortTile;
+  uint32_t k[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const int64_t idx = base + int64_t(i) * kSortThreads + threadIdx.x;
-    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    k[i] = idx < n ? keys[idx] : 0u;
+  }
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const int64_t idx = base + int64_t(i) * kSortThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&h[(k[i] >> shift) & unsigned(ND - 1)], 1u);
   }
   __syncthreads();
-  hist[int64_t(threadIdx.x) * nblk + blockIdx.x] = h[threadIdx.x];
+  for (int d = threadIdx.x; d < ND; d += kSortThreads) hist[int64_t(d) * nblk + blockIdx.x] = h[d];
 }
 
 // Exclusive scan of one digit's row hist[d][0..nblk) in place; the row total
@@ -64,6 +73,24 @@ __global__ void __launch_bounds__(256) k_sort_rowscan(uint32_t* __restrict__ his
   if (threadIdx.x == 0) rowtot[blockIdx.x] = carry;
 }
 
+// Exclusive prefix over the kSortThreads threads of a CTA of the per-thread
+// values v (warp shuffles, then the warp sums through wsum). All threads call
+// it; the caller separates two uses of wsum by a barrier.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* wsum) {
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t s = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= unsigned(o)) s += x;
+  }
+  if (lane == 31) wsum[warp] = s;
+  __syncthreads();
+  uint32_t woff = 0;
+  for (unsigned w = 0; w < warp; ++w) woff += wsum[w];
+  return woff + s - v;
+}
+
 // Scatter of one pass. Warp w of the block owns the keys base + 256 w ..
 // base + 256 w + 255 (item i of lane l is key base + 256 w + 32 i + l), so the
 // order (warp, item, lane) is the key order. The items of a warp are ranked
@@ -72,38 +99,45 @@ __global__ void __launch_bounds__(256) k_sort_rowscan(uint32_t* __restrict__ his
 // (keys of that digit in earlier warps) + (its rank in its warp): stable.
 // The block's keys and slots are staged in shared memory in that order, so
 // that consecutive threads write consecutive positions of each digit's run
-// in the output (coalesced even when the digits are uniformly spread). About
-// 22 KB of shared memory and at most 36 registers per thread: 7 blocks per SM,
-// so all blocks of N = 2e6 keys are resident at once.
-__global__ void __launch_bounds__(kSortThreads, 7) k_sort_scatter(
+// in the output (coalesced even when the digits are uniformly spread). Thread
+// t owns the digits DPT t .. DPT t + DPT - 1 in the per-digit steps. With 256
+// digits about 22 KB of shared memory and at most 36 registers per thread (7
+// blocks per SM, so all blocks of N = 2e6 keys are resident at once); with
+// 1024 digits about 41 KB (5 blocks per SM).
+template <int ND>
+__global__ void __launch_bounds__(kSortThreads, ND == 256 ? 7 : 5) k_sort_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, int64_t nblk,
     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ rowtot) {
   constexpr int kWarps = kSortThreads / 32;
+  constexpr int DPT = ND / kSortThreads;
   static_assert(kSortItems * 32 <= 256 && kSortTile <= 65535, "per-warp counts fit 16 bits");
-  __shared__ uint16_t whist[kWarps][256];
+  __shared__ __align__(16) uint16_t whist[kWarps][ND];
   __shared__ __align__(16) uint32_t sk[kSortTile];
   __shared__ __align__(16) uint32_t sv[kSortTile];
-  __shared__ uint32_t dbase[256];   // global start of digit d for this block
-  __shared__ uint32_t lstart[256];  // block-local start of digit d
+  __shared__ uint32_t dbase[ND];   // global start of digit d for this block
+  __shared__ uint32_t lstart[ND];  // block-local start of digit d
   __shared__ uint32_t wsum[kWarps];
   const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) whist[w][t] = 0;
+  {
+    uint4* z = reinterpret_cast<uint4*>(&whist[0][0]);
+    for (int k = t; k < kWarps * ND * 2 / 16; k += kSortThreads) z[k] = make_uint4(0u, 0u, 0u, 0u);
+  }
   // exclusive scan of the digit totals -> global start of each digit
   {
-    const uint32_t v = rowtot[t];
-    uint32_t s = v;
+    uint32_t c[DPT], sum = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t x = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= unsigned(o)) s += x;
+    for (int k = 0; k < DPT; ++k) {
+      c[k] = rowtot[DPT * t + k];
+      sum += c[k];
     }
-    if (lane == 31) wsum[warp] = s;
-    __syncthreads();
-    uint32_t woff = 0;
-    for (unsigned w = 0; w < warp; ++w) woff += wsum[w];
-    dbase[t] = woff + s - v + hist[int64_t(t) * nblk + blockIdx.x];
+    uint32_t off = block_excl_scan(sum, wsum);
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+      const unsigned d = DPT * t + k;
+      dbase[d] = off + hist[int64_t(d) * nblk + blockIdx.x];
+      off += c[k];
+    }
   }
   const int64_t base = int64_t(blockIdx.x) * kSortTile;
   const int64_t wbase = base + int64_t(warp) * (32 * kSortItems);
@@ -119,7 +153,7 @@ __global__ void __launch_bounds__(kSortThreads, 7) k_sort_scatter(
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const bool ok = wbase + 32 * i + lane < n;
-    const unsigned d = ok ? ((key[i] >> shift) & 255u) : 256u;
+    const unsigned d = ok ? ((key[i] >> shift) & unsigned(ND - 1)) : unsigned(ND);
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const unsigned before = ok ? unsigned(whist[warp][d]) : 0u;
     wrank[i / 4] |= (before + __popc(peers & lt)) << (8 * (i % 4));
@@ -128,38 +162,37 @@ __global__ void __launch_bounds__(kSortThreads, 7) k_sort_scatter(
     __syncwarp();
   }
   __syncthreads();
-  uint32_t total;  // block count of digit t; whist[w][t] becomes the count in warps before w
-  {
+  // block count of each digit of this thread; whist[w][d] becomes the count in warps before w
+  uint32_t total[DPT], tsum = 0;
+#pragma unroll
+  for (int k = 0; k < DPT; ++k) {
+    const unsigned d = DPT * t + k;
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-      const uint32_t c = whist[w][t];
-      whist[w][t] = uint16_t(run);
+      const uint32_t c = whist[w][d];
+      whist[w][d] = uint16_t(run);
       run += c;
     }
-    total = run;
+    total[k] = run;
+    tsum += run;
   }
   // block-local digit starts: exclusive scan of the block counts over d
   {
-    uint32_t s = total;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t x = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= unsigned(o)) s += x;
-    }
     __syncthreads();  // wsum reuse
-    if (lane == 31) wsum[warp] = s;
-    __syncthreads();
-    uint32_t woff = 0;
-    for (unsigned w = 0; w < warp; ++w) woff += wsum[w];
-    lstart[t] = woff + s - total;
+    uint32_t off = block_excl_scan(tsum, wsum);
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+      lstart[DPT * t + k] = off;
+      off += total[k];
+    }
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const int64_t idx = wbase + 32 * i + lane;
     if (idx < n) {
-      const unsigned d = (key[i] >> shift) & 255u;
+      const unsigned d = (key[i] >> shift) & unsigned(ND - 1);
       const uint32_t lpos = lstart[d] + whist[warp][d] + ((wrank[i / 4] >> (8 * (i % 4))) & 255u);
       sk[lpos] = key[i];
       sv[lpos] = vin[idx];
@@ -172,7 +205,7 @@ __global__ void __launch_bounds__(kSortThreads, 7) k_sort_scatter(
     const int p = i * kSortThreads + int(t);
     if (p < nvalid) {
       const uint32_t k = sk[p];
-      const unsigned d = (k >> shift) & 255u;
+      const unsigned d = (k >> shift) & unsigned(ND - 1);
       const uint32_t g = dbase[d] + (uint32_t(p) - lstart[d]);
       kout[g] = k;
       vout[g] = sv[p];
@@ -180,19 +213,22 @@ __global__ void __launch_bounds__(kSortThreads, 7) k_sort_scatter(
   }
 }
 
-// Sort of one top-byte bucket by the three low key bytes, in one CTA. The
-// first pass of the sort (on the top byte, over the whole array) leaves the
-// keys of bucket b contiguous and in their input order; this CTA then runs
-// three stable LSD passes over its bucket, bytes 0, 1, 2, which need no
-// global synchronisation: in shared memory when the bucket fits (loaded once,
-// written once), else between the two global key/value buffers (in L2; the
-// CTA alone touches that range). A pass: the scan of the byte's digit counts,
-// then the bucket in chunks of 4096 keys in order; each warp ranks its 256
-// keys (item i of lane l is chunk slot 256 w + 32 i + l) against its running
-// digit counts, the warps' counts are scanned per digit, and each key goes to
-// (digit start) + (keys of that digit in earlier chunks and warps) + (its rank
-// in its warp): stable. The next byte's counts are gathered as keys are placed.
-// The result is the permutation of a stable LSD sort on all four bytes.
+// Sort of one top-digit bucket by the key bits below the digit, in one CTA.
+// The first pass of the sort (on the top byte, or on the top 10 bits, over the
+// whole array) leaves the keys of bucket b contiguous and in their input
+// order; this CTA then runs three stable LSD passes over its bucket, bytes 0,
+// 1, 2 (with a 10-bit top digit the two top bits of byte 2 are the same for
+// the whole bucket), which need no global synchronisation: in shared memory
+// when the bucket fits (the first pass reads the bucket from global memory,
+// the last writes it back), else between the two global key/value buffers (in
+// L2; the CTA alone touches that range). A pass: the scan of the byte's digit
+// counts, then the bucket in chunks of NT * kBsItems keys in order; each warp
+// ranks its 256 keys (item i of lane l is chunk slot 256 w + 32 i + l) against
+// its running digit counts, the warps' counts are scanned per digit, and each
+// key goes to (digit start) + (keys of that digit in earlier chunks and warps)
+// + (its rank in its warp): stable. The next byte's counts are gathered as
+// keys are placed. The result is the permutation of a stable LSD sort on all
+// four bytes.
 constexpr int kBsItems = 8;
 
 template <int NT> struct BsShared {
@@ -279,16 +315,33 @@ __device__ __forceinline__ void bucket_pass(const K* ki, const K* vi, K* ko, K* 
   __syncthreads();  // this pass's writes are visible to the CTA's next pass
 }
 
-// cap: the largest segment sorted in shared memory (dynamic shared memory of
-// 16 cap bytes: two key and two value buffers). With rowtot, CTA c sorts the
-// top-byte buckets g c .. g c + g - 1 of k1/v1 into k0/v0: by bytes 0..2 when
-// g = 1, by all four bytes when a CTA takes several buckets (small instances:
-// fewer, fuller CTAs). Without rowtot (one CTA, n_single <= cap), the whole
-// array k0/v0 by all four bytes, in place.
+// Counts of the low byte of keys[0 .. len) into cnt (loads in flight together).
 template <int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_bucket_sort(uint32_t* k1, uint32_t* v1, uint32_t* k0,
-                                                              uint32_t* v0, const uint32_t* __restrict__ rowtot,
-                                                              int64_t n_single, int cap, int g) {
+__device__ __forceinline__ void count_low_byte(const uint32_t* keys, int64_t len, uint32_t* cnt) {
+  for (int64_t i0 = 0; i0 < len; i0 += int64_t(NT) * kBsItems) {
+    uint32_t k[kBsItems];
+#pragma unroll
+    for (int i = 0; i < kBsItems; ++i) {
+      const int64_t idx = i0 + int64_t(i) * NT + threadIdx.x;
+      k[i] = idx < len ? keys[idx] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kBsItems; ++i)
+      if (i0 + int64_t(i) * NT + threadIdx.x < len) atomicAdd(&cnt[k[i] & 255u], 1u);
+  }
+}
+
+// cap: the largest segment sorted in shared memory (dynamic shared memory of
+// 16 cap bytes: two key and two value buffers). With rowtot (nd digit totals
+// of the first pass), CTA c sorts the top-digit buckets g c .. g c + g - 1 of
+// k1/v1 into k0/v0: by bytes 0..2 when g = 1, by all four bytes when a CTA
+// takes several buckets (small instances: fewer, fuller CTAs). Without rowtot
+// (one CTA, n_single <= cap), the whole array k0/v0 by all four bytes, in
+// place. MINB: resident CTAs per SM asked of the register allocation.
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_bucket_sort(uint32_t* k1, uint32_t* v1, uint32_t* k0, uint32_t* v0,
+                                                          const uint32_t* __restrict__ rowtot, int64_t n_single,
+                                                          int cap, int g, int nd) {
   extern __shared__ __align__(16) uint32_t sbuf[];
   __shared__ BsShared<NT> sh;
   __shared__ uint32_t s_len[8];
@@ -296,9 +349,18 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_bucket_sort(uint32_t*
   const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const unsigned b0 = blockIdx.x * unsigned(g), b1 = b0 + unsigned(g);
   // segment start and length: the sizes of the buckets before it and in it
+  // (thread t < 256 adds the digits nd / 256 t .. nd / 256 (t + 1) - 1)
   if (t < 256) {
-    uint32_t v = (rowtot && t < b0) ? rowtot[t] : 0u;
-    uint32_t w = (rowtot && t >= b0 && t < b1) ? rowtot[t] : 0u;
+    uint32_t v = 0u, w = 0u;
+    if (rowtot) {
+      const unsigned per = unsigned(nd) / 256u;
+      for (unsigned k = 0; k < per; ++k) {
+        const unsigned d = per * t + k;
+        const uint32_t c = rowtot[d];
+        if (d < b0) v += c;
+        else if (d < b1) w += c;
+      }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       v += __shfl_down_sync(0xffffffffu, v, o);
@@ -325,37 +387,24 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_bucket_sort(uint32_t*
   const int64_t start = s_start;
   const int64_t len = single ? n_single : s_n;
   if (len == 0) return;  // uniform over the CTA
-  const bool all4 = single || g > 1;  // the segment spans several top bytes
-  const uint32_t *sk = single ? k0 : k1 + start, *sv = single ? v0 : v1 + start;
+  const bool all4 = single || g > 1;  // the segment spans several top digits
+  uint32_t *sk = single ? k0 : k1 + start, *sv = single ? v0 : v1 + start;
   uint32_t *gk0 = k0 + start, *gv0 = v0 + start, *gk1 = k1 + start, *gv1 = v1 + start;
+  count_low_byte<NT>(sk, len, sh.cnt[0]);
+  __syncthreads();
   if (len <= cap) {
+    // first pass from global memory, the middle ones in shared memory, the
+    // last into global memory
     uint32_t *ka = sbuf, *va = sbuf + cap, *kb = sbuf + 2 * cap, *vb = sbuf + 3 * cap;
-    for (int64_t i = t; i < len; i += NT) {
-      const uint32_t k = sk[i];
-      ka[i] = k;
-      va[i] = sv[i];
-      atomicAdd(&sh.cnt[0][k & 255u], 1u);
-    }
-    __syncthreads();
-    bucket_pass<NT>(ka, va, kb, vb, len, 0, sh.cnt[0], sh.cnt[1], sh);
-    bucket_pass<NT>(kb, vb, ka, va, len, 8, sh.cnt[1], sh.cnt[0], sh);
+    bucket_pass<NT>(sk, sv, ka, va, len, 0, sh.cnt[0], sh.cnt[1], sh);
+    bucket_pass<NT>(ka, va, kb, vb, len, 8, sh.cnt[1], sh.cnt[0], sh);
     if (all4) {
-      bucket_pass<NT>(ka, va, kb, vb, len, 16, sh.cnt[0], sh.cnt[1], sh);
-      bucket_pass<NT>(kb, vb, ka, va, len, 24, sh.cnt[1], nullptr, sh);
-      for (int64_t i = t; i < len; i += NT) {
-        gk0[i] = ka[i];
-        gv0[i] = va[i];
-      }
+      bucket_pass<NT>(kb, vb, ka, va, len, 16, sh.cnt[0], sh.cnt[1], sh);
+      bucket_pass<NT>(ka, va, gk0, gv0, len, 24, sh.cnt[1], nullptr, sh);
     } else {
-      bucket_pass<NT>(ka, va, kb, vb, len, 16, sh.cnt[0], nullptr, sh);
-      for (int64_t i = t; i < len; i += NT) {
-        gk0[i] = kb[i];
-        gv0[i] = vb[i];
-      }
+      bucket_pass<NT>(kb, vb, gk0, gv0, len, 16, sh.cnt[0], nullptr, sh);
     }
   } else {  // a segment (never the single array) larger than cap: through L2
-    for (int64_t i = t; i < len; i += NT) atomicAdd(&sh.cnt[0][gk1[i] & 255u], 1u);
-    __syncthreads();
     bucket_pass<NT>(gk1, gv1, gk0, gv0, len, 0, sh.cnt[0], sh.cnt[1], sh);
     bucket_pass<NT>(gk0, gv0, gk1, gv1, len, 8, sh.cnt[1], sh.cnt[0], sh);
     if (all4) {
@@ -375,61 +424,74 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_bucket_sort(uint32_t*
 // r^2 up to 1.45 times its mean) must fit the shared-memory capacity; beyond
 // it they take the global path, and one CTA's share of the work outweighs the
 // saved passes (N = 4e6: 0.256 ms against 0.222 for the four global passes;
-// N = 1.6e7: 0.91 against 0.74 ms).
+// N = 1.6e7: 0.91 against 0.74 ms, both with the 8-bit first pass).
 constexpr int64_t kBucketSortMaxN = 2250000;
 constexpr int kBsCapMax = 13312;  // 208 KB of buckets beside the static shared memory
-constexpr int64_t kBsSmallN = 1 << 19;  // up to here, CTAs of 256 threads (buckets of ~2048 keys)
+constexpr int64_t kBsSmallN = 1 << 19;  // up to here an 8-bit first pass (256 buckets), beyond a 10-bit one
 constexpr int64_t kBsSingleN = 3072;     // up to here, one CTA sorts everything (N = 1000: 13 us)
-// shared-memory capacity: three times the mean segment of g buckets
-inline int bucket_cap(int64_t n, int g) {
-  int64_t c = (3 * (int64_t(g) * n / 256) + 511) / 512 * 512;
+// shared-memory capacity for segments of g of nd buckets: three times the mean
+// segment with 256 buckets; 1.5 times with 1024 (four CTAs of 55 KB per SM at
+// N = 2e6; a larger bucket goes through L2)
+inline int bucket_cap(int64_t n, int g, int nd) {
+  const int64_t mean = int64_t(g) * n / nd;
+  int64_t c = ((nd == 256 ? 3 * mean : mean + mean / 2) + 255) / 256 * 256;
   if (c < 2048) c = 2048;
   return int(c < kBsCapMax ? c : kBsCapMax);
 }
 
 cudaError_t set_sort_attributes() {
-  const cudaError_t e = cudaFuncSetAttribute(k_bucket_sort<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const cudaError_t e = cudaFuncSetAttribute(k_bucket_sort<256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              16 * kBsCapMax);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_bucket_sort<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kBsCapMax);
+  return cudaFuncSetAttribute(k_bucket_sort<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kBsCapMax);
 }
 
 const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
                                   int64_t n, int first_byte, cudaStream_t s, bool shared_gpu) {
   if (n <= 1) return v0;
   const int64_t nblk = sort_blocks(n);
-  uint32_t* rowtot = hist + 256 * nblk;
   if (first_byte == 0 && n <= kBsSingleN) {
     // one CTA sorts the whole array in shared memory, all four bytes
     const int cap = int((n + 255) / 256 * 256);
-    k_bucket_sort<256><<<1, 256, size_t(16) * cap, s>>>(k1, v1, k0, v0, nullptr, n, cap, 256);
+    k_bucket_sort<256, 3><<<1, 256, size_t(16) * cap, s>>>(k1, v1, k0, v0, nullptr, n, cap, 256, 256);
     return v0;
   }
   if (first_byte == 0 && n <= kBucketSortMaxN) {
-    // the top byte over the whole array into 256 contiguous buckets (k0 -> k1),
-    // then the three low bytes per bucket (into k0). Alone on the GPU, one CTA
-    // per bucket (the most parallel); sharing it (a batch), a small instance
-    // takes segments of several buckets, about 2048 keys per CTA (fewer CTAs,
-    // all four bytes each): the same permutation either way
+    // the top digit over the whole array into nd contiguous buckets (k0 -> k1),
+    // then the bits below it per bucket (into k0): 256 buckets (the top byte)
+    // up to kBsSmallN keys, 1024 (the top 10 bits, buckets of ~2000 keys at
+    // N = 2e6, four CTAs per SM) beyond. Alone on the GPU, one CTA per bucket
+    // (the most parallel); sharing it (a batch), a small instance takes
+    // segments of several buckets, about 2048 keys per CTA (fewer CTAs, all
+    // four bytes each): the same permutation either way
+    const bool wide = n > kBsSmallN;
+    const int nd = wide ? 1024 : 256, shift = wide ? 22 : 24;
+    uint32_t* rowtot = hist + int64_t(nd) * nblk;
     int g = 1;
-    while (shared_gpu && g < 256 && int64_t(g) * 2 * n <= int64_t(2048) * 256) g *= 2;
-    const int cap = bucket_cap(n, g);
-    k_sort_hist<<<unsigned(nblk), kSortThreads, 0, s>>>(k0, n, 24, nblk, hist);
-    k_sort_rowscan<<<256, 256, 0, s>>>(hist, nblk, rowtot);
-    k_sort_scatter<<<unsigned(nblk), kSortThreads, 0, s>>>(k0, v0, k1, v1, n, 24, nblk, hist, rowtot);
-    if (n <= kBsSmallN)
-      k_bucket_sort<256><<<unsigned(256 / g), 256, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, 0, cap, g);
-    else
-      k_bucket_sort<512><<<256, 512, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, 0, cap, 1);
+    while (shared_gpu && g < nd && int64_t(g) * 2 * n <= int64_t(2048) * nd) g *= 2;
+    const int cap = bucket_cap(n, g, nd);
+    if (wide) {
+      k_sort_hist<1024><<<unsigned(nblk), kSortThreads, 0, s>>>(k0, n, shift, nblk, hist);
+      k_sort_rowscan<<<1024, 256, 0, s>>>(hist, nblk, rowtot);
+      k_sort_scatter<1024><<<unsigned(nblk), kSortThreads, 0, s>>>(k0, v0, k1, v1, n, shift, nblk, hist, rowtot);
+      k_bucket_sort<256, 4><<<unsigned(1024 / g), 256, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, 0, cap, g,
+                                                                              1024);
+    } else {
+      k_sort_hist<256><<<unsigned(nblk), kSortThreads, 0, s>>>(k0, n, shift, nblk, hist);
+      k_sort_rowscan<<<256, 256, 0, s>>>(hist, nblk, rowtot);
+      k_sort_scatter<256><<<unsigned(nblk), kSortThreads, 0, s>>>(k0, v0, k1, v1, n, shift, nblk, hist, rowtot);
+      k_bucket_sort<256, 3><<<unsigned(256 / g), 256, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, 0, cap, g,
+                                                                             256);
+    }
     return v0;
   }
+  uint32_t* rowtot = hist + 256 * nblk;
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int pass = first_byte; pass < 4; ++pass) {
     const int shift = 8 * pass;
-    k_sort_hist<<<unsigned(nblk), kSortThreads, 0, s>>>(ki, n, shift, nblk, hist);
+    k_sort_hist<256><<<unsigned(nblk), kSortThreads, 0, s>>>(ki, n, shift, nblk, hist);
     k_sort_rowscan<<<256, 256, 0, s>>>(hist, nblk, rowtot);
-    k_sort_scatter<<<unsigned(nblk), kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, nblk, hist,
-                                                           rowtot);
+    k_sort_scatter<256><<<unsigned(nblk), kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, nblk, hist, rowtot);
     uint32_t* tk = ki; ki = ko; ko = tk;
     uint32_t* tv = vi; vi = vo; vo = tv;
   }
@@ -994,8 +1056,14 @@ template <class T> cudaError_t preload_core_kernels_t() {
 cudaError_t preload_core_kernels() {
   if (set_sort_attributes() != cudaSuccess) return cudaErrorInvalidValue;
   cudaFuncAttributes fa;
-  const void* fns[] = {reinterpret_cast<const void*>(&k_sort_hist), reinterpret_cast<const void*>(&k_sort_rowscan),
-                       reinterpret_cast<const void*>(&k_sort_scatter), reinterpret_cast<const void*>(&k_finalize),
+  const void* fns[] = {reinterpret_cast<const void*>(&k_sort_hist<256>),
+                       reinterpret_cast<const void*>(&k_sort_hist<1024>),
+                       reinterpret_cast<const void*>(&k_sort_rowscan),
+                       reinterpret_cast<const void*>(&k_sort_scatter<256>),
+                       reinterpret_cast<const void*>(&k_sort_scatter<1024>),
+                       reinterpret_cast<const void*>(&k_bucket_sort<256, 3>),
+                       reinterpret_cast<const void*>(&k_bucket_sort<256, 4>),
+                       reinterpret_cast<const void*>(&k_finalize),
                        reinterpret_cast<const void*>(&k_init_step), reinterpret_cast<const void*>(&k_dft)};
   for (const void* f : fns) {
     const cudaError_t e = cudaFuncGetAttributes(&fa, f);

@@ -43,12 +43,14 @@ inline double coef_canti(int l, double d, double eps) {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per CTA
-inline int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
-// Sorts (key, val) pairs by the key bytes first_byte..3 (stable LSD radix
-// sort, one pass of 8 bits per byte; keys equal in those bytes keep their
-// order). k0/v0 hold the input; k1/v1 are scratch of n; hist: 256 *
-// sort_blocks(n) + 256 words. Returns the buffer that holds the sorted values
-// (v0 after an even number of passes, v1 after an odd one).
+constexpr int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+// Words of the sort's histogram buffer for n keys: block counts of up to 1024
+// digits per block, and the digit totals.
+constexpr int64_t sort_hist_words(int64_t n) { return 1024 * sort_blocks(n) + 1024; }
+// Sorts (key, val) pairs by the key bytes first_byte..3 (stable radix sort;
+// keys equal in those bytes keep their order). k0/v0 hold the input; k1/v1 are
+// scratch of n; hist: sort_hist_words(n) words. Returns the buffer that holds
+// the sorted values (v0 after an even number of passes, v1 after an odd one).
 // Key bytes sorted: all four, in both precisions. The radius key is
 // floor((r^2 - 1) / (r_out^2 - 1) * 2^32) of the exact FP64 r^2 of the stored
 // position, and the sorted index j of a particle is its count of electrons

@@ -31,7 +31,6 @@ constexpr Layout layout(int64_t n, int L, size_t es) {
   const int64_t ntiles = (n + 31) / 32;
   const int64_t ngroups = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
   const int64_t nc = 2 * int64_t(ncomp(L));
-  const int64_t nblk = (n + kSortTile - 1) / kSortTile;
   size_t at = 0;
   o.part = at; at += align256(size_t(n) * 8 * es);  // Part<T> records: 8 elements each
   for (int k = 0; k < 6; ++k) { o.st[k] = at; at += align256(size_t(n) * es); }
@@ -40,7 +39,7 @@ constexpr Layout layout(int64_t n, int L, size_t es) {
   o.idx0 = at; at += align256(size_t(n) * 4);
   o.key1 = at; at += align256(size_t(n) * 4);
   o.idx1 = at; at += align256(size_t(n) * 4);
-  o.hist = at; at += align256(size_t(256 * nblk + 256) * 4);
+  o.hist = at; at += align256(size_t(sort_hist_words(n)) * 4);
   o.agg = at; at += align256(size_t(nc * tile_stride(ntiles)) * es);
   o.pfx = at; at += align256(size_t(nc * tile_stride(ntiles)) * es);
   o.gagg = at; at += align256(size_t(nc * ngroups) * 8);
