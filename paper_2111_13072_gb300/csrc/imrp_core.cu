@@ -11,11 +11,11 @@ namespace imrp {
 
 // ============================================================================
 // Radix sort: stable LSD passes of 8-bit digits, and a wide first pass of
-// 10-bit digits for the bucket sort of large arrays. Each CTA owns
+// 9-bit digits for the bucket sort of large arrays. Each CTA owns
 // kSortTile = 2048 consecutive keys in a striped layout (item i of thread t is
 // key base + i*256 + t), which keeps the slot order (item, warp, lane) equal
 // to the key order, so the local ranks below are stable. ND: digits of the
-// pass (256 or 1024); hist holds ND rows of nblk block counts.
+// pass (256 or 512); hist holds ND rows of nblk block counts.
 // ============================================================================
 template <int ND>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys,
@@ -25,58 +25,36 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
   for (int d = threadIdx.x; d < ND; d += kSortThreads) h[d] = 0;
   __syncthreads();
   const int64_t base = int64_t(blockIdx.x) * kSortTile;
+  const int nvalid = n - base < kSortTile ? int(n - base) : kSortTile;
+  const unsigned lane = threadIdx.x & 31;
   uint32_t k[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    const int64_t idx = base + int64_t(i) * kSortThreads + threadIdx.x;
-    k[i] = idx < n ? keys[idx] : 0u;
+    const int o = i * kSortThreads + int(threadIdx.x);
+    k[i] = o < nvalid ? keys[base + o] : 0u;
   }
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    const int64_t idx = base + int64_t(i) * kSortThreads + threadIdx.x;
-    if (idx < n) atomicAdd(&h[(k[i] >> shift) & unsigned(ND - 1)], 1u);
+    // a warp holds 32 consecutive keys: when they share the digit (nearly
+    // sorted input), one atomic adds all 32
+    const bool ok = i * kSortThreads + int(threadIdx.x) < nvalid;
+    const unsigned d = (k[i] >> shift) & unsigned(ND - 1);
+    const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
+    if (__all_sync(0xffffffffu, ok && d == d0)) {
+      if (lane == 0) atomicAdd(&h[d0], 32u);
+    } else if (ok) {
+      atomicAdd(&h[d], 1u);
+    }
   }
   __syncthreads();
   for (int d = threadIdx.x; d < ND; d += kSortThreads) hist[int64_t(d) * nblk + blockIdx.x] = h[d];
 }
 
-// Exclusive scan of one digit's row hist[d][0..nblk) in place; the row total
-// goes to rowtot[d]. One CTA per digit.
-__global__ void __launch_bounds__(256) k_sort_rowscan(uint32_t* __restrict__ hist, int64_t nblk,
-                                                     uint32_t* __restrict__ rowtot) {
-  __shared__ uint32_t wsum[8];
-  uint32_t* row = hist + int64_t(blockIdx.x) * nblk;
-  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t carry = 0;
-  for (int64_t b0 = 0; b0 < nblk; b0 += 256) {
-    const int64_t i = b0 + threadIdx.x;
-    const uint32_t v = i < nblk ? row[i] : 0u;
-    uint32_t s = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= unsigned(o)) s += t;
-    }
-    if (lane == 31) wsum[warp] = s;
-    __syncthreads();
-    uint32_t woff = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      const uint32_t ws = wsum[w];
-      if (unsigned(w) < warp) woff += ws;
-      tot += ws;
-    }
-    if (i < nblk) row[i] = carry + woff + s - v;
-    carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) rowtot[blockIdx.x] = carry;
-}
-
 // Exclusive prefix over the kSortThreads threads of a CTA of the per-thread
-// values v (warp shuffles, then the warp sums through wsum). All threads call
-// it; the caller separates two uses of wsum by a barrier.
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* wsum) {
+// values v (warp shuffles, then the warp sums through wsum); *total gets the
+// sum over the CTA. All threads call it; the caller separates two uses of wsum
+// by a barrier.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* wsum, uint32_t* total = nullptr) {
   const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t s = v;
 #pragma unroll
@@ -86,9 +64,57 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* wsum) 
   }
   if (lane == 31) wsum[warp] = s;
   __syncthreads();
-  uint32_t woff = 0;
-  for (unsigned w = 0; w < warp; ++w) woff += wsum[w];
+  uint32_t woff = 0, tot = 0;
+#pragma unroll
+  for (unsigned w = 0; w < kSortThreads / 32; ++w) {
+    const uint32_t x = wsum[w];
+    woff += w < warp ? x : 0u;
+    tot += x;
+  }
+  if (total) *total = tot;
   return woff + s - v;
+}
+
+// Exclusive scan of one digit's row hist[d][0..nblk) in place; the row total
+// goes to rowtot[d]. One CTA per digit.
+__global__ void __launch_bounds__(kSortThreads) k_sort_rowscan(uint32_t* __restrict__ hist, int64_t nblk,
+                                                              uint32_t* __restrict__ rowtot) {
+  constexpr int R = 8;  // consecutive entries per thread, loaded together
+  __shared__ uint32_t wsum[kSortThreads / 32];
+  uint32_t* row = hist + int64_t(blockIdx.x) * nblk;
+  uint32_t carry = 0;
+  for (int64_t b0 = 0; b0 < nblk; b0 += int64_t(kSortThreads) * R) {
+    const int64_t i0 = b0 + int64_t(R) * threadIdx.x;
+    uint32_t v[R], sum = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      v[r] = i0 + r < nblk ? row[i0 + r] : 0u;
+      sum += v[r];
+    }
+    uint32_t tot;
+    uint32_t run = carry + block_excl_scan(sum, wsum, &tot);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (i0 + r < nblk) row[i0 + r] = run;
+      run += v[r];
+    }
+    carry += tot;
+    __syncthreads();  // wsum reuse
+  }
+  if (threadIdx.x == 0) rowtot[blockIdx.x] = carry;
+}
+
+// Lanes of the warp whose digit equals this lane's (bits BITS of d), among
+// the lanes with ok set: one ballot per digit bit.
+template <int BITS>
+__device__ __forceinline__ unsigned digit_peers(unsigned d, bool ok) {
+  unsigned p = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+  for (int b = 0; b < BITS; ++b) {
+    const unsigned m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+    p &= ((d >> b) & 1u) ? m : ~m;
+  }
+  return p;
 }
 
 // Scatter of one pass. Warp w of the block owns the keys base + 256 w ..
@@ -103,9 +129,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* wsum) 
 // t owns the digits DPT t .. DPT t + DPT - 1 in the per-digit steps. With 256
 // digits about 22 KB of shared memory and at most 36 registers per thread (7
 // blocks per SM, so all blocks of N = 2e6 keys are resident at once); with
-// 1024 digits about 41 KB (5 blocks per SM).
+// 512 digits about 29 KB. Ranking by __match_any_sync: the keys of a warp
+// arrive nearly sorted, so few distinct top digits (faster here than ballots).
 template <int ND>
-__global__ void __launch_bounds__(kSortThreads, ND == 256 ? 7 : 5) k_sort_scatter(
+__global__ void __launch_bounds__(kSortThreads, ND == 256 ? 7 : 6) k_sort_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, int64_t nblk,
     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ rowtot) {
@@ -214,21 +241,24 @@ __global__ void __launch_bounds__(kSortThreads, ND == 256 ? 7 : 5) k_sort_scatte
 }
 
 // Sort of one top-digit bucket by the key bits below the digit, in one CTA.
-// The first pass of the sort (on the top byte, or on the top 10 bits, over the
+// The first pass of the sort (on the top byte, or on the top 9 bits, over the
 // whole array) leaves the keys of bucket b contiguous and in their input
 // order; this CTA then runs three stable LSD passes over its bucket, bytes 0,
-// 1, 2 (with a 10-bit top digit the two top bits of byte 2 are the same for
-// the whole bucket), which need no global synchronisation: in shared memory
-// when the bucket fits (the first pass reads the bucket from global memory,
-// the last writes it back), else between the two global key/value buffers (in
-// L2; the CTA alone touches that range). A pass: the scan of the byte's digit
+// 1, 2 (with a 9-bit top digit the top bit of byte 2 is the same for the
+// whole bucket), which need no global synchronisation: in shared memory when
+// the bucket fits (the first pass reads the bucket from global memory, the
+// last writes it back), else between the two global key/value buffers (in L2;
+// the CTA alone touches that range). A pass: the scan of the byte's digit
 // counts, then the bucket in chunks of NT * kBsItems keys in order; each warp
 // ranks its 256 keys (item i of lane l is chunk slot 256 w + 32 i + l) against
 // its running digit counts, the warps' counts are scanned per digit, and each
 // key goes to (digit start) + (keys of that digit in earlier chunks and warps)
-// + (its rank in its warp): stable. The next byte's counts are gathered as
-// keys are placed. The result is the permutation of a stable LSD sort on all
-// four bytes.
+// + (its rank in its warp): stable. A warp whose part of the chunk holds no
+// keys, and items past the end, skip the ranking. The peers of a key in its
+// warp come from one ballot per digit bit (the low bytes are spread evenly
+// over the digits, where that is faster than __match_any_sync). The next
+// byte's counts are gathered as keys are placed. The result is the
+// permutation of a stable LSD sort on all four bytes.
 constexpr int kBsItems = 8;
 
 template <int NT> struct BsShared {
@@ -238,11 +268,11 @@ template <int NT> struct BsShared {
   uint32_t wsum[8];
 };
 
-// One pass over len keys (slots 0 .. len-1 of ki/vi into ko/vo), digit =
+// One pass over len (< 2^31) keys (slots 0 .. len-1 of ki/vi into ko/vo), digit =
 // byte at `shift`; cnt: this byte's counts; cnx (or null): zeroed here, then
 // the counts of the byte at shift + 8.
 template <int NT, class K>
-__device__ __forceinline__ void bucket_pass(const K* ki, const K* vi, K* ko, K* vo, int64_t len, int shift,
+__device__ __forceinline__ void bucket_pass(const K* ki, const K* vi, K* ko, K* vo, int len, int shift,
                                             const uint32_t* cnt, uint32_t* cnx, BsShared<NT>& sh) {
   constexpr int kWarps = NT / 32, kChunk = NT * kBsItems;
   const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -265,28 +295,32 @@ __device__ __forceinline__ void bucket_pass(const K* ki, const K* vi, K* ko, K* 
     for (unsigned w = 0; w < warp; ++w) off += sh.wsum[w];
     sh.dst[t] = off + s1 - c;
   }
-  for (int64_t c0 = 0; c0 < len; c0 += kChunk) {
+  for (int c0 = 0; c0 < len; c0 += kChunk) {
     for (int k = t; k < kWarps * 256; k += NT) (&sh.whist[0][0])[k] = 0;
     __syncthreads();
-    const int64_t wb = c0 + int64_t(warp) * (32 * kBsItems);
+    const int wb = c0 + int(warp) * (32 * kBsItems);
+    const int nv = len - wb;  // keys of this warp's range that exist (warp-uniform)
     uint32_t key[kBsItems], val[kBsItems];
-    uint32_t wrank[kBsItems / 2] = {};
+    uint32_t wrank[(kBsItems + 1) / 2] = {};
+    if (nv > 0) {
 #pragma unroll
-    for (int i = 0; i < kBsItems; ++i) {
-      const int64_t idx = wb + 32 * i + lane;
-      key[i] = idx < len ? ki[idx] : 0u;
-      val[i] = idx < len ? vi[idx] : 0u;
-    }
+      for (int i = 0; i < kBsItems; ++i) {
+        const int o = 32 * i + int(lane);
+        key[i] = o < nv ? ki[wb + o] : 0u;
+        val[i] = o < nv ? vi[wb + o] : 0u;
+      }
 #pragma unroll
-    for (int i = 0; i < kBsItems; ++i) {
-      const bool ok = wb + 32 * i + lane < len;
-      const unsigned d = ok ? ((key[i] >> shift) & 255u) : 256u;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      const unsigned before = ok ? unsigned(sh.whist[warp][d]) : 0u;
-      wrank[i / 2] |= (before + __popc(peers & lt)) << (16 * (i % 2));
-      __syncwarp();
-      if (ok && lane == unsigned(__ffs(peers) - 1)) sh.whist[warp][d] = uint16_t(before + __popc(peers));
-      __syncwarp();
+      for (int i = 0; i < kBsItems; ++i) {
+        if (32 * i >= nv) break;
+        const bool ok = 32 * i + int(lane) < nv;
+        const unsigned d = ok ? ((key[i] >> shift) & 255u) : 256u;
+        const unsigned peers = digit_peers<8>(d, ok);
+        const unsigned before = ok ? unsigned(sh.whist[warp][d]) : 0u;
+        wrank[i / 2] |= (before + __popc(peers & lt)) << (16 * (i % 2));
+        __syncwarp();
+        if (ok && lane == unsigned(__ffs(peers) - 1)) sh.whist[warp][d] = uint16_t(before + __popc(peers));
+        __syncwarp();
+      }
     }
     __syncthreads();
     uint32_t total = 0;
@@ -299,14 +333,17 @@ __device__ __forceinline__ void bucket_pass(const K* ki, const K* vi, K* ko, K* 
       }
     }
     __syncthreads();
+    if (nv > 0) {
 #pragma unroll
-    for (int i = 0; i < kBsItems; ++i) {
-      if (wb + 32 * i + lane < len) {
-        const unsigned d = (key[i] >> shift) & 255u;
-        const uint32_t g = sh.dst[d] + sh.whist[warp][d] + ((wrank[i / 2] >> (16 * (i % 2))) & 0xffffu);
-        ko[g] = key[i];
-        vo[g] = val[i];
-        if (cnx) atomicAdd(&cnx[(key[i] >> (shift + 8)) & 255u], 1u);
+      for (int i = 0; i < kBsItems; ++i) {
+        if (32 * i >= nv) break;
+        if (32 * i + int(lane) < nv) {
+          const unsigned d = (key[i] >> shift) & 255u;
+          const uint32_t g = sh.dst[d] + sh.whist[warp][d] + ((wrank[i / 2] >> (16 * (i % 2))) & 0xffffu);
+          ko[g] = key[i];
+          vo[g] = val[i];
+          if (cnx) atomicAdd(&cnx[(key[i] >> (shift + 8)) & 255u], 1u);
+        }
       }
     }
     __syncthreads();
@@ -396,26 +433,26 @@ __global__ void __launch_bounds__(NT, MINB) k_bucket_sort(uint32_t* k1, uint32_t
     // first pass from global memory, the middle ones in shared memory, the
     // last into global memory
     uint32_t *ka = sbuf, *va = sbuf + cap, *kb = sbuf + 2 * cap, *vb = sbuf + 3 * cap;
-    bucket_pass<NT>(sk, sv, ka, va, len, 0, sh.cnt[0], sh.cnt[1], sh);
-    bucket_pass<NT>(ka, va, kb, vb, len, 8, sh.cnt[1], sh.cnt[0], sh);
+    bucket_pass<NT>(sk, sv, ka, va, int(len), 0, sh.cnt[0], sh.cnt[1], sh);
+    bucket_pass<NT>(ka, va, kb, vb, int(len), 8, sh.cnt[1], sh.cnt[0], sh);
     if (all4) {
-      bucket_pass<NT>(kb, vb, ka, va, len, 16, sh.cnt[0], sh.cnt[1], sh);
-      bucket_pass<NT>(ka, va, gk0, gv0, len, 24, sh.cnt[1], nullptr, sh);
+      bucket_pass<NT>(kb, vb, ka, va, int(len), 16, sh.cnt[0], sh.cnt[1], sh);
+      bucket_pass<NT>(ka, va, gk0, gv0, int(len), 24, sh.cnt[1], nullptr, sh);
     } else {
-      bucket_pass<NT>(kb, vb, gk0, gv0, len, 16, sh.cnt[0], nullptr, sh);
+      bucket_pass<NT>(kb, vb, gk0, gv0, int(len), 16, sh.cnt[0], nullptr, sh);
     }
   } else {  // a segment (never the single array) larger than cap: through L2
-    bucket_pass<NT>(gk1, gv1, gk0, gv0, len, 0, sh.cnt[0], sh.cnt[1], sh);
-    bucket_pass<NT>(gk0, gv0, gk1, gv1, len, 8, sh.cnt[1], sh.cnt[0], sh);
+    bucket_pass<NT>(gk1, gv1, gk0, gv0, int(len), 0, sh.cnt[0], sh.cnt[1], sh);
+    bucket_pass<NT>(gk0, gv0, gk1, gv1, int(len), 8, sh.cnt[1], sh.cnt[0], sh);
     if (all4) {
-      bucket_pass<NT>(gk1, gv1, gk0, gv0, len, 16, sh.cnt[0], sh.cnt[1], sh);
-      bucket_pass<NT>(gk0, gv0, gk1, gv1, len, 24, sh.cnt[1], nullptr, sh);
+      bucket_pass<NT>(gk1, gv1, gk0, gv0, int(len), 16, sh.cnt[0], sh.cnt[1], sh);
+      bucket_pass<NT>(gk0, gv0, gk1, gv1, int(len), 24, sh.cnt[1], nullptr, sh);
       for (int64_t i = t; i < len; i += NT) {
         gk0[i] = gk1[i];
         gv0[i] = gv1[i];
       }
     } else {
-      bucket_pass<NT>(gk1, gv1, gk0, gv0, len, 16, sh.cnt[0], nullptr, sh);
+      bucket_pass<NT>(gk1, gv1, gk0, gv0, int(len), 16, sh.cnt[0], nullptr, sh);
     }
   }
 }
@@ -427,10 +464,10 @@ __global__ void __launch_bounds__(NT, MINB) k_bucket_sort(uint32_t* k1, uint32_t
 // N = 1.6e7: 0.91 against 0.74 ms, both with the 8-bit first pass).
 constexpr int64_t kBucketSortMaxN = 2250000;
 constexpr int kBsCapMax = 13312;  // 208 KB of buckets beside the static shared memory
-constexpr int64_t kBsSmallN = 1 << 19;  // up to here an 8-bit first pass (256 buckets), beyond a 10-bit one
+constexpr int64_t kBsSmallN = 1 << 19;  // up to here an 8-bit first pass (256 buckets), beyond a 9-bit one (512)
 constexpr int64_t kBsSingleN = 3072;     // up to here, one CTA sorts everything (N = 1000: 13 us)
 // shared-memory capacity for segments of g of nd buckets: three times the mean
-// segment with 256 buckets; 1.5 times with 1024 (four CTAs of 55 KB per SM at
+// segment with 256 buckets; 1.5 times with 512 (two CTAs of 99 KB per SM at
 // N = 2e6; a larger bucket goes through L2)
 inline int bucket_cap(int64_t n, int g, int nd) {
   const int64_t mean = int64_t(g) * n / nd;
@@ -443,7 +480,7 @@ cudaError_t set_sort_attributes() {
   const cudaError_t e = cudaFuncSetAttribute(k_bucket_sort<256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              16 * kBsCapMax);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_bucket_sort<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kBsCapMax);
+  return cudaFuncSetAttribute(k_bucket_sort<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kBsCapMax);
 }
 
 const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
@@ -459,26 +496,26 @@ const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint
   if (first_byte == 0 && n <= kBucketSortMaxN) {
     // the top digit over the whole array into nd contiguous buckets (k0 -> k1),
     // then the bits below it per bucket (into k0): 256 buckets (the top byte)
-    // up to kBsSmallN keys, 1024 (the top 10 bits, buckets of ~2000 keys at
-    // N = 2e6, four CTAs per SM) beyond. Alone on the GPU, one CTA per bucket
+    // up to kBsSmallN keys, 512 (the top 9 bits, buckets of ~3900 keys at
+    // N = 2e6, two CTAs per SM) beyond. Alone on the GPU, one CTA per bucket
     // (the most parallel); sharing it (a batch), a small instance takes
     // segments of several buckets, about 2048 keys per CTA (fewer CTAs, all
     // four bytes each): the same permutation either way
     const bool wide = n > kBsSmallN;
-    const int nd = wide ? 1024 : 256, shift = wide ? 22 : 24;
+    const int nd = wide ? 512 : 256, shift = wide ? 23 : 24;
     uint32_t* rowtot = hist + int64_t(nd) * nblk;
     int g = 1;
     while (shared_gpu && g < nd && int64_t(g) * 2 * n <= int64_t(2048) * nd) g *= 2;
     const int cap = bucket_cap(n, g, nd);
     if (wide) {
-      k_sort_hist<1024><<<unsigned(nblk), kSortThreads, 0, s>>>(k0, n, shift, nblk, hist);
-      k_sort_rowscan<<<1024, 256, 0, s>>>(hist, nblk, rowtot);
-      k_sort_scatter<1024><<<unsigned(nblk), kSortThreads, 0, s>>>(k0, v0, k1, v1, n, shift, nblk, hist, rowtot);
-      k_bucket_sort<256, 4><<<unsigned(1024 / g), 256, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, 0, cap, g,
-                                                                              1024);
+      k_sort_hist<512><<<unsigned(nblk), kSortThreads, 0, s>>>(k0, n, shift, nblk, hist);
+      k_sort_rowscan<<<512, kSortThreads, 0, s>>>(hist, nblk, rowtot);
+      k_sort_scatter<512><<<unsigned(nblk), kSortThreads, 0, s>>>(k0, v0, k1, v1, n, shift, nblk, hist, rowtot);
+      k_bucket_sort<256, 2><<<unsigned(512 / g), 256, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, 0, cap, g,
+                                                                             512);
     } else {
       k_sort_hist<256><<<unsigned(nblk), kSortThreads, 0, s>>>(k0, n, shift, nblk, hist);
-      k_sort_rowscan<<<256, 256, 0, s>>>(hist, nblk, rowtot);
+      k_sort_rowscan<<<256, kSortThreads, 0, s>>>(hist, nblk, rowtot);
       k_sort_scatter<256><<<unsigned(nblk), kSortThreads, 0, s>>>(k0, v0, k1, v1, n, shift, nblk, hist, rowtot);
       k_bucket_sort<256, 3><<<unsigned(256 / g), 256, size_t(16) * cap, s>>>(k1, v1, k0, v0, rowtot, 0, cap, g,
                                                                              256);
@@ -490,7 +527,7 @@ const uint32_t* launch_radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint
   for (int pass = first_byte; pass < 4; ++pass) {
     const int shift = 8 * pass;
     k_sort_hist<256><<<unsigned(nblk), kSortThreads, 0, s>>>(ki, n, shift, nblk, hist);
-    k_sort_rowscan<<<256, 256, 0, s>>>(hist, nblk, rowtot);
+    k_sort_rowscan<<<256, kSortThreads, 0, s>>>(hist, nblk, rowtot);
     k_sort_scatter<256><<<unsigned(nblk), kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, nblk, hist, rowtot);
     uint32_t* tk = ki; ki = ko; ko = tk;
     uint32_t* tv = vi; vi = vo; vo = tv;
@@ -1057,12 +1094,12 @@ cudaError_t preload_core_kernels() {
   if (set_sort_attributes() != cudaSuccess) return cudaErrorInvalidValue;
   cudaFuncAttributes fa;
   const void* fns[] = {reinterpret_cast<const void*>(&k_sort_hist<256>),
-                       reinterpret_cast<const void*>(&k_sort_hist<1024>),
+                       reinterpret_cast<const void*>(&k_sort_hist<512>),
                        reinterpret_cast<const void*>(&k_sort_rowscan),
                        reinterpret_cast<const void*>(&k_sort_scatter<256>),
-                       reinterpret_cast<const void*>(&k_sort_scatter<1024>),
+                       reinterpret_cast<const void*>(&k_sort_scatter<512>),
                        reinterpret_cast<const void*>(&k_bucket_sort<256, 3>),
-                       reinterpret_cast<const void*>(&k_bucket_sort<256, 4>),
+                       reinterpret_cast<const void*>(&k_bucket_sort<256, 2>),
                        reinterpret_cast<const void*>(&k_finalize),
                        reinterpret_cast<const void*>(&k_init_step), reinterpret_cast<const void*>(&k_dft)};
   for (const void* f : fns) {

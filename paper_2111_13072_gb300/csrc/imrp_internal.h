@@ -44,9 +44,9 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per CTA
 constexpr int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
-// Words of the sort's histogram buffer for n keys: block counts of up to 1024
+// Words of the sort's histogram buffer for n keys: block counts of up to 512
 // digits per block, and the digit totals.
-constexpr int64_t sort_hist_words(int64_t n) { return 1024 * sort_blocks(n) + 1024; }
+constexpr int64_t sort_hist_words(int64_t n) { return 512 * sort_blocks(n) + 512; }
 // Sorts (key, val) pairs by the key bytes first_byte..3 (stable radix sort;
 // keys equal in those bytes keep their order). k0/v0 hold the input; k1/v1 are
 // scratch of n; hist: sort_hist_words(n) words. Returns the buffer that holds
