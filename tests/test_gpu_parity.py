@@ -45,8 +45,8 @@ BASE = WORKLOADS["fp64_n2e4_l8"]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("n,L", [(1, 8), (2, 4), (31, 8), (33, 2), (1000, 1), (4103, 12),
-                                 (8269, 8), (3001, 16), (1500, 24)])
+@pytest.mark.parametrize("n,L", [(1, 8), (2, 4), (31, 8), (32, 4), (33, 2), (1000, 1), (1024, 8),
+                                 (1025, 8), (4103, 12), (8269, 8), (3001, 16), (1500, 24)])
 def test_field_matches_oracle(imrp, prec, n, L):
     x, v = workload_state(BASE, N=n)
     p, op = _pair(imrp, BASE, n, precision=prec, l_max=L)
@@ -62,12 +62,13 @@ def test_field_matches_oracle(imrp, prec, n, L):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("n,L", [(150000, 16), (100003, 24)])
+@pytest.mark.parametrize("n,L", [(150000, 16), (100003, 24), (600001, 2)])
 def test_field_matches_oracle_every_particle_large(imrp, prec, n, L):
     """Every particle at sizes beyond one segment of the group scan (more than
     64 groups of 1024 particles: the multi-segment sums, the ticketed last-CTA
     scan and the segment bases all run), at the bench's degree and at the
-    largest one, against the oracle's scan evaluator."""
+    largest one, and beyond 2^19 particles (the sort's 9-bit top pass into 512
+    buckets) at a low degree, against the oracle's scan evaluator."""
     x, v = workload_state(BASE, N=n)
     p, op = _pair(imrp, BASE, n, precision=prec, l_max=L, drive_kind=1, V_volts=50.0)
     with imrp.Sim(p) as sim:
