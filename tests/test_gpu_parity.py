@@ -62,13 +62,15 @@ def test_field_matches_oracle(imrp, prec, n, L):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("n,L", [(150000, 16), (100003, 24), (600001, 2)])
+@pytest.mark.parametrize("n,L", [(150000, 16), (100003, 24), (600001, 2), (250001, 16), (1300001, 2)])
 def test_field_matches_oracle_every_particle_large(imrp, prec, n, L):
     """Every particle at sizes beyond one segment of the group scan (more than
     64 groups of 1024 particles: the multi-segment sums, the ticketed last-CTA
     scan and the segment bases all run), at the bench's degree and at the
     largest one, and beyond 2^19 particles (the sort's 9-bit top pass into 512
-    buckets) at a low degree, against the oracle's scan evaluator."""
+    buckets) at a low degree; the last two with at least twice as many tiles
+    as the GPU holds resident warps (several waves of field CTAs). Against the
+    oracle's scan evaluator."""
     x, v = workload_state(BASE, N=n)
     p, op = _pair(imrp, BASE, n, precision=prec, l_max=L, drive_kind=1, V_volts=50.0)
     with imrp.Sim(p) as sim:
