@@ -1014,7 +1014,8 @@ template <class T, int L>
 __global__ void __launch_bounds__(256, field_min_blocks<T>()) k_field(FieldArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  field_tile<T, L>(a, smem_raw, warp, wpb, int64_t(blockIdx.x) * wpb + warp);
+  // tiles in decreasing order: the particle rows written last (still in L2) first
+  field_tile<T, L>(a, smem_raw, warp, wpb, int64_t(gridDim.x - 1 - blockIdx.x) * wpb + warp);
 }
 
 // Batched field: the instances of one degree and precision in one launch. CTA
