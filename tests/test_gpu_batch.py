@@ -105,6 +105,25 @@ def test_autotune_keeps_results(imrp):
     s.close()
 
 
+def test_autotune_is_not_slower(imrp):
+    """The autotuner times the field kernel at every CTA size, the default
+    among them, and keeps the fastest: the field stage after tuning is no
+    slower than before (medians of three timed runs of 20 steps each, N = 2e5
+    at l_max = 16, 10 % allowed for run-to-run noise)."""
+    s = _make(imrp, (200000, 16, 3.0, 1e16, 1, 9))
+
+    def field_ms():
+        return float(np.median([s.profile_steps(20)["field"] for _ in range(3)]))
+
+    s.profile_steps(5)  # warm-up
+    before = field_ms()
+    s.autotune()
+    after = field_ms()
+    print(f"field stage: {before:.4f} ms before tuning, {after:.4f} ms after")
+    assert after <= 1.10 * before
+    s.close()
+
+
 def test_batch_autotune_keeps_results(imrp):
     """The batch autotuner picks a CTA size per batched field launch; steps
     after it are bit-identical to steps of the same contexts alone, and a
