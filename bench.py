@@ -594,6 +594,9 @@ def main():
     stream = torch.cuda.Stream()
     sim.set_stream(stream.cuda_stream)
     sim.load(x, v)
+    # the library's autotuner (field-only passes, the state does not advance):
+    # the field CTA size and the group-scan segment length for this instance
+    tuned = sim.autotune()
     sim.step_async(args.warmup)
     sim.sync()
 
@@ -727,7 +730,8 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": workload_desc(w), "N": N, "l_max": w.l_max,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                           "l2": "inputs larger than L2 (per-step working set > 300 MB)"},
+                           "l2": "inputs larger than L2 (per-step working set > 300 MB)",
+                           "autotuned": {"warps_per_cta": tuned[0], "groups_per_segment": tuned[1]}},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": step_launches(N) * args.steps, "clocks": clocks, "fp64_gpu": fp64,
                 "oracle_err": oerr, "configs": subs, "serving": serving, "ensemble": ensemble,
