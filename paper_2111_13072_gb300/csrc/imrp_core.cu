@@ -467,8 +467,8 @@ constexpr int kBsCapMax = 13312;  // 208 KB of buckets beside the static shared 
 constexpr int64_t kBsSmallN = 1 << 19;  // up to here an 8-bit first pass (256 buckets), beyond a 9-bit one (512)
 constexpr int64_t kBsSingleN = 3072;     // up to here, one CTA sorts everything (N = 1000: 13 us)
 // shared-memory capacity for segments of g of nd buckets: three times the mean
-// segment with 256 buckets; 1.5 times with 512 (two CTAs of 99 KB per SM at
-// N = 2e6; a larger bucket goes through L2)
+// segment with 256 buckets; 1.5 times with 512 (at N = 2e6 two CTAs per SM of
+// 101 KB, 94 KB of them buckets; a larger bucket goes through L2)
 inline int bucket_cap(int64_t n, int g, int nd) {
   const int64_t mean = int64_t(g) * n / nd;
   int64_t c = ((nd == 256 ? 3 * mean : mean + mean / 2) + 255) / 256 * 256;
